@@ -1,0 +1,104 @@
+"""Exact diagonalisation of H_eta = H - eta Q for the hard-core Bose-Hubbard
+model on a small periodic Lx x Ly lattice (TEST INFRASTRUCTURE ONLY).
+
+H is Eq. 5 of the paper read per bond over the same bond list the Monte Carlo
+uses (bond b = 2a + d joins a to a + x^ or a + y^, so a 2-site-wide direction
+carries every pair twice):
+    H = sum_b [ -t (b+_a b_c + b+_c b_a) + V n_a n_c - (mu/4)(n_a + n_c) ],
+which is -t sum(b+b + h.c.) + V sum n n - mu sum_i n_i on the square lattice
+(each site ends 4 bonds), and Q = sum_i (b_i + b+_i) (the worm source term).
+Thermal averages at inverse temperature beta from numpy's eigh.
+"""
+import numpy as np
+
+
+def bonds(Lx, Ly):
+    out = []
+    for y in range(Ly):
+        for x in range(Lx):
+            a = x + Lx * y
+            out.append((a, (x + 1) % Lx + Lx * y))
+            out.append((a, x + Lx * ((y + 1) % Ly)))
+    return out
+
+
+def _ops(N):
+    dim = 1 << N
+    states = np.arange(dim)
+    occ = [((states >> i) & 1).astype(np.float64) for i in range(N)]
+    return dim, states, occ
+
+
+def hamiltonians(Lx, Ly, t, V, mu, eta):
+    """Dense H (model only) and Q; H_eta = H - eta Q."""
+    N = Lx * Ly
+    dim, states, occ = _ops(N)
+    H = np.zeros((dim, dim))
+    diag = np.zeros(dim)
+    for a, c in bonds(Lx, Ly):
+        diag += V * occ[a] * occ[c] - (mu / 4.0) * (occ[a] + occ[c])
+        # hopping: |..1_a..0_c..> <-> |..0_a..1_c..>
+        m = (occ[a] == 1) & (occ[c] == 0)
+        src = states[m]
+        dst = src ^ (1 << a) ^ (1 << c)
+        H[dst, src] += -t
+        H[src, dst] += -t
+    H[np.arange(dim), np.arange(dim)] += diag
+    Q = np.zeros((dim, dim))
+    for i in range(N):
+        src = states
+        dst = states ^ (1 << i)
+        Q[dst, src] += 1.0
+    return H, Q
+
+
+def thermal(Lx, Ly, beta, t, V, mu, eta, slices_r=True):
+    """Exact thermal averages: E/N (of H), <n>, <Q>/N, <b+b+h.c.> per bond,
+    and G_QQ(r) = <Q_i Q_{i+r x^}> averaged over i, r = 1..Lx-1."""
+    N = Lx * Ly
+    H, Q = hamiltonians(Lx, Ly, t, V, mu, eta)
+    Heta = H - eta * Q
+    w, U = np.linalg.eigh(Heta)
+    w0 = w.min()
+    p = np.exp(-beta * (w - w0))
+    Z = p.sum()
+
+    def avg(A):
+        diag = np.einsum("ik,ik->k", U, A @ U)   # <k|A|k> in the eigenbasis
+        return float(p @ diag / Z)
+
+    dim, states, occ = _ops(N)
+    nop = np.diag(sum(occ))
+    Hkin = H - np.diag(np.diag(H))
+    out = dict(E=avg(H) / N, n=avg(nop) / N, Q=avg(Q) / N,
+               kin=avg(-Hkin) / (t * 2 * N) if t > 0 else 0.0)
+    if slices_r:
+        G = []
+        Qi = []
+        for i in range(N):
+            A = np.zeros((dim, dim))
+            A[states ^ (1 << i), states] = 1.0
+            Qi.append(A)
+        for r in range(1, Lx):
+            acc = 0.0
+            for y in range(Ly):
+                for x in range(Lx):
+                    i = x + Lx * y
+                    j = (x + r) % Lx + Lx * y
+                    acc += avg(Qi[i] @ Qi[j])
+            G.append(acc / N)
+        out["G"] = np.array(G)
+    return out
+
+
+def single_site(beta, mu, eta):
+    """Closed form at t = 0, V = 0, where the sites decouple.  Each site is
+    h = -mu n - eta (b + b+) = -mu/2 + (mu/2) sz - eta sx (sz = 1 - 2n), a spin
+    in a field of size D = sqrt(mu^2/4 + eta^2), so
+        <n> = 1/2 + (mu / (4 D)) tanh(beta D),  <Q_i> = (eta / D) tanh(beta D),
+    and E/N = -mu <n>."""
+    D = np.sqrt(mu * mu / 4.0 + eta * eta)
+    th = np.tanh(beta * D)
+    n = 0.5 + (mu / (4.0 * D)) * th
+    Q = (eta / D) * th
+    return dict(n=n, Q=Q, E=-mu * n)

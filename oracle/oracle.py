@@ -1,0 +1,246 @@
+"""ctypes binding of the plain C oracle (pmwa_oracle.c).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The oracle follows the
+paper's Steps 2-6 (Masaki-Kato et al., "Parallelized Quantum Monte Carlo
+Algorithm with Nonlocal Worm Updates": Eqs. 1, 2, 4, 5 and Supplement S-I) in
+the deterministic arithmetic the GPU path also implements.
+"""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pmwa_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle_pmwa.so")
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "pmwa_oracle.h")))):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32),
+                ("beta", C.c_double), ("t", C.c_double), ("V", C.c_double),
+                ("mu", C.c_double), ("eta", C.c_double),
+                ("seed", C.c_uint64),
+                ("dom_x", C.c_int32), ("dom_y", C.c_int32),
+                ("exchange_every", C.c_int32), ("n_cycle", C.c_int32),
+                ("sub_block", C.c_int32), ("init", C.c_int32),
+                ("init_seed", C.c_uint64), ("c_off", C.c_double),
+                ("replica", C.c_uint32)]
+
+
+class Row(C.Structure):
+    _fields_ = [("sweep", C.c_uint64), ("n_v", C.c_uint64), ("n_k", C.c_uint64),
+                ("n_w", C.c_uint64), ("occ_lo", C.c_uint64), ("occ_hi", C.c_uint64),
+                ("q_impr", C.c_double), ("pad", C.c_double)]
+
+
+ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
+                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("pad", "<f8")])
+
+DEFAULTS = dict(Lx=4, Ly=4, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1,
+                dom_x=0, dom_y=0, exchange_every=2, n_cycle=8, sub_block=0,
+                init=1, init_seed=1, c_off=-1.0, replica=0)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.POINTER
+        L.or_create.argtypes = [P(Params), P(C.c_void_p)]
+        L.or_destroy.argtypes = [C.c_void_p]
+        L.or_sweep.argtypes = [C.c_void_p, C.c_int64]
+        L.or_boundary.argtypes = [C.c_void_p]
+        L.or_tile.argtypes = [C.c_void_p, C.c_int]
+        L.or_check.argtypes = [C.c_void_p]
+        L.or_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.or_rows.restype = C.c_int64
+        L.or_export_bytes.argtypes = [C.c_void_p]
+        L.or_export_bytes.restype = C.c_size_t
+        L.or_export.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.or_import.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.or_sweep_index.argtypes = [C.c_void_p]
+        L.or_sweep_index.restype = C.c_uint64
+        L.or_set_sweep_index.argtypes = [C.c_void_p, C.c_uint64]
+        L.or_rho_slices.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_exp_det.argtypes = [C.c_double]
+        L.or_exp_det.restype = C.c_double
+        L.or_expm1_det.argtypes = [C.c_double]
+        L.or_expm1_det.restype = C.c_double
+        L.or_zig_tables.argtypes = [C.c_void_p] * 6
+        L.or_exp_deviates.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                      C.c_int64, C.c_void_p]
+        L.or_sample_worms.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                      C.c_uint64, C.c_int, C.c_double, C.c_void_p, C.c_int]
+        L.or_tables.argtypes = [P(Params)] + [C.c_void_p] * 6
+        _lib = L
+    return _lib
+
+
+def make_params(**kw):
+    d = dict(DEFAULTS)
+    d.update(kw)
+    if not d["dom_x"]:
+        d["dom_x"] = d["Lx"]
+    if not d["dom_y"]:
+        d["dom_y"] = d["Ly"]
+    return Params(**d)
+
+
+class Oracle:
+    """One PMWA instance on the CPU."""
+
+    def __init__(self, **kw):
+        self.params = make_params(**kw)
+        self.h = C.c_void_p()
+        rc = lib().or_create(C.byref(self.params), C.byref(self.h))
+        if rc:
+            raise ValueError("or_create failed with status %d" % rc)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.or_destroy(self.h)
+            self.h = None
+
+    def _ok(self, rc, what):
+        if rc:
+            raise RuntimeError("%s failed with status %d" % (what, rc))
+
+    def sweep(self, n=1):
+        self._ok(lib().or_sweep(self.h, n), "or_sweep")
+
+    def boundary(self):
+        self._ok(lib().or_boundary(self.h), "or_boundary")
+
+    def tile(self, stop_after=6):
+        self._ok(lib().or_tile(self.h, stop_after), "or_tile")
+
+    def check(self):
+        return lib().or_check(self.h)
+
+    @property
+    def sweep_index(self):
+        return lib().or_sweep_index(self.h)
+
+    @sweep_index.setter
+    def sweep_index(self, v):
+        lib().or_set_sweep_index(self.h, v)
+
+    def rows(self, max_rows=1 << 24):
+        out = np.zeros(max_rows, dtype=ROW_DTYPE) if max_rows < 4096 else None
+        chunks = []
+        while True:
+            buf = np.zeros(min(max_rows, 65536), dtype=ROW_DTYPE)
+            n = lib().or_rows(self.h, buf.ctypes.data, len(buf))
+            chunks.append(buf[:n])
+            if n < len(buf):
+                break
+        del out
+        return np.concatenate(chunks)
+
+    def export(self):
+        n = lib().or_export_bytes(self.h)
+        buf = np.zeros(n // 8, dtype=np.uint64)
+        self._ok(lib().or_export(self.h, buf.ctypes.data, n), "or_export")
+        return buf
+
+    def import_(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint64)
+        self._ok(lib().or_import(self.h, buf.ctypes.data, buf.nbytes), "or_import")
+
+    def rho_slices(self, K):
+        N = self.params.Lx * self.params.Ly
+        out = np.zeros((N, K), dtype=np.float64)
+        self._ok(lib().or_rho_slices(self.h, K, out.ctypes.data), "or_rho_slices")
+        return out
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return o
+
+
+def zig_tables():
+    X = np.zeros(257); F = np.zeros(257); W = np.zeros(256)
+    K = np.zeros(256, dtype=np.uint64); R = C.c_double(); v = C.c_double()
+    lib().or_zig_tables(X.ctypes.data, F.ctypes.data, W.ctypes.data, K.ctypes.data,
+                        C.byref(R), C.byref(v))
+    return dict(X=X, F=F, W=W, K=K, R=R.value, v=v.value)
+
+
+def exp_deviates(n, seed=1, unit=0, c2=0, sweep=0):
+    out = np.zeros(n)
+    rc = lib().or_exp_deviates(seed, unit, c2, sweep, n, out.ctypes.data)
+    if rc:
+        raise RuntimeError("or_exp_deviates status %d" % rc)
+    return out
+
+
+def sample_worms(M, sigma, SW, seed=1, unit=0, c2=0, sweep=0, maxn=4096):
+    offs = np.zeros(maxn, dtype=np.uint64)
+    n = lib().or_sample_worms(seed, unit, c2, sweep, M, sigma, SW, offs.ctypes.data, maxn)
+    if n < 0:
+        raise RuntimeError("or_sample_worms failed")
+    return offs[:n]
+
+
+def tables(**kw):
+    p = make_params(**kw)
+    d4 = np.zeros(4); D = C.c_double(); TV = np.zeros(4, dtype=np.uint64)
+    TH = np.zeros(256, dtype=np.uint64); SV = C.c_double(); SW = C.c_double()
+    lib().or_tables(C.byref(p), d4.ctypes.data, C.byref(D), TV.ctypes.data, TH.ctypes.data,
+                    C.byref(SV), C.byref(SW))
+    return dict(d=d4, D=D.value, TV=TV, TH=TH.reshape(16, 4, 4), SV=SV.value, SW=SW.value)
+
+
+def observables(rows, p):
+    """Per-sweep physical observables from measured rows (Step 6).
+
+    E/N = (N_b C - n_v / beta) / N with C = max E(s) + c_off; density from the
+    occupied time; <Q>/N raw = n_w / (beta eta N), improved = sum x g(x) /
+    (beta eta N); kinetic <b+_i b_j + h.c.> per bond = n_k / (beta t N_b).
+    """
+    N = p.Lx * p.Ly
+    Nb = 2 * N
+    c_off = 0.5 * p.t if p.c_off < 0 else p.c_off
+    E = [p.V * (s & 1) * (s >> 1) - (p.mu / 4.0) * ((s & 1) + (s >> 1)) for s in range(4)]
+    Cc = max(E) + c_off
+    nv = rows["n_v"].astype(np.float64)
+    occ = rows["occ_lo"].astype(np.float64) + rows["occ_hi"].astype(np.float64) * 2.0 ** 64
+    out = dict(
+        E=(Nb * Cc - nv / p.beta) / N,
+        n=occ / (2.0 ** 62 * N),
+        Q_raw=rows["n_w"].astype(np.float64) / (p.beta * p.eta * N),
+        Q_impr=rows["q_impr"] / (p.beta * p.eta * N),
+    )
+    if p.t > 0:
+        out["kin"] = rows["n_k"].astype(np.float64) / (p.beta * p.t * Nb)
+    return out
+
+
+def binned(x, nbins=32):
+    """Mean and standard error from nbins equal bins of the series."""
+    x = np.asarray(x, dtype=np.float64)
+    m = len(x) // nbins
+    b = x[: m * nbins].reshape(nbins, m).mean(axis=1)
+    return float(b.mean()), float(b.std(ddof=1) / np.sqrt(nbins))

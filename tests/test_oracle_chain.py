@@ -1,0 +1,210 @@
+"""Pins of the whole oracle Markov chain (Steps 2-6) against exact
+diagonalisation, closed forms and invariants.
+
+Monte Carlo results are compared within 4 standard errors.  The error of an
+average comes from the scatter of R independent replicas (different seeds),
+which stays honest when the autocorrelation time is long (small lattices at
+small beta eta hold less than one worm on average and mix slowly).
+Each case lists the paper passage it exercises: Step 3 vertex phase, Step 4
+worm creation (Eq. 1), Step 5 worm scattering (Eq. 2), Step 2 spatial
+boundary update (Eq. 4), Step 6 measurements (Supplement S-I estimators).
+"""
+import numpy as np
+import pytest
+
+from oracle import ed
+from oracle import oracle as O
+
+Z = 4.0
+
+
+def _run(Lx, Ly, sweeps, therm=2000, **kw):
+    o = O.Oracle(Lx=Lx, Ly=Ly, **kw)
+    o.sweep(therm)
+    o.rows()
+    o.sweep(sweeps)
+    assert o.check() == 0
+    return o, O.observables(o.rows(), o.params)
+
+
+def _replicas(Lx, Ly, R, sweeps, therm=1000, seed0=1, **kw):
+    """Per-replica means of every observable: dict name -> array (R,)."""
+    out = {}
+    for r in range(R):
+        _, ob = _run(Lx, Ly, sweeps, therm=therm, seed=seed0 + r, **kw)
+        for k, v in ob.items():
+            out.setdefault(k, []).append(v.mean())
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def _mean_err(v):
+    return float(v.mean()), float(v.std(ddof=1) / np.sqrt(len(v)))
+
+
+def _agree(ob, ex, keys=("E", "n", "Q_raw", "Q_impr", "kin")):
+    want = dict(E=ex["E"], n=ex["n"], Q_raw=ex["Q"], Q_impr=ex["Q"], kin=ex.get("kin"))
+    msgs = []
+    for k in keys:
+        m, s = _mean_err(ob[k])
+        z = (m - want[k]) / s
+        msgs.append("%s %.5f+-%.5f ed %.5f z=%.2f" % (k, m, s, want[k], z))
+        assert abs(z) < Z, "; ".join(msgs)
+
+
+CASES = [
+    # (Lx, Ly, model, geometry, sweeps) -- model dicts use t, V, mu, beta, eta
+    (2, 2, dict(beta=2.0, eta=0.2), dict(), 200_000),                       # config-1 parameters
+    (3, 3, dict(beta=2.0, eta=0.2), dict(), 120_000),                       # config-1 parameters
+    (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=1.0), dict(), 120_000),
+    (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=-1.0), dict(), 120_000),
+    (3, 3, dict(beta=0.25, eta=1.0), dict(), 240_000),                      # beta t = 1/4
+    (4, 2, dict(beta=2.0, eta=0.3, V=1.0, mu=0.5), dict(dom_x=2, dom_y=2, sub_block=2), 100_000),
+    (2, 4, dict(beta=2.0, eta=0.3, mu=-0.7), dict(dom_x=2, dom_y=2, exchange_every=3), 100_000),
+    (4, 2, dict(beta=1.0, eta=0.3, V=0.5, t=0.6), dict(dom_x=4, dom_y=2, sub_block=2), 100_000),
+]
+
+
+@pytest.mark.parametrize("Lx,Ly,model,geo,sweeps", CASES)
+def test_chain_matches_ed(Lx, Ly, model, geo, sweeps):
+    m = dict(t=1.0, V=0.0, mu=0.0)
+    m.update(model)
+    ex = ed.thermal(Lx, Ly, m["beta"], m["t"], m["V"], m["mu"], m["eta"], slices_r=False)
+    ob = _replicas(Lx, Ly, 24, sweeps // 24, n_cycle=8, seed0=11, **m, **geo)
+    _agree(ob, ex)
+
+
+@pytest.mark.parametrize("geo", [dict(), dict(dom_x=4, dom_y=4, sub_block=2)])
+def test_decoupled_sites_at_any_size(geo):
+    """t = V = 0: every site is an independent two-level problem
+    -mu n - eta (b + b+), exact at any L (the vertices of Step 3 still carry
+    the chemical potential through d(s) = C + (mu/4)(na + nb))."""
+    beta, mu, eta = 2.0, 1.0, 0.4
+    ob = _replicas(8, 8, 16, 300, therm=100, beta=beta, t=0.0, V=0.0, mu=mu, eta=eta, c_off=0.5,
+                   n_cycle=4, seed0=5, **geo)
+    cf = ed.single_site(beta, mu, eta)
+    for k, want in [("n", cf["n"]), ("Q_raw", cf["Q"]), ("Q_impr", cf["Q"]), ("E", cf["E"])]:
+        m, s = _mean_err(ob[k])
+        assert abs(m - want) < Z * s, (k, m, s, want)
+
+
+def test_particle_hole_half_filling():
+    """V = mu = 0 is particle-hole symmetric: <n> = 1/2."""
+    ob = _replicas(6, 6, 16, 1500, therm=300, beta=2.0, eta=0.3, n_cycle=8, seed0=2,
+                   dom_x=3, dom_y=3)
+    m, s = _mean_err(ob["n"])
+    assert abs(m - 0.5) < Z * s
+
+
+def test_improved_estimator_identity():
+    """Supplement S-I: <rho>/eta (improved) and n_w/(beta eta) (raw) have the
+    same expectation; their per-sweep difference averages to zero."""
+    ob = _replicas(4, 4, 16, 2500, therm=500, beta=4.0, eta=0.3, V=0.5, mu=0.3, n_cycle=8, seed0=3)
+    m, s = _mean_err(ob["Q_raw"] - ob["Q_impr"])
+    assert abs(m) < Z * s
+
+
+def test_green_function_two_point():
+    """Supplement S-I: <Q_i Q_j> = <rho_i rho_j> / eta^2 for i != j at equal
+    time, against ED on 3x3 (r = 1 along x, 4 time slices)."""
+    Lx = Ly = 3
+    beta, eta = 2.0, 0.3
+    ex = ed.thermal(Lx, Ly, beta, 1.0, 0.0, 0.0, eta)
+    o = O.Oracle(Lx=Lx, Ly=Ly, beta=beta, eta=eta, n_cycle=8, seed=17)
+    o.sweep(1000)
+    vals = []
+    idx = np.arange(Lx * Ly)
+    nbr = (idx % Lx + 1) % Lx + Lx * (idx // Lx)
+    for _ in range(60000):
+        o.sweep(1)
+        r = o.rho_slices(4)
+        vals.append((r * r[nbr]).mean() / eta ** 2)
+    m, s = O.binned(np.array(vals), 64)
+    assert abs(m - ex["G"][0]) < Z * s, (m, s, ex["G"][0])
+
+
+def test_eta_to_zero_quadratic_extrapolation():
+    """Eq. 6: the O(eta) term of <H>_eta vanishes, so E(eta) = a + b eta^2 +
+    c eta^4; the weighted fit of Monte Carlo energies at four eta reaches the
+    ED energy of H at eta = 0."""
+    Lx = Ly = 3
+    beta = 2.0
+    etas = np.array([0.3, 0.45, 0.6, 0.75])
+    E, S = [], []
+    for k, eta in enumerate(etas):
+        ob = _replicas(Lx, Ly, 16, 4000, beta=beta, eta=eta, n_cycle=8, seed0=100 + 16 * k)
+        m, s = _mean_err(ob["E"])
+        E.append(m)
+        S.append(s)
+    E, S = np.array(E), np.array(S)
+    A = np.stack([np.ones_like(etas), etas ** 2, etas ** 4], axis=1) / S[:, None]
+    coef, *_ = np.linalg.lstsq(A, E / S, rcond=None)
+    cov = np.linalg.inv(A.T @ A)
+    e0 = ed.thermal(Lx, Ly, beta, 1.0, 0.0, 0.0, 0.0, slices_r=False)["E"]
+    assert abs(coef[0] - e0) < Z * np.sqrt(cov[0, 0]), (coef, np.sqrt(cov[0, 0]), e0)
+
+
+INV_CASES = [
+    dict(Lx=2, Ly=2, beta=1.0, eta=0.5, init=0),
+    dict(Lx=4, Ly=4, beta=2.0, eta=0.3, V=1.0, mu=0.7, dom_x=2, dom_y=2, sub_block=2, exchange_every=1),
+    dict(Lx=6, Ly=4, beta=3.0, eta=0.2, mu=-1.0, dom_x=3, dom_y=2, exchange_every=2),
+    dict(Lx=8, Ly=8, beta=1.0, eta=0.4, dom_x=4, dom_y=4, sub_block=2, t=0.5, V=2.0, mu=1.5),
+    dict(Lx=3, Ly=5, beta=4.0, eta=0.1, t=0.0, c_off=0.3, mu=0.8),
+]
+
+
+@pytest.mark.parametrize("kw", INV_CASES)
+def test_invariants_after_every_step(kw):
+    """Occupations in {0,1}, strictly increasing times, continuity of every
+    worldline away from worms, partner legs, particle conservation at every
+    vertex: checked after Step 2, Step 3, Step 4, Step 5 of every sweep."""
+    o = O.Oracle(n_cycle=4, seed=23, **kw)
+    nd = (kw["Lx"] // kw.get("dom_x", kw["Lx"])) * (kw["Ly"] // kw.get("dom_y", kw["Ly"]))
+    K = kw.get("exchange_every", 2)
+    for s in range(60):
+        if nd > 1 and s % K == 0:
+            o.boundary()
+            assert o.check() == 0
+        snap = o.export()
+        for stop in (3, 4, 5, 6):
+            o.import_(snap)
+            o.tile(stop)
+            assert o.check() == 0, (s, stop)
+        o.sweep_index = o.sweep_index + 1
+
+
+def test_checkpoint_resume_bit_exact():
+    """2n sweeps equal n sweeps, export, import into a fresh instance, n more."""
+    kw = dict(Lx=6, Ly=6, beta=2.0, eta=0.3, V=0.5, mu=0.2, dom_x=3, dom_y=3,
+              sub_block=0, n_cycle=5, seed=77)
+    a = O.Oracle(**kw)
+    a.sweep(40)
+    b = O.Oracle(**kw)
+    b.sweep(20)
+    snap = b.export()
+    c = O.Oracle(**kw)
+    c.import_(snap)
+    c.sweep_index = 20
+    c.sweep(20)
+    assert np.array_equal(a.export(), c.export())
+
+
+def test_deterministic():
+    kw = dict(Lx=4, Ly=4, beta=2.0, eta=0.3, n_cycle=3, seed=9, dom_x=2, dom_y=2, sub_block=2)
+    a = O.Oracle(**kw)
+    b = O.Oracle(**kw)
+    a.sweep(15)
+    b.sweep(15)
+    assert np.array_equal(a.export(), b.export())
+    kw["seed"] = 10
+    c = O.Oracle(**kw)
+    c.sweep(15)
+    assert not np.array_equal(a.export(), c.export())
+
+
+def test_half_filled_initial_state():
+    o = O.Oracle(Lx=8, Ly=6, init=1, init_seed=7)
+    buf = o.export()
+    assert buf[0] == 48
+    hdr = buf[1:]
+    assert np.all((hdr & np.uint64(0x7FFFFFFF)) == 0)
+    assert int((hdr >> np.uint64(63)).sum()) == 24

@@ -1,0 +1,312 @@
+"""Benchmark of the PMWA sweep on GB300: vertex updates per second.
+
+A step is one MC sweep (Steps 2-6 of the paper's pseudo code) of the whole
+lattice.  The default workload is the 256x256 hard-core Bose-Hubbard lattice
+(t=1, V=0, mu=0, beta t=4, eta=0.1) cut into 16x16-site domains spanning the
+full beta, boundary exchange every 2 sweeps, half-filled static start (seed
+7); N_cycle follows the rule "every part of the space-time updated about
+once" (each vertex leg visited once per sweep on average: N_cycle =
+ceil(2 <n_v> / <n_w>) from a pilot run).  Inputs are synthetic: the lattice
+parameters are the whole input.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload config2|config4|config1]
+
+Prints one JSON line.  `value` = vertices summed over the timed sweeps / the
+device time of those sweeps (CUDA events recorded by the library on its
+stream around each sweep), max over ranks; L2 is flushed before every timed
+sweep.  `--impl reference` times the CPU oracle instead (single thread).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertex updates/s per GB300 (hard-core BH), batched vs plain; % of HBM roofline"
+UNIT = "vertex updates/s"
+
+WORKLOADS = {
+    "config2": dict(Lx=256, Ly=256, beta=4.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
+                    exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
+    "config4": dict(Lx=2048, Ly=2048, beta=16.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
+                    exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
+    "config1": dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, dom_x=8, dom_y=8,
+                    exchange_every=2, sub_block=0, init=1, init_seed=1, seed=1),
+}
+DESCR = {
+    "config2": "256x256 periodic hcBH, t=1 V=0 mu=0 beta*t=4 eta=0.1, 16x16-site domains, K=2",
+    "config4": "2048x2048 periodic hcBH, t=1 V=0 mu=0 beta*t=16 eta=0.1, 128x128 domains of 16x16 sites, K=2",
+    "config1": "8x8 periodic hcBH, t=1 V=0 mu=0 beta*t=2 eta=0.2, one domain",
+}
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncycle_rule(n_v, n_w):
+    """Every vertex leg visited once per sweep on average: each move lands a
+    worm on one leg, a sweep has 2 n_v legs and n_w worms move per pass."""
+    return max(1, min(4095, int(math.ceil(2.0 * n_v / max(n_w, 1.0)))))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle legs
+def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
+    """Time the CPU oracle (as it stands, one thread) on the workload:
+    vertices summed over the timed sweeps / wall time."""
+    from oracle import oracle as O
+    kw = dict(WORKLOADS[wl])
+    o = O.Oracle(n_cycle=n_cycle, **kw)
+    o.sweep(max(1, warmup))
+    o.rows()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.sweep(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps and steps >= max_steps) or (not max_steps and el >= seconds):
+            break
+    r = o.rows()
+    return float(r["n_v"].sum()) / el, steps, el
+
+
+def run_reference(args, wl, n_cycle):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rate, steps, el = oracle_rate(wl, n_cycle, 0, max_steps=args.steps, warmup=args.warmup)
+    sample = "%d oracle sweeps (%d warm-up) of the %s workload, N_cycle=%d" % (steps, args.warmup, wl, n_cycle)
+    line = dict(metric=METRIC, value=rate, unit=UNIT, impl="reference", n_gpus=args.gpus,
+                steps=steps, warmup=args.warmup, ms_per_step=1000.0 * el / steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u64",
+                data="synthetic", config=dict(workload=DESCR[wl], n_cycle=n_cycle),
+                cpu_baseline=dict(value=rate, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=rate, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
+    ap.add_argument("--pilot", type=int, default=30, help="thermalisation sweeps of the N_cycle pilot")
+    ap.add_argument("--n-cycle", type=int, default=0, help="fix N_cycle instead of the pilot rule")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = args.workload
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        nc = args.n_cycle or {"config2": 86, "config4": 60, "config1": 8}[wl]
+        run_reference(args, wl, nc)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1307_0328_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load()
+
+    kw = dict(WORKLOADS[wl])
+    kw["replica"] = rank  # independent replicas, one per GPU
+    # pilot: thermalise and apply the N_cycle rule
+    if args.n_cycle:
+        nc = args.n_cycle
+        sim = P.Sim(n_cycle=nc, **kw)
+        sim.sweep(args.pilot)
+        sim.rows()
+    else:
+        pilot = P.Sim(n_cycle=16, **kw)
+        pilot.sweep(args.pilot)
+        r = pilot.rows()
+        half = r[len(r) // 2:]
+        nc = ncycle_rule(half["n_v"].mean(), half["n_w"].mean())
+        snap = pilot.export()
+        s_idx = pilot.sweep_index
+        pilot.close()
+        del pilot
+        sim = P.Sim(n_cycle=nc, **kw)
+        sim.import_(snap)
+        sim.sweep_index = s_idx
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = sim.stream
+
+    # warm-up
+    sim.sweep(args.warmup)
+    sim.rows()
+    # timed region: per-sweep device spans (library events on its stream)
+    P.pmwa_profile(sim.h, True)
+    P.pmwa_profile_read(sim.h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 (256 MB > 129 MB) between timed sweeps
+        sim.sweep(1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    prof = P.pmwa_profile_read(sim.h)
+    P.pmwa_profile(sim.h, False)
+    clk = clocks.stop()
+    rows = sim.rows()
+    span_ms = prof["sweep"][0]
+    nv = float(rows["n_v"].sum())
+    nw = float(rows["n_w"].mean())
+    t_local = span_ms / 1000.0
+    if world > 1:
+        t = torch.tensor([t_local, nv], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        t_job, nv_job = float(tmax[0]), float(t[1])
+    else:
+        t_job, nv_job = t_local, nv
+    value = nv_job / t_job
+
+    # e2e through the public API: sweep + read the step's measurement row
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    nv_e2e = 0.0
+    for _ in range(args.steps):
+        sim.sweep(1)
+        r = sim.rows()
+        nv_e2e += float(r["n_v"].sum())
+    e_t = time.perf_counter() - e0
+    e2e_local = nv_e2e / e_t
+    if world > 1:
+        t = torch.tensor([e_t, nv_e2e], device=dev, dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_val = float(t[1]) / float(tm[0])
+    else:
+        e2e_val = e2e_local
+
+    if rank == 0:
+        kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
+        top = max((k for k in kernels if k != "sweep"), key=lambda k: kernels[k]["ms_total"])
+        peak, which = peaks()
+        # algorithmic bytes of the merge + worm-creation kernel: read the old
+        # configuration and the new vertices, write keys and labels of the new one
+        ev = float(2 * rows["n_v"].mean() + rows["n_w"].mean())
+        alg = dict(merge_worm_creation=8.0 * (ev + 0.5 * 2 * rows["n_v"].mean() + 2 * ev),
+                   vertex_candidates=8.0 * (2 * ev + 0.5 * rows["n_v"].mean()),
+                   scatter=8.0 * 4 * ev, measure=8.0 * ev, boundary=8.0 * ev * 0.25)
+        tk = kernels[top]
+        per_launch_ms = tk["ms_total"] / tk["launches"]
+        achieved = alg.get(top, 0.0) / (per_launch_ms / 1000.0) / 1e9
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=1000.0 * t_job / args.steps, higher_is_better=True, scaling="weak",
+            vs_baseline=None, dtype="u64", data="synthetic",
+            config=dict(workload=DESCR[wl], n_cycle=nc, sub_block=kw["sub_block"], replicas_per_gpu=1,
+                        l2="flushed before every timed sweep (256 MB write)",
+                        mean_vertices=float(rows["n_v"].mean()), mean_worms=nw,
+                        plain_per_instance=True),
+            roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=peak, unit="GB/s",
+                          frac=achieved / peak, traffic=None,
+                          peak_source=which + " MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"),
+            kernels=kernels,
+            e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=64),
+            gpu_launches=int(sum(v["launches"] for k, v in kernels.items() if k != "sweep")),
+            clocks=clk, wall_s=wall,
+        )
+        if not args.no_cpu:
+            rate, steps, el = oracle_rate(wl, nc, args.cpu_seconds, warmup=1)
+            line["cpu_baseline"] = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
+                                        sample="%d oracle sweeps of the %s workload (N_cycle=%d), %.1f s"
+                                        % (steps, wl, nc, el))
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

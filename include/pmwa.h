@@ -1,0 +1,165 @@
+/*
+ * pmwa.h -- C ABI of libpmwa.so: the parallelized multiple-worm algorithm
+ * (PMWA) Monte Carlo sweep for the hard-core Bose-Hubbard model on one GB300.
+ *
+ * Method: Masaki-Kato, Suzuki, Harada, Todo, Kawashima, "Parallelized Quantum
+ * Monte Carlo Algorithm with Nonlocal Worm Updates" (arXiv:1307.0328).
+ * The simulated Hamiltonian is H_eta = H - eta Q with Q = sum_i (b_i + b_i^+)
+ * (introduction; Eq. 5 for H, read as -t sum_<ij>(b+_i b_j + h.c.)
+ * + V sum_<ij> n_i n_j - mu sum_i n_i and written per bond with
+ * -(mu/4)(n_i + n_j)).  One MC step ("sweep") is the paper's pseudo code:
+ *   Step 2  spatial-boundary update of the vertices on bonds between domains
+ *           (Eq. 4), every `exchange_every` sweeps, followed there by Step 3
+ *           on those bonds;
+ *   Step 3  vertex phase on all other bonds;
+ *   Step 4  worm creation on every interval (Eq. 1);
+ *   Step 5  N_cycle passes of worm scattering (Eq. 2);
+ *   Step 6  measurement (energy, density, order parameter <Q>, and the
+ *           worm-density estimator of Supplement S-I).
+ * All domains live in one GPU's HBM; the paper's neighbour messages become
+ * kernels that read the neighbour's sites directly.
+ *
+ * Conventions for every call:
+ *   - Status: 0 = PMWA_OK, else one of the PMWA_E* codes; pmwa_strerror()
+ *     names them.  Calls never abort the process.
+ *   - Memory: the caller owns the params, the device arena and every output
+ *     buffer.  The handle holds small host tables only.
+ *   - Streams: work is queued on the stream given to pmwa_create (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).  Calls that
+ *     return data to the host are synchronous; pmwa_sweep is synchronous too
+ *     (it reports device-side errors).
+ *   - Layout of the configuration (canonical export format, identical to the
+ *     CPU oracle's): u64 n_sites, then for every site i = x + Lx*y a u64
+ *     header (count | base_state << 63) followed by `count` u64 event keys
+ *     sorted in time.  Key bits 63..5: time-grid index m (2^59 points per
+ *     beta); bits 4..2: tag (0..5 vertex leg of the bond of class tag, 7
+ *     worm); bit 1: state below (vertex leg) or direction up (worm); bit 0:
+ *     state above.
+ */
+#ifndef PMWA_H
+#define PMWA_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMWA_OK          0
+#define PMWA_EINVAL      1  /* bad parameter or buffer size                       */
+#define PMWA_ECAPACITY   2  /* a fixed-capacity list would overflow               */
+#define PMWA_ETIMEOUT    3  /* a bounded device loop reached its cap              */
+#define PMWA_ECUDA       4  /* a CUDA runtime call failed                         */
+#define PMWA_EINVARIANT  5  /* the configuration breaks an invariant              */
+#define PMWA_EROWS       6  /* measurement row buffer full: call pmwa_measure     */
+
+/* Simulation parameters (problem statement: introduction, Eq. 5; domains:
+   Supplement S-II; Step-5 passes: Step 6 of the pseudo code). */
+typedef struct {
+  int32_t  Lx, Ly;          /* periodic square lattice, both >= 2                 */
+  double   beta, t, V, mu, eta; /* beta > 0, t >= 0, eta > 0                      */
+  uint64_t seed;            /* Philox4x32-10 key of every random draw             */
+  int32_t  dom_x, dom_y;    /* sites per domain; 0 = whole axis; must divide L;
+                               >= 2 when an axis has several domains              */
+  int32_t  exchange_every;  /* K >= 1: Step 2 runs when sweep % K == 0            */
+  int32_t  n_cycle;         /* Step-5 passes per sweep, 0..4095                   */
+  int32_t  sub_block;       /* Step-5 shifted sub-block edge B (even); 0 = domain */
+  int32_t  init;            /* 0: empty lattice; 1: floor(N/2) particles placed by
+                               a Fisher-Yates permutation of stream init_seed     */
+  uint64_t init_seed;
+  double   c_off;           /* diagonal vertex weight offset; < 0 means t/2       */
+  uint32_t replica;         /* 0..65535, mixed into every Philox counter          */
+  int32_t  cap_site;        /* events per site slot; 0 = sized from beta, t, V, mu */
+  int32_t  rows_cap;        /* measurement rows held on the device; 0 = 4096      */
+  int32_t  reserved[5];     /* must be 0                                          */
+} pmwa_params;
+
+/* One row per sweep (Step 6 measurement after Step 5). */
+typedef struct {
+  uint64_t sweep;   /* sweep index                                              */
+  uint64_t n_v;     /* vertices (diagonal + kinks) on all bonds                 */
+  uint64_t n_k;     /* kinks                                                    */
+  uint64_t n_w;     /* worms                                                    */
+  uint64_t occ_lo;  /* sum over sites of occupied imaginary time, in units of   */
+  uint64_t occ_hi;  /*   beta / 2^62, as a 128-bit integer (hi:lo)              */
+  double   q_impr;  /* Supplement S-I: sum over intervals of x g_sigma(x),
+                       x = I eta, g_0 = tanh, g_1 = coth; <Q> = q_impr/(beta eta) */
+  double   pad;
+} pmwa_row;
+
+typedef struct pmwa_handle pmwa_handle;
+
+/* Bytes of device arena that pmwa_create needs for these parameters
+   (0 if the parameters are invalid). */
+size_t pmwa_footprint(const pmwa_params* p);
+
+/* Validate p, carve the caller's device arena (arena_bytes >=
+   pmwa_footprint(p), 256-byte aligned), build the host tables (directed-loop
+   thresholds of Eq. 2, vertex thinning thresholds, ziggurat), write the
+   initial configuration, and return a handle.  The arena must stay valid
+   until pmwa_destroy.  stream: cudaStream_t or NULL. */
+int pmwa_create(const pmwa_params* p, void* dev_arena, size_t arena_bytes,
+                void* stream, pmwa_handle** out);
+
+/* Run n_sweeps MC steps (pseudo code Steps 1-6; Step 1 is absent because
+   every domain spans the whole of beta).  One measurement row per sweep.
+   PMWA_EROWS if the rows would not fit: drain them with pmwa_measure first. */
+int pmwa_sweep(pmwa_handle* h, int64_t n_sweeps);
+
+/* Fine-grained steps, for parity checks: Step 2 (+ Step 3 on the boundary
+   bonds) regardless of the sweep index; and Steps 3..stop_after of one sweep
+   (stop_after in 3..6; 6 also records a row).  Neither advances the sweep
+   index. */
+int pmwa_boundary(pmwa_handle* h);
+int pmwa_tile(pmwa_handle* h, int32_t stop_after);
+
+/* Copy up to max_rows pending rows to host memory `rows`, oldest first, and
+   drop them from the device buffer; *n_rows = number copied. */
+int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_rows);
+
+/* Supplement S-I worm density at K equal-time slices tau_k = k beta / K:
+   host_out[i*K + k] = eta g_sigma(I eta) of the interval (between vertex
+   legs) that holds tau_k on site i.  host_out holds N*K doubles. */
+int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out);
+
+/* Canonical configuration (format in the header comment) to / from host
+   memory.  pmwa_export_bytes gives the size; pmwa_import checks the
+   invariants and the per-site capacity. */
+int pmwa_export_bytes(pmwa_handle* h, size_t* bytes);
+int pmwa_export(pmwa_handle* h, void* host_buf, size_t bytes);
+int pmwa_import(pmwa_handle* h, const void* host_buf, size_t bytes);
+
+/* Sweep index (the Philox counter word of every draw of a sweep). */
+int pmwa_get_sweep(pmwa_handle* h, uint64_t* sweep);
+int pmwa_set_sweep(pmwa_handle* h, uint64_t sweep);
+
+/* Release the handle (the arena stays the caller's). */
+int pmwa_destroy(pmwa_handle* h);
+
+/* Host tables derived from p, for comparison with an independent
+   implementation: d4[4] diagonal vertex weights d(s) = C - E(s); *D = max d;
+   tv4[4] thinning thresholds floor(d/D 2^32); th256[16*4*4] directed-loop
+   cumulative exit thresholds (Eq. 2) by root state S, entry leg i, exit leg
+   j; *sv = 2^59/(beta D); *sw = 2^59/(beta eta); zig: X[257], F[257],
+   W[256] doubles and K[256] u64 of the exponential ziggurat (any may be NULL). */
+int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4,
+                uint64_t* th256, double* sv, double* sw,
+                double* zig_x, double* zig_f, double* zig_w, uint64_t* zig_k);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+   every launch (enable = 1 turns it on, 0 off and clears).  pmwa_profile_read
+   synchronises and returns, for kernel k = 0 boundary, 1 vertex candidates,
+   2 merge + worm creation, 3 scattering, 4 measurement, 5 rho slices, and
+   6 the device span of each whole sweep of pmwa_sweep, the summed device
+   milliseconds ms[k] and the number of launches[k] since the last read
+   (n >= 7 entries each), then clears them.  No paper counterpart:
+   measurement plumbing. */
+int pmwa_profile(pmwa_handle* h, int32_t enable);
+int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
+
+const char* pmwa_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

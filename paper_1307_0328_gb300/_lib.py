@@ -1,0 +1,278 @@
+"""ctypes binding of libpmwa.so (C ABI in include/pmwa.h).
+
+Argument marshalling only: every step of the sweep runs in the library's
+CUDA kernels.  Loading fails loudly when the library is missing; there is no
+fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PMWA_OK, PMWA_EINVAL, PMWA_ECAPACITY, PMWA_ETIMEOUT = 0, 1, 2, 3
+PMWA_ECUDA, PMWA_EINVARIANT, PMWA_EROWS = 4, 5, 6
+
+
+class PmwaError(RuntimeError):
+    def __init__(self, call, status):
+        super().__init__("%s: %s (status %d)" % (call, pmwa_strerror(status), status))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32),
+                ("beta", C.c_double), ("t", C.c_double), ("V", C.c_double),
+                ("mu", C.c_double), ("eta", C.c_double),
+                ("seed", C.c_uint64),
+                ("dom_x", C.c_int32), ("dom_y", C.c_int32),
+                ("exchange_every", C.c_int32), ("n_cycle", C.c_int32),
+                ("sub_block", C.c_int32), ("init", C.c_int32),
+                ("init_seed", C.c_uint64), ("c_off", C.c_double),
+                ("replica", C.c_uint32), ("cap_site", C.c_int32),
+                ("rows_cap", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
+                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("pad", "<f8")])
+
+DEFAULTS = dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1, dom_x=0, dom_y=0,
+                exchange_every=2, n_cycle=8, sub_block=0, init=1, init_seed=1, c_off=-1.0,
+                replica=0, cap_site=0, rows_cap=0)
+
+_lib = None
+
+
+def load(build=True):
+    """Load libpmwa.so (building it with nvcc first if it is stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libpmwa.so not found at %s; run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    P, vp, sz = C.POINTER, C.c_void_p, C.c_size_t
+    sig = {
+        "pmwa_footprint": (sz, [P(Params)]),
+        "pmwa_create": (C.c_int, [P(Params), vp, sz, vp, P(vp)]),
+        "pmwa_sweep": (C.c_int, [vp, C.c_int64]),
+        "pmwa_boundary": (C.c_int, [vp]),
+        "pmwa_tile": (C.c_int, [vp, C.c_int32]),
+        "pmwa_measure": (C.c_int, [vp, vp, C.c_int64, P(C.c_int64)]),
+        "pmwa_rho_slices": (C.c_int, [vp, C.c_int32, vp]),
+        "pmwa_export_bytes": (C.c_int, [vp, P(sz)]),
+        "pmwa_export": (C.c_int, [vp, vp, sz]),
+        "pmwa_import": (C.c_int, [vp, vp, sz]),
+        "pmwa_get_sweep": (C.c_int, [vp, P(C.c_uint64)]),
+        "pmwa_set_sweep": (C.c_int, [vp, C.c_uint64]),
+        "pmwa_destroy": (C.c_int, [vp]),
+        "pmwa_tables": (C.c_int, [P(Params)] + [vp] * 10),
+        "pmwa_strerror": (C.c_char_p, [C.c_int]),
+        "pmwa_profile": (C.c_int, [vp, C.c_int32]),
+        "pmwa_profile_read": (C.c_int, [vp, vp, vp, C.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def make_params(**kw):
+    d = dict(DEFAULTS)
+    unknown = set(kw) - set(d)
+    if unknown:
+        raise TypeError("unknown parameters: %s" % sorted(unknown))
+    d.update(kw)
+    p = Params()
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(call, rc):
+    if rc:
+        raise PmwaError(call, rc)
+
+
+# -- thin wrappers with the C names ------------------------------------------
+def pmwa_strerror(status):
+    return load().pmwa_strerror(status).decode()
+
+
+def pmwa_footprint(p):
+    return load().pmwa_footprint(C.byref(p))
+
+
+def pmwa_create(p, arena_ptr, arena_bytes, stream_ptr):
+    h = C.c_void_p()
+    _check("pmwa_create", load().pmwa_create(C.byref(p), arena_ptr, arena_bytes, stream_ptr, C.byref(h)))
+    return h
+
+
+def pmwa_sweep(h, n):
+    _check("pmwa_sweep", load().pmwa_sweep(h, n))
+
+
+def pmwa_boundary(h):
+    _check("pmwa_boundary", load().pmwa_boundary(h))
+
+
+def pmwa_tile(h, stop_after):
+    _check("pmwa_tile", load().pmwa_tile(h, stop_after))
+
+
+def pmwa_measure(h, max_rows=1 << 20):
+    chunks = []
+    while True:
+        buf = np.zeros(min(max_rows, 65536), dtype=ROW_DTYPE)
+        n = C.c_int64()
+        _check("pmwa_measure", load().pmwa_measure(h, buf.ctypes.data, len(buf), C.byref(n)))
+        chunks.append(buf[: n.value])
+        if n.value < len(buf):
+            break
+    return np.concatenate(chunks)
+
+
+def pmwa_rho_slices(h, N, K):
+    out = np.zeros((N, K), dtype=np.float64)
+    _check("pmwa_rho_slices", load().pmwa_rho_slices(h, K, out.ctypes.data))
+    return out
+
+
+def pmwa_export_bytes(h):
+    n = C.c_size_t()
+    _check("pmwa_export_bytes", load().pmwa_export_bytes(h, C.byref(n)))
+    return n.value
+
+
+def pmwa_export(h):
+    n = pmwa_export_bytes(h)
+    buf = np.zeros(n // 8, dtype=np.uint64)
+    _check("pmwa_export", load().pmwa_export(h, buf.ctypes.data, n))
+    return buf
+
+
+def pmwa_import(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint64)
+    _check("pmwa_import", load().pmwa_import(h, buf.ctypes.data, buf.nbytes))
+
+
+def pmwa_get_sweep(h):
+    s = C.c_uint64()
+    _check("pmwa_get_sweep", load().pmwa_get_sweep(h, C.byref(s)))
+    return s.value
+
+
+def pmwa_set_sweep(h, s):
+    _check("pmwa_set_sweep", load().pmwa_set_sweep(h, s))
+
+
+def pmwa_destroy(h):
+    _check("pmwa_destroy", load().pmwa_destroy(h))
+
+
+KERNELS = ("boundary", "vertex_candidates", "merge_worm_creation", "scatter", "measure", "rho",
+           "sweep")
+
+
+def pmwa_profile(h, enable):
+    _check("pmwa_profile", load().pmwa_profile(h, 1 if enable else 0))
+
+
+def pmwa_profile_read(h):
+    ms = np.zeros(8)
+    n = np.zeros(8, dtype=np.int64)
+    _check("pmwa_profile_read", load().pmwa_profile_read(h, ms.ctypes.data, n.ctypes.data, 8))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+def pmwa_tables(**kw):
+    """Host tables the library derives from the parameters (no GPU needed)."""
+    p = make_params(**kw)
+    d4 = np.zeros(4); D = C.c_double(); tv = np.zeros(4, dtype=np.uint64)
+    th = np.zeros(256, dtype=np.uint64); sv = C.c_double(); sw = C.c_double()
+    zx = np.zeros(257); zf = np.zeros(257); zw = np.zeros(256); zk = np.zeros(256, dtype=np.uint64)
+    _check("pmwa_tables", load().pmwa_tables(C.byref(p), d4.ctypes.data, C.byref(D), tv.ctypes.data,
+                                             th.ctypes.data, C.byref(sv), C.byref(sw), zx.ctypes.data,
+                                             zf.ctypes.data, zw.ctypes.data, zk.ctypes.data))
+    return dict(d=d4, D=D.value, TV=tv, TH=th.reshape(16, 4, 4), SV=sv.value, SW=sw.value,
+                X=zx, F=zf, W=zw, K=zk)
+
+
+class Sim:
+    """One PMWA instance whose configuration lives in a torch-allocated arena."""
+
+    def __init__(self, device="cuda", stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: libpmwa has no CPU path")
+        self.params = make_params(**kw)
+        nbytes = pmwa_footprint(self.params)
+        if nbytes == 0:
+            raise PmwaError("pmwa_footprint", PMWA_EINVAL)
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        self.h = pmwa_create(self.params, self.arena.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.N = self.params.Lx * self.params.Ly
+
+    def close(self):
+        if getattr(self, "h", None):
+            pmwa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        pmwa_sweep(self.h, n)
+
+    def boundary(self):
+        pmwa_boundary(self.h)
+
+    def tile(self, stop_after=6):
+        pmwa_tile(self.h, stop_after)
+
+    def rows(self):
+        return pmwa_measure(self.h)
+
+    def export(self):
+        return pmwa_export(self.h)
+
+    def import_(self, buf):
+        pmwa_import(self.h, buf)
+
+    def rho_slices(self, K):
+        return pmwa_rho_slices(self.h, self.N, K)
+
+    @property
+    def sweep_index(self):
+        return pmwa_get_sweep(self.h)
+
+    @sweep_index.setter
+    def sweep_index(self, s):
+        pmwa_set_sweep(self.h, s)
+
+
+def observables(rows, p):
+    """Physical observables per measured sweep (same definitions as the
+    paper's Step 6): E/N = (N_b C - n_v/beta)/N, density, <Q>/N raw and
+    improved, kinetic <b+_i b_j + h.c.> per bond."""
+    N = p.Lx * p.Ly
+    Nb = 2 * N
+    c_off = 0.5 * p.t if p.c_off < 0 else p.c_off
+    E = [p.V * (s & 1) * (s >> 1) - (p.mu / 4.0) * ((s & 1) + (s >> 1)) for s in range(4)]
+    Cc = max(E) + c_off
+    occ = rows["occ_lo"].astype(np.float64) + rows["occ_hi"].astype(np.float64) * 2.0 ** 64
+    out = dict(E=(Nb * Cc - rows["n_v"].astype(np.float64) / p.beta) / N,
+               n=occ / (2.0 ** 62 * N),
+               Q_raw=rows["n_w"].astype(np.float64) / (p.beta * p.eta * N),
+               Q_impr=rows["q_impr"] / (p.beta * p.eta * N))
+    if p.t > 0:
+        out["kin"] = rows["n_k"].astype(np.float64) / (p.beta * p.t * Nb)
+    return out

@@ -1,0 +1,291 @@
+// pmwa_device.cuh -- device building blocks of the PMWA sweep: counter-based
+// random numbers, deterministic exponentials, the worm-number sampler of
+// Eq. 1, lattice geometry and the per-site event slots.
+//
+// Every floating-point operation that decides an integer (ziggurat wedge
+// test, grid gaps, boundary heat-bath) uses explicit round-to-nearest
+// intrinsics, so no multiply-add is ever contracted and the result is the
+// IEEE binary64 result of the written expression.
+#pragma once
+#include <cstdint>
+
+#include "pmwa_internal.h"
+
+namespace pmwa {
+
+__constant__ double c_zX[257];
+__constant__ double c_zF[257];
+__constant__ double c_zW[256];
+__constant__ unsigned long long c_zK[256];
+__constant__ double c_zR;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
+// mixed into the other two words, key advanced by the Weyl increments.
+struct P4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ P4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return P4{c0, c1, c2, c3};
+}
+
+// Sequence of 64-bit words of the blocks with counter (block, unit, c2, sweep):
+// word w is the low (w even) or high (w odd) half of block w/2.
+struct Stream {
+  uint32_t k0, k1, unit, c2, sweep;
+  uint64_t pos;
+  P4 blk;
+  uint64_t cached;  // block index held in blk, or ~0
+  __device__ void init(uint32_t key0, uint32_t key1, uint32_t u, uint32_t cc2, uint32_t sw) {
+    k0 = key0; k1 = key1; unit = u; c2 = cc2; sweep = sw; pos = 0; cached = ~0ull;
+  }
+  __device__ uint64_t word() {
+    const uint64_t b = pos >> 1;
+    if (b != cached) { blk = philox(uint32_t(b), unit, c2, sweep, k0, k1); cached = b; }
+    const uint64_t w = (pos & 1) ? (uint64_t(blk.z) | (uint64_t(blk.w) << 32))
+                                 : (uint64_t(blk.x) | (uint64_t(blk.y) << 32));
+    ++pos;
+    return w;
+  }
+};
+
+__device__ __forceinline__ uint32_t c2_word(uint32_t phase, uint32_t pass, uint32_t replica) {
+  return phase | (pass << 4) | (replica << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic e^x: x = k ln2 + r with ln2 = LN2_HI (24 significant bits) +
+// LN2_LO, then the Taylor polynomial of e^r to degree 13 (Horner), then the
+// exact power of two.  Coefficients 1/n! are the correctly rounded quotients
+// of exact factorials.
+__device__ __forceinline__ double pow2i(int k) {
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__device__ inline double exp_det(double x) {
+  if (x != x) return x;
+  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  if (x < -745.0) return 0.0;
+  const double kd = floor(__dadd_rn(__dmul_rn(x, 1.4426950408889634), 0.5));
+  const int k = int(kd);
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, 0.693147182464599609375)),
+                             __dmul_rn(kd, -1.9046542999577678e-09));
+  double fact = 1.0;
+  double c[14];
+#pragma unroll
+  for (int n = 0; n <= 13; ++n) {
+    if (n > 0) fact = __dmul_rn(fact, double(n));
+    c[n] = __ddiv_rn(1.0, fact);
+  }
+  double p = c[13];
+#pragma unroll
+  for (int n = 12; n >= 0; --n) p = __dadd_rn(__dmul_rn(p, r), c[n]);
+  if (k >= -1022) return __dmul_rn(p, pow2i(k));
+  return __dmul_rn(__dmul_rn(p, pow2i(k + 600)), pow2i(-600));
+}
+
+// e^x - 1: degree-24 Taylor polynomial (no constant term) on [-1, 1].
+__device__ inline double expm1_det(double x) {
+  if (!(x <= 1.0 && x >= -1.0)) return __dsub_rn(exp_det(x), 1.0);
+  double fact = 1.0;
+  double c[25];
+#pragma unroll
+  for (int n = 1; n <= 24; ++n) { fact = __dmul_rn(fact, double(n)); c[n] = __ddiv_rn(1.0, fact); }
+  double p = c[24];
+#pragma unroll
+  for (int n = 23; n >= 1; --n) p = __dadd_rn(__dmul_rn(p, x), c[n]);
+  return __dmul_rn(p, x);
+}
+
+// x tanh x / x coth x building blocks (x >= 0): with e = e^{-2x} - 1,
+// tanh x = -e / (2 + e) and coth x = (2 + e) / -e.
+__device__ inline double g_sigma(int sigma, double x) {
+  const double e = expm1_det(__dmul_rn(-2.0, x));
+  return sigma ? __ddiv_rn(__dadd_rn(2.0, e), -e) : __ddiv_rn(-e, __dadd_rn(2.0, e));
+}
+
+// ---------------------------------------------------------------------------
+// Unit exponential from the ziggurat of Marsaglia and Tsang (2000): strip i
+// from the low 8 bits of a word, a 53-bit uniform u from its high bits,
+// x = u W[i]; accept when u < K[i]; strip 0 past R restarts at R + new
+// deviate; else a wedge test y < e^-x with a second word.  <= 64 words.
+__device__ inline double zig_exp(Stream& s, int* bad) {
+  double acc = 0.0;
+  for (int tries = 0; tries < 64; ++tries) {
+    const uint64_t w = s.word();
+    const unsigned i = unsigned(w & 255u);
+    const uint64_t u = w >> 11;
+    const double x = __dmul_rn(__ull2double_rn(u), c_zW[i]);
+    if (u < c_zK[i]) return __dadd_rn(acc, x);
+    if (i == 0) { acc = __dadd_rn(acc, c_zR); continue; }
+    const uint64_t w2 = s.word();
+    const double t1 = __dmul_rn(__ull2double_rn(w2 >> 11), 0x1p-53);
+    const double t2 = __dsub_rn(c_zF[i + 1], c_zF[i]);
+    const double y = __dadd_rn(c_zF[i], __dmul_rn(t1, t2));
+    if (y < exp_det(-x)) return __dadd_rn(acc, x);
+  }
+  *bad = PMWA_ETIMEOUT;
+  return 0.0;
+}
+
+// Gap of a Bernoulli process of mean spacing `scale` on an integer grid:
+// 1 + floor(E scale), saturating at 2^62.
+__device__ __forceinline__ uint64_t grid_gap(double E, double scale) {
+  const double g = __dmul_rn(E, scale);
+  if (!(g < 0x1p62)) return kTwo62;
+  return 1 + __double2ull_rz(g);
+}
+
+// Eq. 1 for hard-core bosons: worms on an interval of M worm grid points with
+// parity sigma.  Rate-eta Bernoulli/Poisson process (mean spacing SW grid
+// points) conditioned on the parity of its count; for sigma = 1 and x <= 1
+// (M <= SWI) the proposal is 1 + count, kept with probability 1/n when n is
+// odd, the extra worm uniform on the interval (a clash rejects).  Returns the
+// count (offsets sorted in offs[0..n)), or -1 with *bad set.
+template <int MAXN>
+__device__ int sample_worms(Stream& s, uint64_t M, int sigma, double SW, uint64_t SWI,
+                            uint64_t* offs, int* bad) {
+  if (M == 0) { if (sigma) { *bad = PMWA_EINVARIANT; return -1; } return 0; }
+  for (int tries = 0; tries < 128; ++tries) {
+    int n = 0;
+    bool first = true;
+    uint64_t pos = 0;
+    for (;;) {
+      const double E = zig_exp(s, bad);
+      const uint64_t g = grid_gap(E, SW);
+      const uint64_t nxt = first ? g - 1 : pos + g;
+      first = false;
+      if (nxt >= M) break;
+      pos = nxt;
+      if (n >= MAXN) { *bad = PMWA_ECAPACITY; return -1; }
+      offs[n++] = pos;
+    }
+    if (sigma == 1 && M <= SWI) {
+      const int ntot = n + 1;
+      if ((ntot & 1) == 0) continue;
+      if (__umul64hi(s.word(), uint64_t(ntot)) != 0) continue;
+      const uint64_t extra = __umul64hi(s.word(), M);
+      int at = n;
+      bool clash = false;
+      for (int k = 0; k < n; ++k) {
+        if (offs[k] == extra) { clash = true; break; }
+        if (offs[k] > extra) { at = k; break; }
+      }
+      if (clash) continue;
+      if (n >= MAXN) { *bad = PMWA_ECAPACITY; return -1; }
+      for (int k = n; k > at; --k) offs[k] = offs[k - 1];
+      offs[at] = extra;
+      return ntot;
+    }
+    if ((n & 1) == sigma) return n;
+  }
+  *bad = PMWA_ETIMEOUT;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Event keys.
+__device__ __forceinline__ uint64_t kpk(uint64_t k) { return k >> 2; }
+__device__ __forceinline__ int ktag(uint64_t k) { return int((k >> 2) & 7); }
+__device__ __forceinline__ bool kworm(uint64_t k) { return ((k >> 2) & 7) == 7; }
+__device__ __forceinline__ int kab(uint64_t k) { return int(k & 1); }
+__device__ __forceinline__ int kbl(uint64_t k) { return kworm(k) ? int(1 - (k & 1)) : int((k >> 1) & 1); }
+__device__ __forceinline__ int kdir(uint64_t k) { return int((k >> 1) & 1); }
+__device__ __forceinline__ uint64_t wkey(uint64_t m, int dir, int above) {
+  return (m << 5) | (7ull << 2) | (uint64_t(dir) << 1) | uint64_t(above);
+}
+// worm grid points strictly between pk a and pk b going up from a (b == a:
+// the whole circle); first worm point above / below a vertex point.
+__device__ __forceinline__ uint64_t wpts(uint64_t a, uint64_t b) {
+  const uint64_t hi = (b > a) ? b : b + kTwo62;
+  return (hi >> 3) - ((a + 1) >> 3);
+}
+__device__ __forceinline__ uint64_t wm_above(uint64_t a) { return ((a + 1) >> 3) & (kTwo59 - 1); }
+__device__ __forceinline__ uint64_t wm_below(uint64_t a) { return (((a + 1) >> 3) + kTwo59 - 1) & (kTwo59 - 1); }
+
+// ---------------------------------------------------------------------------
+// Lattice geometry: site i = x + Lx y, bond 2a + d from a to a + x^ / a + y^;
+// tag of a bond 3d + cls(c), cls(c) = 2 if c = L-1 else c & 1 (c the
+// coordinate of a along d): distinct for the four bonds of a site.
+__device__ __forceinline__ int clsf(int c, int L) { return (c == L - 1) ? 2 : (c & 1); }
+__device__ __forceinline__ int site_step(const Dev& d, int s, int dir, int sgn) {
+  int x = s % d.Lx, y = s / d.Lx;
+  if (dir == 0) x = (x + sgn + d.Lx) % d.Lx; else y = (y + sgn + d.Ly) % d.Ly;
+  return x + d.Lx * y;
+}
+__device__ __forceinline__ int bond_tag(const Dev& d, int a, int dir) {
+  return dir ? 3 + clsf(a / d.Lx, d.Ly) : clsf(a % d.Lx, d.Lx);
+}
+// lower site and direction of the bond of a vertex leg with tag t on site s
+__device__ __forceinline__ int leg_lower(const Dev& d, int s, int t, int* dir) {
+  const int dd = t / 3, cl = t % 3;
+  const int c = dd ? s / d.Lx : s % d.Lx, L = dd ? d.Ly : d.Lx;
+  *dir = dd;
+  return (cl == clsf(c, L)) ? s : site_step(d, s, dd, -1);
+}
+__device__ __forceinline__ bool boundary_bond(const Dev& d, int a, int dir) {
+  if (dir == 0) return d.ndx > 1 && ((a % d.Lx) + 1) % d.dom_x == 0;
+  return d.ndy > 1 && ((a / d.Lx) + 1) % d.dom_y == 0;
+}
+__device__ __forceinline__ int dom_of(const Dev& d, int s) {
+  return (s % d.Lx) / d.dom_x + d.ndx * ((s / d.Lx) / d.dom_y);
+}
+
+// Step-5 sub-blocks: blocks of B sites at offset 0 or B/2 per axis (periodic
+// when one domain spans the axis, clipped at domain edges otherwise).
+__device__ __forceinline__ int sb_axis(int c, int D, int B, int nd, int off) {
+  if (B == 0 || B >= D) return 0;
+  if (nd == 1) return ((c - off + D) % D) / B;
+  return (c - off + B) / B;
+}
+__device__ __forceinline__ int sb_slots(int D, int B, int nd) {
+  if (B == 0 || B >= D) return 1;
+  return (nd == 1) ? D / B : D / B + 1;
+}
+__device__ __forceinline__ int sb_local(const Dev& d, int s, int pass) {
+  const int B = d.sub_block;
+  const int ox = (B && B < d.dom_x) ? (pass & 1) * (B / 2) : 0;
+  const int oy = (B && B < d.dom_y) ? ((pass >> 1) & 1) * (B / 2) : 0;
+  const int bx = sb_axis((s % d.Lx) % d.dom_x, d.dom_x, B, d.ndx, ox);
+  const int by = sb_axis((s / d.Lx) % d.dom_y, d.dom_y, B, d.ndy, oy);
+  return bx + sb_slots(d.dom_x, B, d.ndx) * by;
+}
+
+// ---------------------------------------------------------------------------
+// Per-site event slots: keys sorted by pk in key[s*cap .. s*cap + n).
+struct Slot {
+  uint64_t* k;
+  int n;
+};
+__device__ __forceinline__ int slot_lower(const uint64_t* k, int n, uint64_t p) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (kpk(k[mid]) < p) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int slot_find(const uint64_t* k, int n, uint64_t p) {
+  const int i = slot_lower(k, n, p);
+  return (i < n && kpk(k[i]) == p) ? i : -1;
+}
+// occupation just before time point p (cyclic); base when the slot is empty
+__device__ __forceinline__ int slot_state(const uint64_t* k, int n, int base, uint64_t p) {
+  if (n == 0) return base;
+  const int i = slot_lower(k, n, p);
+  return kab(k[(i == 0) ? n - 1 : i - 1]);
+}
+
+__device__ __forceinline__ void set_err(DevErr* e, int code, int where) {
+  if (atomicCAS(&e->code, 0, code) == 0) e->where = where;
+}
+
+}  // namespace pmwa

@@ -1,0 +1,612 @@
+// pmwa_host.cpp -- host side of libpmwa.so: parameter checks, the tables of
+// the deterministic arithmetic, the device arena, and the sweep driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pmwa_internal.h"
+
+using namespace pmwa;
+
+constexpr int kKernels = 7;  // 6 = whole sweep span
+
+struct Timed {
+  int kernel;
+  cudaEvent_t start, stop;
+};
+
+struct pmwa_handle {
+  pmwa_params p;
+  Dev d;
+  cudaStream_t stream;
+  uint64_t sweep;
+  int rows_cap;
+  int rows_pending;
+  uint64_t TH[256];
+  DevErr* err;
+  bool profiling = false;
+  std::vector<Timed> timed;            // events of launches not yet read
+  std::vector<cudaEvent_t> event_pool;  // spare events
+};
+
+namespace {
+
+struct Derived {
+  int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap;
+  double d[4], D, tkink, SV, SW, XW;
+  uint64_t TV[4], SWI;
+  uint64_t TH[256];
+};
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+int validate(const pmwa_params* p) {
+  if (!p) return PMWA_EINVAL;
+  if (p->Lx < 2 || p->Ly < 2 || p->Lx > 65536 || p->Ly > 65536) return PMWA_EINVAL;
+  if ((long long)p->Lx * p->Ly > (1LL << 30)) return PMWA_EINVAL;
+  if (!(p->beta > 0.0) || !(p->eta > 0.0) || !(p->t >= 0.0)) return PMWA_EINVAL;
+  if (!std::isfinite(p->beta) || !std::isfinite(p->eta) || !std::isfinite(p->t) ||
+      !std::isfinite(p->V) || !std::isfinite(p->mu))
+    return PMWA_EINVAL;
+  const int dx = p->dom_x ? p->dom_x : p->Lx, dy = p->dom_y ? p->dom_y : p->Ly;
+  if (dx < 1 || dy < 1 || p->Lx % dx || p->Ly % dy) return PMWA_EINVAL;
+  if (p->Lx / dx > 1 && dx < 2) return PMWA_EINVAL;
+  if (p->Ly / dy > 1 && dy < 2) return PMWA_EINVAL;
+  if (p->exchange_every < 1 || p->n_cycle < 0 || p->n_cycle > 4095) return PMWA_EINVAL;
+  const int B = p->sub_block;
+  if (B < 0 || (B & 1)) return PMWA_EINVAL;
+  if (B && B < dx && dx % B) return PMWA_EINVAL;
+  if (B && B < dy && dy % B) return PMWA_EINVAL;
+  if (p->replica >= 65536u || p->init < 0 || p->init > 1) return PMWA_EINVAL;
+  if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
+  for (int k = 0; k < 5; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  return PMWA_OK;
+}
+
+// Weight of a vertex with root states S (bit l = state at the root of leg l:
+// 0 = lower site below, 1 = upper site below, 2 = lower site above,
+// 3 = upper site above): 0 unless particles are conserved; d(s) when the
+// states do not change (diagonal), t for a kink.
+double weight_of(const Derived& g, int S) {
+  const int s0 = S & 1, s1 = (S >> 1) & 1, s2 = (S >> 2) & 1, s3 = (S >> 3) & 1;
+  if (s0 + s1 != s2 + s3) return 0.0;
+  return (s0 == s2) ? g.d[s0 | (s1 << 1)] : g.tkink;
+}
+
+// Directed loops with minimal bounce for a family with leg weights w[4]:
+// with the positive weights sorted a >= b >= c (absent ones are 0),
+// a <= b + c gives the bounce-free symmetric solution
+//   w_ab = (a+b-c)/2, w_ac = (a+c-b)/2, w_bc = (b+c-a)/2,
+// and a > b + c the one with a bounce on the largest leg
+//   w_aa = a-b-c, w_ab = b, w_ac = c.
+void solve_family(const double w[4], double out[4][4]) {
+  int idx[4] = {0, 1, 2, 3};
+  std::stable_sort(idx, idx + 4, [&](int x, int y) { return w[x] > w[y]; });
+  for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) out[i][j] = 0.0;
+  const int A = idx[0], Bi = idx[1], Ci = idx[2];
+  const double a = w[A], b = w[Bi], c = w[Ci];
+  if (a <= b + c) {
+    out[A][Bi] = out[Bi][A] = ((a + b) - c) / 2.0;
+    out[A][Ci] = out[Ci][A] = ((a + c) - b) / 2.0;
+    out[Bi][Ci] = out[Ci][Bi] = ((b + c) - a) / 2.0;
+  } else {
+    out[A][A] = (a - b) - c;
+    out[A][Bi] = out[Bi][A] = b;
+    out[A][Ci] = out[Ci][A] = c;
+  }
+}
+
+void derive(const pmwa_params* p, Derived* g) {
+  g->dom_x = p->dom_x ? p->dom_x : p->Lx;
+  g->dom_y = p->dom_y ? p->dom_y : p->Ly;
+  g->N = p->Lx * p->Ly;
+  g->ndx = p->Lx / g->dom_x;
+  g->ndy = p->Ly / g->dom_y;
+  g->ndom = g->ndx * g->ndy;
+  const double c_off = (p->c_off < 0.0) ? 0.5 * p->t : p->c_off;
+  // Eq. 5 per bond: E(na, nb) = V na nb - (mu/4)(na + nb)
+  double E[4], Emax = -INFINITY;
+  for (int s = 0; s < 4; ++s) {
+    const int na = s & 1, nb = s >> 1;
+    E[s] = p->V * (double)(na * nb) - (p->mu / 4.0) * (double)(na + nb);
+    Emax = std::max(Emax, E[s]);
+  }
+  const double C = Emax + c_off;
+  g->D = 0.0;
+  for (int s = 0; s < 4; ++s) { g->d[s] = C - E[s]; g->D = std::max(g->D, g->d[s]); }
+  for (int s = 0; s < 4; ++s)
+    g->TV[s] = (g->d[s] == g->D) ? kTwo32 : (uint64_t)std::floor(g->d[s] / g->D * 0x1p32);
+  g->tkink = p->t;
+  g->SV = (g->D > 0.0) ? 0x1p59 / (p->beta * g->D) : INFINITY;
+  g->SW = 0x1p59 / (p->beta * p->eta);
+  g->SWI = (g->SW >= 0x1p62) ? kTwo62 : (uint64_t)g->SW;
+  g->XW = (p->beta * p->eta) * 0x1p-59;
+  for (int S = 0; S < 16; ++S)
+    for (int i = 0; i < 4; ++i) {
+      uint64_t* th = g->TH + (S * 4 + i) * 4;
+      for (int j = 0; j < 4; ++j) th[j] = kTwo32;
+      const double wi = weight_of(*g, S);
+      if (wi <= 0.0) continue;
+      const int T = S ^ (1 << i);  // worm inside the vertex
+      double w[4], m[4][4];
+      for (int l = 0; l < 4; ++l) w[l] = weight_of(*g, T ^ (1 << l));
+      solve_family(w, m);
+      int last = 0;
+      for (int j = 0; j < 4; ++j) if (m[i][j] > 0.0) last = j;
+      double cum = 0.0;
+      for (int j = 0; j < 4; ++j) {
+        cum = cum + m[i][j] / wi;
+        th[j] = (j >= last) ? kTwo32 : (uint64_t)std::floor(cum * 0x1p32);
+      }
+    }
+  // capacities: expected events per site ~ 4 bonds x beta (D + t) + worms
+  const double mean = 4.0 * p->beta * (g->D + p->t) + 2.0 * p->beta * p->eta;
+  int cap = p->cap_site ? p->cap_site : int(mean + 8.0 * std::sqrt(mean) + 24.0);
+  g->cap = (cap + 7) & ~7;
+  const double mb = p->beta * g->D;
+  g->capb = (int(mb + 8.0 * std::sqrt(mb) + 16.0) + 7) & ~7;
+  const int nds = g->dom_x * g->dom_y;
+  const int nsub = sb_slots_host(g->dom_x, p->sub_block, g->ndx) * sb_slots_host(g->dom_y, p->sub_block, g->ndy);
+  const long long room = (200LL * 1024 - 2048 - 8LL * (nsub + 4)) / 24;
+  g->wcap = int(std::min<long long>(8LL * nds + 64, room));
+}
+
+struct Layout {
+  size_t err, TH, rows, cntA, cntB, keyA, keyB, lab, tmp, ccnt, cand, total;
+};
+
+Layout layout(const pmwa_params* p, const Derived& g) {
+  Layout L;
+  size_t o = 0;
+  const size_t N = size_t(g.N), cap = size_t(g.cap);
+  const int rows_cap = p->rows_cap ? p->rows_cap : 4096;
+  L.err = o; o = align_up(o + sizeof(DevErr));
+  L.TH = o; o = align_up(o + 256 * sizeof(uint64_t));
+  L.rows = o; o = align_up(o + size_t(rows_cap) * sizeof(pmwa_row));
+  L.cntA = o; o = align_up(o + N * sizeof(uint32_t));
+  L.cntB = o; o = align_up(o + N * sizeof(uint32_t));
+  L.keyA = o; o = align_up(o + N * cap * sizeof(uint64_t));
+  L.keyB = o; o = align_up(o + N * cap * sizeof(uint64_t));
+  L.lab = o; o = align_up(o + N * cap * sizeof(uint64_t));
+  L.tmp = o; o = align_up(o + N * cap * sizeof(uint64_t));
+  L.ccnt = o; o = align_up(o + 2 * N * sizeof(uint32_t));
+  L.cand = o; o = align_up(o + 2 * N * size_t(g.capb) * sizeof(uint64_t));
+  L.total = o;
+  return L;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PMWA_OK : PMWA_ECUDA; }
+
+// read and clear the device error word (synchronises the stream)
+int drain_error(pmwa_handle* h) {
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PMWA_ECUDA;
+  DevErr e;
+  if (cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) return PMWA_ECUDA;
+  if (e.code) {
+    DevErr z{0, 0};
+    cudaMemcpy(h->err, &z, sizeof z, cudaMemcpyHostToDevice);
+    return e.code;
+  }
+  return PMWA_OK;
+}
+
+cudaEvent_t take_event(pmwa_handle* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// launch `fn` on the handle's stream, bracketed by events when profiling
+template <class F>
+int timed_launch(pmwa_handle* h, int kernel, F fn) {
+  if (!h->profiling) return fn();
+  Timed t{kernel, take_event(h), take_event(h)};
+  cudaEventRecord(t.start, h->stream);
+  const int e = fn();
+  cudaEventRecord(t.stop, h->stream);
+  h->timed.push_back(t);
+  return e;
+}
+
+void swap_buffers(Dev& d) {
+  std::swap(d.keyA, d.keyB);
+  std::swap(d.cntA, d.cntB);
+}
+
+// Steps 3..stop of one sweep on the current configuration (A -> B, swap).
+int run_tile(pmwa_handle* h, int stop, bool record) {
+  Dev& d = h->d;
+  d.sweep = uint32_t(h->sweep);
+  cudaStream_t st = h->stream;
+  if (timed_launch(h, 1, [&] { return launch_step3(d, st); })) return PMWA_ECUDA;
+  if (timed_launch(h, 2, [&] { return launch_step34_sites(d, stop >= 4 ? 1 : 0, st); })) return PMWA_ECUDA;
+  if (stop >= 5 && d.n_cycle > 0 && timed_launch(h, 3, [&] { return launch_step5(d, st); })) return PMWA_ECUDA;
+  if (stop >= 6 && record) {
+    d.row = h->rows_pending;
+    if (cudaMemsetAsync(d.rows + d.row, 0, sizeof(pmwa_row), st)) return PMWA_ECUDA;
+    if (timed_launch(h, 4, [&] { return launch_measure(d, st); })) return PMWA_ECUDA;
+    h->rows_pending++;
+  }
+  swap_buffers(d);
+  return PMWA_OK;
+}
+
+}  // namespace
+
+namespace pmwa {
+
+// Ziggurat of Marsaglia and Tsang for e^-x with 256 strips of area v: the
+// rightmost edge R is bisected in [7, 8] until the strips, stacked from
+// (R, e^-R) upward with F[i+1] = F[i] + v / X[i], X = -ln F, close with a top
+// strip of area v.
+static int lay_strips(double R, Zig* z) {
+  const double v = (R + 1.0) * std::exp(-R);
+  double X[257], F[257];
+  X[1] = R;
+  F[1] = std::exp(-R);
+  for (int i = 1; i < 255; ++i) {
+    F[i + 1] = F[i] + v / X[i];
+    if (!(F[i + 1] < 1.0)) return -1;
+    X[i + 1] = -std::log(F[i + 1]);
+  }
+  if (X[255] * (1.0 - F[255]) < v) return -1;
+  if (z) {
+    z->R = R;
+    z->v = v;
+    X[0] = v / F[1];
+    F[0] = 0.0;
+    X[256] = 0.0;
+    F[256] = 1.0;
+    std::memcpy(z->X, X, sizeof X);
+    std::memcpy(z->F, F, sizeof F);
+    for (int i = 0; i < 256; ++i) {
+      z->K[i] = (uint64_t)std::floor(X[i + 1] / X[i] * 0x1p53);
+      z->W[i] = X[i] * 0x1p-53;
+    }
+  }
+  return 1;
+}
+
+void build_zig(Zig* z) {
+  double lo = 7.0, hi = 8.0;
+  while (true) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    (lay_strips(mid, nullptr) < 0 ? lo : hi) = mid;
+  }
+  lay_strips(hi, z);
+}
+
+}  // namespace pmwa
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* pmwa_strerror(int s) {
+  switch (s) {
+    case PMWA_OK: return "ok";
+    case PMWA_EINVAL: return "invalid argument";
+    case PMWA_ECAPACITY: return "capacity exceeded";
+    case PMWA_ETIMEOUT: return "bounded device loop reached its cap";
+    case PMWA_ECUDA: return "CUDA runtime error";
+    case PMWA_EINVARIANT: return "configuration invariant broken";
+    case PMWA_EROWS: return "measurement row buffer full";
+    default: return "unknown status";
+  }
+}
+
+size_t pmwa_footprint(const pmwa_params* p) {
+  if (validate(p)) return 0;
+  Derived g;
+  derive(p, &g);
+  return layout(p, g).total;
+}
+
+int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4, uint64_t* th256,
+                double* sv, double* sw, double* zig_x, double* zig_f, double* zig_w,
+                uint64_t* zig_k) {
+  if (validate(p)) return PMWA_EINVAL;
+  Derived g;
+  derive(p, &g);
+  if (d4) std::memcpy(d4, g.d, sizeof g.d);
+  if (D) *D = g.D;
+  if (tv4) std::memcpy(tv4, g.TV, sizeof g.TV);
+  if (th256) std::memcpy(th256, g.TH, sizeof g.TH);
+  if (sv) *sv = g.SV;
+  if (sw) *sw = g.SW;
+  if (zig_x || zig_f || zig_w || zig_k) {
+    Zig z;
+    build_zig(&z);
+    if (zig_x) std::memcpy(zig_x, z.X, sizeof z.X);
+    if (zig_f) std::memcpy(zig_f, z.F, sizeof z.F);
+    if (zig_w) std::memcpy(zig_w, z.W, sizeof z.W);
+    if (zig_k) std::memcpy(zig_k, z.K, sizeof z.K);
+  }
+  return PMWA_OK;
+}
+
+int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, pmwa_handle** out) {
+  if (!out) return PMWA_EINVAL;
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  Derived g;
+  derive(p, &g);
+  if (g.wcap < 64) return PMWA_EINVAL;  // domain too large for the Step-5 table
+  const Layout L = layout(p, g);
+  if (!arena || bytes < L.total || (reinterpret_cast<uintptr_t>(arena) & (kAlign - 1))) return PMWA_EINVAL;
+  static bool zig_ready = false;
+  {
+    Zig z;
+    build_zig(&z);
+    if (upload_zig(z)) return PMWA_ECUDA;
+    zig_ready = true;
+  }
+  pmwa_handle* h = new (std::nothrow) pmwa_handle();
+  if (!h) return PMWA_EINVAL;
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->sweep = 0;
+  h->rows_cap = p->rows_cap ? p->rows_cap : 4096;
+  h->rows_pending = 0;
+  std::memcpy(h->TH, g.TH, sizeof g.TH);
+  char* base = static_cast<char*>(arena);
+  Dev& d = h->d;
+  std::memset(&d, 0, sizeof d);
+  d.Lx = p->Lx; d.Ly = p->Ly; d.N = g.N;
+  d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy; d.ndom = g.ndom;
+  d.sub_block = p->sub_block; d.n_cycle = p->n_cycle;
+  d.cap = g.cap; d.capb = g.capb; d.wcap = g.wcap;
+  d.key0 = uint32_t(p->seed); d.key1 = uint32_t(p->seed >> 32); d.replica = p->replica;
+  d.beta = p->beta; d.eta = p->eta; d.SV = g.SV; d.SW = g.SW; d.XW = g.XW; d.SWI = g.SWI;
+  d.has_vertices = g.D > 0.0 ? 1 : 0;
+  for (int s = 0; s < 4; ++s) { d.TV[s] = g.TV[s]; d.dvw[s] = g.d[s]; }
+  d.tkink = g.tkink;
+  d.err = reinterpret_cast<DevErr*>(base + L.err);
+  d.TH = reinterpret_cast<const uint64_t*>(base + L.TH);
+  d.rows = reinterpret_cast<pmwa_row*>(base + L.rows);
+  d.cntA = reinterpret_cast<uint32_t*>(base + L.cntA);
+  d.cntB = reinterpret_cast<uint32_t*>(base + L.cntB);
+  d.keyA = reinterpret_cast<uint64_t*>(base + L.keyA);
+  d.keyB = reinterpret_cast<uint64_t*>(base + L.keyB);
+  d.lab = reinterpret_cast<uint64_t*>(base + L.lab);
+  d.tmp = reinterpret_cast<uint64_t*>(base + L.tmp);
+  d.ccnt = reinterpret_cast<uint32_t*>(base + L.ccnt);
+  d.cand = reinterpret_cast<uint64_t*>(base + L.cand);
+  h->err = d.err;
+  // initial configuration: no events; floor(N/2) occupied sites from a
+  // Fisher-Yates permutation of the stream (init_seed, unit 0, init phase)
+  std::vector<uint32_t> cnt(size_t(g.N), 0u);
+  if (p->init == 1) {
+    std::vector<int> perm(size_t(g.N));
+    for (int k = 0; k < g.N; ++k) perm[size_t(k)] = k;
+    const uint32_t k0 = uint32_t(p->init_seed), k1 = uint32_t(p->init_seed >> 32);
+    const uint32_t c2 = kInit | (p->replica << 16);
+    uint64_t pos = 0;
+    for (int k = g.N - 1; k >= 1; --k, ++pos) {
+      // word `pos` of the stream: Philox block pos/2, half pos&1
+      uint32_t c0 = uint32_t(pos >> 1), c1 = 0, cc2 = c2, c3 = 0, a0 = k0, a1 = k1;
+      for (int r = 0; r < 10; ++r) {
+        const uint64_t m0 = uint64_t(0xD2511F53u) * c0, m1 = uint64_t(0xCD9E8D57u) * cc2;
+        const uint32_t n0 = uint32_t(m1 >> 32) ^ c1 ^ a0, n2 = uint32_t(m0 >> 32) ^ c3 ^ a1;
+        c0 = n0; c1 = uint32_t(m1); cc2 = n2; c3 = uint32_t(m0);
+        a0 += 0x9E3779B9u; a1 += 0xBB67AE85u;
+      }
+      const uint64_t w = (pos & 1) ? (uint64_t(cc2) | (uint64_t(c3) << 32)) : (uint64_t(c0) | (uint64_t(c1) << 32));
+      const int j = int((unsigned __int128)w * uint64_t(k + 1) >> 64);
+      std::swap(perm[size_t(k)], perm[size_t(j)]);
+    }
+    for (int k = 0; k < g.N / 2; ++k) cnt[size_t(perm[size_t(k)])] = 1u << 31;
+  }
+  DevErr z{0, 0};
+  if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(const_cast<uint64_t*>(d.TH), g.TH, sizeof g.TH, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) {
+    delete h;
+    return PMWA_ECUDA;
+  }
+  (void)zig_ready;
+  *out = h;
+  return PMWA_OK;
+}
+
+int pmwa_destroy(pmwa_handle* h) {
+  if (!h) return PMWA_OK;
+  cudaStreamSynchronize(h->stream);
+  for (const Timed& t : h->timed) { cudaEventDestroy(t.start); cudaEventDestroy(t.stop); }
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  delete h;
+  return PMWA_OK;
+}
+
+int pmwa_profile(pmwa_handle* h, int32_t enable) {
+  if (!h) return PMWA_EINVAL;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  for (const Timed& t : h->timed) { h->event_pool.push_back(t.start); h->event_pool.push_back(t.stop); }
+  h->timed.clear();
+  h->profiling = enable != 0;
+  return PMWA_OK;
+}
+
+int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n) {
+  if (!h || !ms || !launches || n < kKernels) return PMWA_EINVAL;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  for (int k = 0; k < n; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  for (const Timed& t : h->timed) {
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, t.start, t.stop)) return PMWA_ECUDA;
+    ms[t.kernel] += e;
+    launches[t.kernel] += 1;
+    h->event_pool.push_back(t.start);
+    h->event_pool.push_back(t.stop);
+  }
+  h->timed.clear();
+  return PMWA_OK;
+}
+
+int pmwa_sweep(pmwa_handle* h, int64_t n) {
+  if (!h || n < 0) return PMWA_EINVAL;
+  if (h->rows_pending + n > h->rows_cap) return PMWA_EROWS;
+  const bool multi = h->d.ndom > 1;
+  for (int64_t k = 0; k < n; ++k) {
+    Timed span{6, nullptr, nullptr};
+    if (h->profiling) {
+      span.start = take_event(h);
+      span.stop = take_event(h);
+      cudaEventRecord(span.start, h->stream);
+    }
+    if (multi && h->sweep % uint64_t(h->p.exchange_every) == 0) {
+      h->d.sweep = uint32_t(h->sweep);
+      const Dev& d = h->d;
+      cudaStream_t st = h->stream;
+      if (d.ndx > 1 && timed_launch(h, 0, [&] { return launch_boundary(d, 0, st); })) return PMWA_ECUDA;
+      if (d.ndy > 1 && timed_launch(h, 0, [&] { return launch_boundary(d, 1, st); })) return PMWA_ECUDA;
+    }
+    const int rc = run_tile(h, 6, true);
+    if (rc) return rc;
+    if (h->profiling) {
+      cudaEventRecord(span.stop, h->stream);
+      h->timed.push_back(span);
+    }
+    h->sweep++;
+  }
+  return drain_error(h);
+}
+
+int pmwa_boundary(pmwa_handle* h) {
+  if (!h) return PMWA_EINVAL;
+  h->d.sweep = uint32_t(h->sweep);
+  if (launch_boundary(h->d, 0, h->stream) || launch_boundary(h->d, 1, h->stream)) return PMWA_ECUDA;
+  return drain_error(h);
+}
+
+int pmwa_tile(pmwa_handle* h, int32_t stop) {
+  if (!h || stop < 3 || stop > 6) return PMWA_EINVAL;
+  if (stop == 6 && h->rows_pending + 1 > h->rows_cap) return PMWA_EROWS;
+  const int rc = run_tile(h, stop, true);
+  if (rc) return rc;
+  return drain_error(h);
+}
+
+int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_rows) {
+  if (!h || !n_rows || max_rows < 0 || (!rows && max_rows)) return PMWA_EINVAL;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  const int n = int(std::min<int64_t>(max_rows, h->rows_pending));
+  if (n && cudaMemcpy(rows, h->d.rows, size_t(n) * sizeof(pmwa_row), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
+  const int rest = h->rows_pending - n;
+  if (rest > 0) {
+    std::vector<pmwa_row> tail(static_cast<size_t>(rest));
+    if (cudaMemcpy(tail.data(), h->d.rows + n, size_t(rest) * sizeof(pmwa_row), cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(h->d.rows, tail.data(), size_t(rest) * sizeof(pmwa_row), cudaMemcpyHostToDevice))
+      return PMWA_ECUDA;
+  }
+  h->rows_pending = rest;
+  *n_rows = n;
+  return PMWA_OK;
+}
+
+int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
+  if (!h || K < 1 || !host_out) return PMWA_EINVAL;
+  if (size_t(K) > size_t(h->d.cap)) return PMWA_EINVAL;  // scratch is the tmp slots
+  double* dev = reinterpret_cast<double*>(h->d.tmp);
+  if (launch_rho(h->d, K, dev, h->stream)) return PMWA_ECUDA;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  if (cudaMemcpy(host_out, dev, size_t(h->d.N) * size_t(K) * sizeof(double), cudaMemcpyDeviceToHost))
+    return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+int pmwa_get_sweep(pmwa_handle* h, uint64_t* s) {
+  if (!h || !s) return PMWA_EINVAL;
+  *s = h->sweep;
+  return PMWA_OK;
+}
+
+int pmwa_set_sweep(pmwa_handle* h, uint64_t s) {
+  if (!h) return PMWA_EINVAL;
+  h->sweep = s;
+  return PMWA_OK;
+}
+
+int pmwa_export_bytes(pmwa_handle* h, size_t* bytes) {
+  if (!h || !bytes) return PMWA_EINVAL;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  std::vector<uint32_t> cnt(size_t(h->d.N));
+  if (cudaMemcpy(cnt.data(), h->d.cntA, cnt.size() * 4, cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
+  size_t n = 1 + cnt.size();
+  for (uint32_t c : cnt) n += c & 0x7fffffffu;
+  *bytes = n * sizeof(uint64_t);
+  return PMWA_OK;
+}
+
+int pmwa_export(pmwa_handle* h, void* buf, size_t bytes) {
+  size_t need = 0;
+  int rc = pmwa_export_bytes(h, &need);
+  if (rc) return rc;
+  if (!buf || bytes < need) return PMWA_EINVAL;
+  const size_t N = size_t(h->d.N), cap = size_t(h->d.cap);
+  std::vector<uint32_t> cnt(N);
+  std::vector<uint64_t> keys(N * cap);
+  if (cudaMemcpy(cnt.data(), h->d.cntA, N * 4, cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(keys.data(), h->d.keyA, N * cap * 8, cudaMemcpyDeviceToHost))
+    return PMWA_ECUDA;
+  uint64_t* o = static_cast<uint64_t*>(buf);
+  size_t k = 0;
+  o[k++] = N;
+  for (size_t s = 0; s < N; ++s) {
+    const size_t n = cnt[s] & 0x7fffffffu;
+    o[k++] = uint64_t(n) | (uint64_t(cnt[s] >> 31) << 63);
+    std::memcpy(o + k, keys.data() + s * cap, n * 8);
+    k += n;
+  }
+  return PMWA_OK;
+}
+
+int pmwa_import(pmwa_handle* h, const void* buf, size_t bytes) {
+  if (!h || !buf) return PMWA_EINVAL;
+  const uint64_t* in = static_cast<const uint64_t*>(buf);
+  const size_t nw = bytes / 8, N = size_t(h->d.N), cap = size_t(h->d.cap);
+  if (nw < 1 || in[0] != N) return PMWA_EINVAL;
+  std::vector<uint32_t> cnt(N);
+  std::vector<uint64_t> keys(N * cap, 0);
+  size_t k = 1;
+  for (size_t s = 0; s < N; ++s) {
+    if (k >= nw) return PMWA_EINVAL;
+    const uint64_t hd = in[k++];
+    const size_t n = size_t(hd & 0x7fffffffu);
+    if (n > cap) return PMWA_ECAPACITY;
+    if (k + n > nw) return PMWA_EINVAL;
+    for (size_t j = 0; j < n; ++j) {
+      const uint64_t key = in[k + j];
+      if (((key >> 2) & 7) == 6) return PMWA_EINVARIANT;
+      if (j && (in[k + j - 1] >> 2) >= (key >> 2)) return PMWA_EINVARIANT;
+      // continuity: state above each event = state below the next one
+      const uint64_t nx = in[k + (j + 1) % n];
+      const int above = int(key & 1);
+      const int below_next = (((nx >> 2) & 7) == 7) ? int(1 - (nx & 1)) : int((nx >> 1) & 1);
+      if (above != below_next) return PMWA_EINVARIANT;
+    }
+    if (n && int(hd >> 63) != int(in[k + n - 1] & 1)) return PMWA_EINVARIANT;
+    std::memcpy(keys.data() + s * cap, in + k, n * 8);
+    cnt[s] = uint32_t(n) | (uint32_t(hd >> 63) << 31);
+    k += n;
+  }
+  if (cudaStreamSynchronize(h->stream) ||
+      cudaMemcpy(h->d.cntA, cnt.data(), N * 4, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(h->d.keyA, keys.data(), N * cap * 8, cudaMemcpyHostToDevice))
+    return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+}  // extern "C"

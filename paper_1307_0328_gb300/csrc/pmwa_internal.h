@@ -1,0 +1,80 @@
+// pmwa_internal.h -- state shared by the host side (pmwa_host.cpp) and the
+// CUDA kernels (pmwa_kernels.cu) of libpmwa.so.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pmwa.h"
+
+namespace pmwa {
+
+constexpr uint64_t kTwo59 = uint64_t(1) << 59;
+constexpr uint64_t kTwo62 = uint64_t(1) << 62;
+constexpr uint64_t kTwo32 = uint64_t(1) << 32;
+
+// Philox counter word c2 = phase | pass << 4 | replica << 16.
+enum Phase : uint32_t { kInit = 1, kBx = 2, kBy = 3, kVertex = 4, kRegen = 5, kScatter = 6 };
+
+// Error word layout on the device: first error code wins (atomicCAS).
+struct DevErr {
+  int code;
+  int where;
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  // geometry
+  int Lx, Ly, N, dom_x, dom_y, ndx, ndy, ndom;
+  int sub_block, n_cycle;
+  int cap;      // events per site slot
+  int capb;     // candidate vertices per bond slot
+  int wcap;     // worms per domain in the Step-5 table
+  // random numbers
+  uint32_t key0, key1, replica, sweep;
+  // model
+  double beta, eta, SV, SW, XW;
+  uint64_t SWI;
+  int has_vertices;
+  uint64_t TV[4];
+  double dvw[4];    // diagonal vertex weights d(s), s = na | nb << 1
+  double tkink;     // kink weight t
+  // buffers
+  uint64_t* keyA;   // current configuration: N slots of cap keys
+  uint32_t* cntA;   // count | base << 31
+  uint64_t* keyB;   // next configuration
+  uint32_t* cntB;
+  uint64_t* lab;    // worm labels, parallel to keyB
+  uint64_t* tmp;    // per-site scratch slot (vertex legs of Step 3)
+  uint64_t* cand;   // per-bond candidate vertices of Step 3
+  uint32_t* ccnt;
+  const uint64_t* TH;  // 16*4*4 directed-loop thresholds
+  DevErr* err;
+  pmwa_row* rows;
+  int row;
+};
+
+// Exponential ziggurat tables, built on the host (pmwa_host.cpp).
+struct Zig {
+  double X[257], F[257], W[256];
+  uint64_t K[256];
+  double R, v;
+};
+void build_zig(Zig* z);
+
+// Kernel launchers (pmwa_kernels.cu).  All return a cudaError_t as int.
+int upload_zig(const Zig& z);
+int launch_boundary(const Dev& d, int dir, void* stream);
+int launch_step3(const Dev& d, void* stream);
+int launch_step34_sites(const Dev& d, int regen, void* stream);
+int launch_step5(const Dev& d, void* stream);
+int launch_measure(const Dev& d, void* stream);
+int launch_rho(const Dev& d, int K, double* out, void* stream);
+size_t step5_smem(const Dev& d);
+
+// Step-5 sub-block count along one axis (host copy of the device rule).
+inline int sb_slots_host(int D, int B, int nd) {
+  if (B == 0 || B >= D) return 1;
+  return (nd == 1) ? D / B : D / B + 1;
+}
+
+}  // namespace pmwa

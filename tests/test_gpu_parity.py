@@ -1,0 +1,129 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, bit for bit in configuration and integer counters, FP64
+estimators within 1e-12 relative (summation order differs).
+
+Each step of the paper's pseudo code is checked on its own from the same
+imported configuration (Step 2 + boundary Step 3; Steps 3, 3-4, 3-5, 3-6),
+and whole sweeps are checked sweep by sweep.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+
+import paper_1307_0328_gb300 as P  # noqa: E402
+
+REL = 1e-12
+
+GEOMS = [
+    # config-1 parameters on the 8x8 lattice, one domain
+    dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=6, seed=1, init=1, init_seed=1),
+    # 2x2 lattice (every pair carries two bonds), empty start
+    dict(Lx=2, Ly=2, beta=1.5, eta=0.5, n_cycle=4, seed=3, init=0),
+    # domains + sub-blocks, non-zero V and mu
+    dict(Lx=8, Ly=8, beta=2.0, eta=0.3, V=1.0, mu=0.7, dom_x=4, dom_y=4, sub_block=2,
+         n_cycle=5, exchange_every=1, seed=5),
+    # 16x16 in 8x8 domains (config-2 shape, smaller), K = 2
+    dict(Lx=16, Ly=16, beta=4.0, eta=0.1, dom_x=8, dom_y=8, sub_block=4, n_cycle=8,
+         exchange_every=2, seed=7, init=1, init_seed=7),
+    # odd sizes, non-square domains, t = 0 and a long circle
+    dict(Lx=6, Ly=9, beta=4.0, eta=0.15, t=0.0, c_off=0.3, mu=0.8, dom_x=3, dom_y=3,
+         n_cycle=3, seed=11),
+    # large V, negative mu, bounce-rich directed loops
+    dict(Lx=12, Ly=4, beta=3.0, eta=0.25, V=3.0, mu=-1.5, t=0.7, dom_x=6, dom_y=2,
+         sub_block=2, n_cycle=4, seed=13),
+]
+
+
+def _pair(kw):
+    return P.Sim(**kw), O.Oracle(**kw)
+
+
+def _same(a, b, what):
+    if not np.array_equal(a, b):
+        n = min(len(a), len(b))
+        diff = np.nonzero(a[:n] != b[:n])[0]
+        first = int(diff[0]) if len(diff) else n
+        raise AssertionError("%s: %d vs %d words, first difference at word %d" % (what, len(a), len(b), first))
+
+
+@pytest.mark.parametrize("kw", GEOMS)
+def test_steps_bit_exact(kw):
+    """From the same configuration, every step on its own."""
+    g, o = _pair(kw)
+    nd = (kw["Lx"] // (kw.get("dom_x") or kw["Lx"])) * (kw["Ly"] // (kw.get("dom_y") or kw["Ly"]))
+    for s in range(6):
+        snap = o.export()
+        if nd > 1:
+            g.import_(snap); g.sweep_index = s
+            o.boundary(); g.boundary()
+            _same(g.export(), o.export(), "Step 2 at sweep %d" % s)
+            snap = o.export()
+        for stop in (3, 4, 5, 6):
+            o.import_(snap); o.sweep_index = s
+            g.import_(snap); g.sweep_index = s
+            o.tile(stop); g.tile(stop)
+            _same(g.export(), o.export(), "Steps 3..%d at sweep %d" % (stop, s))
+        ro, rg = o.rows(), g.rows()
+        assert len(ro) == 1 and len(rg) == 1
+        for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+            assert ro[f][0] == rg[f][0], f
+        assert rg["q_impr"][0] == pytest.approx(ro["q_impr"][0], rel=REL)
+        o.sweep_index = s + 1
+
+
+@pytest.mark.parametrize("kw", GEOMS)
+def test_sweeps_bit_exact(kw):
+    """Whole sweeps from the initial state, compared after every sweep."""
+    g, o = _pair(kw)
+    for s in range(12):
+        o.sweep(1)
+        g.sweep(1)
+        _same(g.export(), o.export(), "after sweep %d" % s)
+    ro, rg = o.rows(), g.rows()
+    for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+        assert np.array_equal(ro[f], rg[f]), f
+    assert np.allclose(rg["q_impr"], ro["q_impr"], rtol=REL, atol=0)
+
+
+def test_rho_slices_match():
+    kw = GEOMS[2]
+    g, o = _pair(kw)
+    o.sweep(5)
+    g.sweep(5)
+    assert np.allclose(g.rho_slices(8), o.rho_slices(8), rtol=REL, atol=0)
+
+
+def test_many_sweeps_config1_shape():
+    """Config-1 shape over 200 sweeps: configuration identical at the end."""
+    kw = dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=8, seed=1, init=1, init_seed=1)
+    g, o = _pair(kw)
+    o.sweep(200)
+    g.sweep(200)
+    _same(g.export(), o.export(), "after 200 sweeps")
+    ro, rg = o.rows(), g.rows()
+    assert np.array_equal(ro["n_v"], rg["n_v"]) and np.array_equal(ro["n_w"], rg["n_w"])
+
+
+def test_capacity_overflow_is_reported():
+    """A per-site slot far too small makes pmwa_sweep return PMWA_ECAPACITY
+    (no device fault); the handle stays usable for queries."""
+    g = P.Sim(Lx=8, Ly=8, beta=8.0, eta=0.2, n_cycle=2, cap_site=8)
+    with pytest.raises(P.PmwaError) as e:
+        g.sweep(3)
+    assert e.value.status == P.PMWA_ECAPACITY
+    assert g.sweep_index >= 0
+
+
+def test_rows_buffer_full_is_reported():
+    g = P.Sim(Lx=4, Ly=4, rows_cap=4, n_cycle=1)
+    g.sweep(4)
+    with pytest.raises(P.PmwaError) as e:
+        g.sweep(1)
+    assert e.value.status == P.PMWA_EROWS
+    assert len(g.rows()) == 4
+    g.sweep(1)

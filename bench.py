@@ -233,6 +233,7 @@ def main():
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     prof = P.pmwa_profile_read(sim.h)
+    phases = P.pmwa_profile_phases(sim.h)
     P.pmwa_profile(sim.h, False)
     clk = clocks.stop()
     rows = sim.rows()
@@ -273,12 +274,15 @@ def main():
         kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
         top = max((k for k in kernels if k != "sweep"), key=lambda k: kernels[k]["ms_total"])
         peak, which = peaks()
-        # algorithmic bytes of the merge + worm-creation kernel: read the old
-        # configuration and the new vertices, write keys and labels of the new one
+        # algorithmic bytes per launch: the tile kernel reads the whole current
+        # configuration and writes the whole next one (8-byte event keys: two
+        # vertex legs per vertex plus the worms); a boundary launch reads and
+        # writes the lists of the two sites of every bond between domains
         ev = float(2 * rows["n_v"].mean() + rows["n_w"].mean())
-        alg = dict(merge_worm_creation=8.0 * (ev + 0.5 * 2 * rows["n_v"].mean() + 2 * ev),
-                   vertex_candidates=8.0 * (2 * ev + 0.5 * rows["n_v"].mean()),
-                   scatter=8.0 * 4 * ev, measure=8.0 * ev, boundary=8.0 * ev * 0.25)
+        per_site = ev / (kw["Lx"] * kw["Ly"])
+        nbsites = 2 * max((kw["Lx"] // kw["dom_x"]) * kw["Ly"] if kw["Lx"] > kw["dom_x"] else 0,
+                          (kw["Ly"] // kw["dom_y"]) * kw["Lx"] if kw["Ly"] > kw["dom_y"] else 0)
+        alg = dict(tile=16.0 * ev, boundary=16.0 * per_site * nbsites)
         tk = kernels[top]
         per_launch_ms = tk["ms_total"] / tk["launches"]
         achieved = alg.get(top, 0.0) / (per_launch_ms / 1000.0) / 1e9
@@ -294,6 +298,7 @@ def main():
                           frac=achieved / peak, traffic=None,
                           peak_source=which + " MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"),
             kernels=kernels,
+            tile_phase_cycles=phases,
             e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=64),
             gpu_launches=int(sum(v["launches"] for k, v in kernels.items() if k != "sweep")),
             clocks=clk, wall_s=wall,

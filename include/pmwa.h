@@ -156,6 +156,12 @@ int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4,
    measurement plumbing. */
 int pmwa_profile(pmwa_handle* h, int32_t enable);
 int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
+/* SM clock cycles spent by the sweep kernel in each of its phases, summed
+   over its CTAs since the last call while profiling is on: 0 vertex
+   candidates (Step 3), 1 leg merge (Step 3), 2 worm creation (Step 4),
+   3 scattering (Step 5), 4 output + measurement (Step 6); n >= 8 entries,
+   cleared after reading.  No paper counterpart: measurement plumbing. */
+int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n);
 
 const char* pmwa_strerror(int status);
 

@@ -72,6 +72,7 @@ def load(build=True):
         "pmwa_strerror": (C.c_char_p, [C.c_int]),
         "pmwa_profile": (C.c_int, [vp, C.c_int32]),
         "pmwa_profile_read": (C.c_int, [vp, vp, vp, C.c_int32]),
+        "pmwa_profile_phases": (C.c_int, [vp, vp, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -174,8 +175,7 @@ def pmwa_destroy(h):
     _check("pmwa_destroy", load().pmwa_destroy(h))
 
 
-KERNELS = ("boundary", "vertex_candidates", "merge_worm_creation", "scatter", "measure", "rho",
-           "sweep")
+KERNELS = ("boundary", "tile", "unused2", "unused3", "unused4", "rho", "sweep")
 
 
 def pmwa_profile(h, enable):
@@ -187,6 +187,15 @@ def pmwa_profile_read(h):
     n = np.zeros(8, dtype=np.int64)
     _check("pmwa_profile_read", load().pmwa_profile_read(h, ms.ctypes.data, n.ctypes.data, 8))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+PHASES = ("vertex_candidates", "leg_merge", "worm_creation", "scatter", "output_measure")
+
+
+def pmwa_profile_phases(h):
+    c = np.zeros(8, dtype=np.uint64)
+    _check("pmwa_profile_phases", load().pmwa_profile_phases(h, c.ctypes.data, 8))
+    return {k: int(c[i]) for i, k in enumerate(PHASES)}
 
 
 def pmwa_tables(**kw):

@@ -18,6 +18,29 @@ __constant__ double c_zF[257];
 __constant__ double c_zW[256];
 __constant__ unsigned long long c_zK[256];
 __constant__ double c_zR;
+// Taylor coefficients 1/n!, n = 0..24: the correctly rounded quotients
+// 1.0 / n! of exact factorials, computed on the host.
+__constant__ double c_inv_fact[25];
+
+// Every translation unit that includes this header owns its own copy of the
+// constant tables above (no relocatable device code), so each unit uploads
+// them through this function.
+static int upload_constants(const Zig& z) {
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_zX, z.X, sizeof z.X))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zF, z.F, sizeof z.F))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zW, z.W, sizeof z.W))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zK, z.K, sizeof z.K))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zR, &z.R, sizeof z.R))) return int(e);
+  double inv_fact[25];
+  double fact = 1.0;
+  for (int n = 0; n <= 24; ++n) {
+    if (n > 0) fact = fact * double(n);  // the same rounded running products as
+    inv_fact[n] = 1.0 / fact;            // the CPU reference computes
+  }
+  if ((e = cudaMemcpyToSymbol(c_inv_fact, inv_fact, sizeof inv_fact))) return int(e);
+  return 0;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
@@ -78,16 +101,9 @@ __device__ inline double exp_det(double x) {
   const int k = int(kd);
   const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, 0.693147182464599609375)),
                              __dmul_rn(kd, -1.9046542999577678e-09));
-  double fact = 1.0;
-  double c[14];
+  double p = c_inv_fact[13];
 #pragma unroll
-  for (int n = 0; n <= 13; ++n) {
-    if (n > 0) fact = __dmul_rn(fact, double(n));
-    c[n] = __ddiv_rn(1.0, fact);
-  }
-  double p = c[13];
-#pragma unroll
-  for (int n = 12; n >= 0; --n) p = __dadd_rn(__dmul_rn(p, r), c[n]);
+  for (int n = 12; n >= 0; --n) p = __dadd_rn(__dmul_rn(p, r), c_inv_fact[n]);
   if (k >= -1022) return __dmul_rn(p, pow2i(k));
   return __dmul_rn(__dmul_rn(p, pow2i(k + 600)), pow2i(-600));
 }
@@ -95,13 +111,9 @@ __device__ inline double exp_det(double x) {
 // e^x - 1: degree-24 Taylor polynomial (no constant term) on [-1, 1].
 __device__ inline double expm1_det(double x) {
   if (!(x <= 1.0 && x >= -1.0)) return __dsub_rn(exp_det(x), 1.0);
-  double fact = 1.0;
-  double c[25];
+  double p = c_inv_fact[24];
 #pragma unroll
-  for (int n = 1; n <= 24; ++n) { fact = __dmul_rn(fact, double(n)); c[n] = __ddiv_rn(1.0, fact); }
-  double p = c[24];
-#pragma unroll
-  for (int n = 23; n >= 1; --n) p = __dadd_rn(__dmul_rn(p, x), c[n]);
+  for (int n = 23; n >= 1; --n) p = __dadd_rn(__dmul_rn(p, x), c_inv_fact[n]);
   return __dmul_rn(p, x);
 }
 
@@ -110,6 +122,32 @@ __device__ inline double expm1_det(double x) {
 __device__ inline double g_sigma(int sigma, double x) {
   const double e = expm1_det(__dmul_rn(-2.0, x));
   return sigma ? __ddiv_rn(__dadd_rn(2.0, e), -e) : __ddiv_rn(-e, __dadd_rn(2.0, e));
+}
+
+// x g_sigma(x) for the worm-density estimator (an FP64 observable, not a
+// decision): the power series in y = x^2, x tanh x = sum_n a_n y^n and
+// x coth x = sum_n b_n y^n with a_n = 2^{2n} (2^{2n} - 1) B_{2n} / (2n)! and
+// b_n = 2^{2n} B_{2n} / (2n)! (B the Bernoulli numbers); 6 terms for
+// y <= 1/400 and 16 for y <= 1/4 keep the truncation below 1e-17, larger x
+// go through expm1_det.
+__constant__ double c_xtanh[16] = {1.0, -0.3333333333333333, 0.13333333333333333, -0.05396825396825397, 0.021869488536155203, -0.008863235529902197, 0.003592128036572481, -0.0014558343870513183, 0.000590027440945586, -0.00023912911424355248, 9.691537956929451e-05, -3.927832388331683e-05, 1.5918905069328964e-05, -6.451689215655431e-06, 2.6147711512907546e-06, -1.0597268320104654e-06};
+__constant__ double c_xcoth[17] = {1.0, 0.3333333333333333, -0.022222222222222223, 0.0021164021164021165, -0.00021164021164021165, 2.1377799155576935e-05, -2.1644042808063972e-06, 2.1925947851873778e-07, -2.2214608789979678e-08, 2.2507846516808994e-09, -2.2805151204592183e-10, 2.3106432599002624e-11, -2.3411706819824882e-12, 2.3721017400233653e-13, -2.4034415333307705e-14, 2.4351954029183367e-15, -2.4673688045172075e-16};
+
+__device__ inline double xg_sigma(int sigma, double x) {
+  const double y = x * x;
+  int n;
+  if (y <= 2.5e-3) n = 6;
+  else if (y <= 0.25) n = 16;
+  else return __dmul_rn(x, g_sigma(sigma, x));
+  double p;
+  if (sigma) {
+    p = c_xcoth[n - 1];
+    for (int k = n - 2; k >= 0; --k) p = fma(p, y, c_xcoth[k]);
+    return p;
+  }
+  p = c_xtanh[n - 1];
+  for (int k = n - 2; k >= 0; --k) p = fma(p, y, c_xtanh[k]);
+  return p * y;
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,7 @@ struct pmwa_handle {
   int rows_pending;
   uint64_t TH[256];
   DevErr* err;
+  unsigned long long* phase;  // device phase-cycle counters
   bool profiling = false;
   std::vector<Timed> timed;            // events of launches not yet read
   std::vector<cudaEvent_t> event_pool;  // spare events
@@ -37,7 +38,8 @@ struct pmwa_handle {
 namespace {
 
 struct Derived {
-  int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap;
+  int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap, poolcap;
+  double legs_per_site, mb;
   double d[4], D, tkink, SV, SW, XW;
   uint64_t TV[4], SWI;
   uint64_t TH[256];
@@ -150,15 +152,18 @@ void derive(const pmwa_params* p, Derived* g) {
   int cap = p->cap_site ? p->cap_site : int(mean + 8.0 * std::sqrt(mean) + 24.0);
   g->cap = (cap + 7) & ~7;
   const double mb = p->beta * g->D;
+  g->mb = mb;
   g->capb = (int(mb + 8.0 * std::sqrt(mb) + 16.0) + 7) & ~7;
+  // shared-memory tile of one domain: legs (<= 4 bonds x beta (D + t) per
+  // site), Step-3 candidates (mean beta D per bond), worms (<= beta eta per site)
   const int nds = g->dom_x * g->dom_y;
-  const int nsub = sb_slots_host(g->dom_x, p->sub_block, g->ndx) * sb_slots_host(g->dom_y, p->sub_block, g->ndy);
-  const long long room = (200LL * 1024 - 2048 - 8LL * (nsub + 4)) / 24;
-  g->wcap = int(std::min<long long>(8LL * nds + 64, room));
+  g->legs_per_site = 4.0 * p->beta * (g->D + p->t);
+  g->poolcap = int(std::min(60000.0, 1.5 * mb * 2.0 * nds + 256.0));
+  g->wcap = int(std::min(16000.0, 2.0 * p->beta * p->eta * nds + 256.0));
 }
 
 struct Layout {
-  size_t err, TH, rows, cntA, cntB, keyA, keyB, lab, tmp, ccnt, cand, total;
+  size_t err, TH, phase, rows, cntA, cntB, keyA, keyB, total;
 };
 
 Layout layout(const pmwa_params* p, const Derived& g) {
@@ -168,15 +173,12 @@ Layout layout(const pmwa_params* p, const Derived& g) {
   const int rows_cap = p->rows_cap ? p->rows_cap : 4096;
   L.err = o; o = align_up(o + sizeof(DevErr));
   L.TH = o; o = align_up(o + 256 * sizeof(uint64_t));
+  L.phase = o; o = align_up(o + 8 * sizeof(uint64_t));
   L.rows = o; o = align_up(o + size_t(rows_cap) * sizeof(pmwa_row));
   L.cntA = o; o = align_up(o + N * sizeof(uint32_t));
   L.cntB = o; o = align_up(o + N * sizeof(uint32_t));
   L.keyA = o; o = align_up(o + N * cap * sizeof(uint64_t));
   L.keyB = o; o = align_up(o + N * cap * sizeof(uint64_t));
-  L.lab = o; o = align_up(o + N * cap * sizeof(uint64_t));
-  L.tmp = o; o = align_up(o + N * cap * sizeof(uint64_t));
-  L.ccnt = o; o = align_up(o + 2 * N * sizeof(uint32_t));
-  L.cand = o; o = align_up(o + 2 * N * size_t(g.capb) * sizeof(uint64_t));
   L.total = o;
   return L;
 }
@@ -229,15 +231,13 @@ int run_tile(pmwa_handle* h, int stop, bool record) {
   Dev& d = h->d;
   d.sweep = uint32_t(h->sweep);
   cudaStream_t st = h->stream;
-  if (timed_launch(h, 1, [&] { return launch_step3(d, st); })) return PMWA_ECUDA;
-  if (timed_launch(h, 2, [&] { return launch_step34_sites(d, stop >= 4 ? 1 : 0, st); })) return PMWA_ECUDA;
-  if (stop >= 5 && d.n_cycle > 0 && timed_launch(h, 3, [&] { return launch_step5(d, st); })) return PMWA_ECUDA;
-  if (stop >= 6 && record) {
+  const int eff = (stop == 6 && !record) ? 5 : stop;
+  if (eff == 6) {
     d.row = h->rows_pending;
     if (cudaMemsetAsync(d.rows + d.row, 0, sizeof(pmwa_row), st)) return PMWA_ECUDA;
-    if (timed_launch(h, 4, [&] { return launch_measure(d, st); })) return PMWA_ECUDA;
-    h->rows_pending++;
   }
+  if (timed_launch(h, 1, [&] { return launch_tile(d, eff, st); })) return PMWA_ECUDA;
+  if (eff == 6) h->rows_pending++;
   swap_buffers(d);
   return PMWA_OK;
 }
@@ -343,14 +343,13 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   if (rc) return rc;
   Derived g;
   derive(p, &g);
-  if (g.wcap < 64) return PMWA_EINVAL;  // domain too large for the Step-5 table
   const Layout L = layout(p, g);
   if (!arena || bytes < L.total || (reinterpret_cast<uintptr_t>(arena) & (kAlign - 1))) return PMWA_EINVAL;
   static bool zig_ready = false;
   {
     Zig z;
     build_zig(&z);
-    if (upload_zig(z)) return PMWA_ECUDA;
+    if (upload_zig(z) || upload_zig_tile(z)) return PMWA_ECUDA;
     zig_ready = true;
   }
   pmwa_handle* h = new (std::nothrow) pmwa_handle();
@@ -367,7 +366,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.Lx = p->Lx; d.Ly = p->Ly; d.N = g.N;
   d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy; d.ndom = g.ndom;
   d.sub_block = p->sub_block; d.n_cycle = p->n_cycle;
-  d.cap = g.cap; d.capb = g.capb; d.wcap = g.wcap;
+  d.cap = g.cap; d.capb = g.capb; d.wcap = g.wcap; d.poolcap = g.poolcap;
   d.key0 = uint32_t(p->seed); d.key1 = uint32_t(p->seed >> 32); d.replica = p->replica;
   d.beta = p->beta; d.eta = p->eta; d.SV = g.SV; d.SW = g.SW; d.XW = g.XW; d.SWI = g.SWI;
   d.has_vertices = g.D > 0.0 ? 1 : 0;
@@ -380,11 +379,13 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.cntB = reinterpret_cast<uint32_t*>(base + L.cntB);
   d.keyA = reinterpret_cast<uint64_t*>(base + L.keyA);
   d.keyB = reinterpret_cast<uint64_t*>(base + L.keyB);
-  d.lab = reinterpret_cast<uint64_t*>(base + L.lab);
-  d.tmp = reinterpret_cast<uint64_t*>(base + L.tmp);
-  d.ccnt = reinterpret_cast<uint32_t*>(base + L.ccnt);
-  d.cand = reinterpret_cast<uint64_t*>(base + L.cand);
   h->err = d.err;
+  h->phase = reinterpret_cast<unsigned long long*>(base + L.phase);
+  d.phase_cycles = nullptr;
+  if (!plan_tile_smem(&d, g.legs_per_site, g.mb)) {  // a domain too large for shared memory
+    delete h;
+    return PMWA_EINVAL;
+  }
   // initial configuration: no events; floor(N/2) occupied sites from a
   // Fisher-Yates permutation of the stream (init_seed, unit 0, init phase)
   std::vector<uint32_t> cnt(size_t(g.N), 0u);
@@ -412,7 +413,8 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   DevErr z{0, 0};
   if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||
       cudaMemcpy(const_cast<uint64_t*>(d.TH), g.TH, sizeof g.TH, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) {
+      cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ||
+      cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) {
     delete h;
     return PMWA_ECUDA;
   }
@@ -436,6 +438,16 @@ int pmwa_profile(pmwa_handle* h, int32_t enable) {
   for (const Timed& t : h->timed) { h->event_pool.push_back(t.start); h->event_pool.push_back(t.stop); }
   h->timed.clear();
   h->profiling = enable != 0;
+  h->d.phase_cycles = h->profiling ? h->phase : nullptr;
+  if (cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n) {
+  if (!h || !cycles || n < 8) return PMWA_EINVAL;
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  if (cudaMemcpy(cycles, h->phase, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
+  if (cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -518,8 +530,8 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
 
 int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
   if (!h || K < 1 || !host_out) return PMWA_EINVAL;
-  if (size_t(K) > size_t(h->d.cap)) return PMWA_EINVAL;  // scratch is the tmp slots
-  double* dev = reinterpret_cast<double*>(h->d.tmp);
+  if (size_t(K) > size_t(h->d.cap)) return PMWA_EINVAL;  // scratch: the idle next-configuration slots
+  double* dev = reinterpret_cast<double*>(h->d.keyB);
   if (launch_rho(h->d, K, dev, h->stream)) return PMWA_ECUDA;
   if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
   if (cudaMemcpy(host_out, dev, size_t(h->d.N) * size_t(K) * sizeof(double), cudaMemcpyDeviceToHost))

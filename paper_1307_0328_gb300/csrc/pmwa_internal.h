@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "../../include/pmwa.h"
 
 namespace pmwa {
@@ -27,8 +29,14 @@ struct Dev {
   int Lx, Ly, N, dom_x, dom_y, ndx, ndy, ndom;
   int sub_block, n_cycle;
   int cap;      // events per site slot
-  int capb;     // candidate vertices per bond slot
-  int wcap;     // worms per domain in the Step-5 table
+  int capb;     // candidate vertices per bond (Step 3)
+  int wcap;     // worms per domain in the shared-memory worm table
+  int legcap;   // vertex legs per domain in shared memory
+  int poolcap;  // Step-3 candidates per domain in shared memory
+  // shared-memory carve-up of the tile kernel (byte offsets)
+  int sm_th, sm_off, sm_base, sm_bcnt, sm_boff, sm_misc, sm_nbr, sm_sub, sm_leg, sm_pool,
+      sm_worm, sm_idx, sm_posu, sm_rw, sm_bkt, sm_fill, sm_total;
+  unsigned long long* phase_cycles;  // 8 counters when profiling, else null
   // random numbers
   uint32_t key0, key1, replica, sweep;
   // model
@@ -43,10 +51,6 @@ struct Dev {
   uint32_t* cntA;   // count | base << 31
   uint64_t* keyB;   // next configuration
   uint32_t* cntB;
-  uint64_t* lab;    // worm labels, parallel to keyB
-  uint64_t* tmp;    // per-site scratch slot (vertex legs of Step 3)
-  uint64_t* cand;   // per-bond candidate vertices of Step 3
-  uint32_t* ccnt;
   const uint64_t* TH;  // 16*4*4 directed-loop thresholds
   DevErr* err;
   pmwa_row* rows;
@@ -62,14 +66,14 @@ struct Zig {
 void build_zig(Zig* z);
 
 // Kernel launchers (pmwa_kernels.cu).  All return a cudaError_t as int.
-int upload_zig(const Zig& z);
+int upload_zig(const Zig& z);       // constants of pmwa_kernels.cu
+int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
-int launch_step3(const Dev& d, void* stream);
-int launch_step34_sites(const Dev& d, int regen, void* stream);
-int launch_step5(const Dev& d, void* stream);
-int launch_measure(const Dev& d, void* stream);
+int launch_tile(const Dev& d, int stop, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
-size_t step5_smem(const Dev& d);
+// shared-memory plan of the tile kernel for this instance (fills the sm_*
+// offsets); returns false if a domain cannot fit in shared memory.
+bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond);
 
 // Step-5 sub-block count along one axis (host copy of the device rule).
 inline int sb_slots_host(int D, int B, int nd) {

@@ -1,0 +1,706 @@
+// pmwa_tile.cu -- Steps 3-6 of one MC sweep in a single kernel: one CTA per
+// domain, the domain's vertex legs and worms resident in shared memory.
+//
+//   phase 1  Step 3 candidates, one thread per bond of the domain, written to
+//            a shared pool (the current configuration is read from HBM/L2)
+//   phase 2  per site: the kept vertex legs of the current configuration
+//            merged in time order with the new ones into the shared leg array
+//   phase 3  Step 4, one thread per site: worms of every interval (Eq. 1)
+//            into the shared worm table; each worm records its site and the
+//            index of the vertex leg just below it (its interval)
+//   phase 4  Step 5, N_cycle passes of the shifted sub-block schedule: worms
+//            bucketed by sub-block, one thread per sub-block moves its worms
+//            in label order (Eq. 2); vertex legs never move in Step 5, so a
+//            move is a handful of shared-memory reads and two bit flips
+//   phase 5  legs and worms merged per site into the next configuration in
+//            HBM, with the Step-6 counters and the Supplement S-I estimator
+//
+// The arithmetic and the order of every random draw are those of the
+// deterministic specification, so the result is bit-identical to the CPU
+// reference for every domain layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "pmwa_device.cuh"
+
+namespace pmwa {
+
+namespace {
+
+constexpr int kTileThreads = 256;
+constexpr int kMaxCandPerBond = 128;
+constexpr int kMaxWormsPerInterval = 128;
+constexpr uint16_t kNone = 0xFFFF;
+constexpr uint32_t kCntMask = 0x7fffffffu;
+constexpr uint64_t kMask62 = kTwo62 - 1;
+constexpr int kSmemLimit = 232448;  // opt-in shared memory per block on sm_103a
+
+struct WormRec {
+  uint64_t key;
+  uint64_t lab;
+  uint16_t site;  // local site index
+  uint16_t leg;   // leg array index of the vertex leg just below (kNone: site without legs)
+  uint32_t pad;
+};
+
+struct Misc {
+  int pool_used;
+  int nworms;
+  int err;
+  int where;
+};
+
+__device__ __forceinline__ int cnt_n(uint32_t c) { return int(c & kCntMask); }
+__device__ __forceinline__ int cnt_base(uint32_t c) { return int(c >> 31); }
+
+__device__ __forceinline__ void tile_fail(Misc* m, int code, int where) {
+  if (atomicCAS(&m->err, 0, code) == 0) m->where = where;
+}
+
+// exclusive scan of a[0..n) in place (a[n] receives the total); all threads
+__device__ int block_scan(int* a, int n, int* wsum) {
+  const int t = threadIdx.x, T = blockDim.x, lane = t & 31, wid = t >> 5, nw = T >> 5;
+  const int chunk = (n + T - 1) / T;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += a[i];
+  int v = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) wsum[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int w = (lane < nw) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    if (lane < nw) wsum[lane] = w;
+  }
+  __syncthreads();
+  int run = v - sum + (wid ? wsum[wid - 1] : 0);
+  for (int i = lo; i < hi; ++i) { const int x = a[i]; a[i] = run; run += x; }
+  const int total = wsum[nw - 1];
+  __syncthreads();
+  if (t == 0) a[n] = total;
+  __syncthreads();
+  return total;
+}
+
+struct Tile {
+  const Dev* d;
+  uint64_t* th;
+  int* off;        // [nds + 1] start of each site's legs in leg[]
+  uint8_t* base;   // [nds] state of a site without legs
+  int* bcnt;       // [2 nds] candidates per bond of the domain
+  int* boff;       // [2 nds] their start in pool[]
+  Misc* misc;
+  uint64_t* leg;   // [legcap]
+  uint64_t* pool;  // [poolcap] (aliases the worm table)
+  WormRec* W;      // [wcap]
+  uint16_t* idx;   // [wcap]
+  uint16_t* posu;  // [wcap] sub-block of each bucketed position
+  uint64_t* rw;    // [2 wcap] Philox words of each bucketed position
+  int* bkt;        // [max(nsub, nds) + 1]
+  int* fill;       // [max(nsub, nds)]
+  int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
+  uint16_t* sub;   // [4 nds] sub-block of each site for offset pattern pass & 3
+  int x0, y0, nds, nsub;
+
+  __device__ int gsite(int li) const { return (x0 + li % d->dom_x) + d->Lx * (y0 + li / d->dom_x); }
+  __device__ int lsite(int s) const { return (s % d->Lx - x0) + d->dom_x * (s / d->Lx - y0); }
+  __device__ int sub_of(int li, int pass) const {
+    const int B = d->sub_block;
+    const int ox = (B && B < d->dom_x) ? (pass & 1) * (B / 2) : 0;
+    const int oy = (B && B < d->dom_y) ? ((pass >> 1) & 1) * (B / 2) : 0;
+    const int bx = sb_axis(li % d->dom_x, d->dom_x, B, d->ndx, ox);
+    const int by = sb_axis(li / d->dom_x, d->dom_y, B, d->ndy, oy);
+    return bx + sb_slots(d->dom_x, B, d->ndx) * by;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// phase 1: Step 3 candidates of bond (a, dir) from the current configuration
+__device__ int bond_candidates(const Dev& d, int a, int dir, uint64_t* buf, int cap, int* bad) {
+  const int b = site_step(d, a, dir, +1);
+  const uint64_t tag = uint64_t(bond_tag(d, a, dir));
+  const uint64_t* KA = d.keyA + size_t(a) * d.cap;
+  const uint64_t* KB = d.keyA + size_t(b) * d.cap;
+  const uint32_t ca = d.cntA[a], cb = d.cntA[b];
+  const int nA = cnt_n(ca), nB = cnt_n(cb);
+  Stream s;
+  s.init(d.key0, d.key1, uint32_t(2 * a + dir), c2_word(kVertex, 0, d.replica), d.sweep);
+  int n = 0, ia = 0, ib = 0;
+  uint64_t pos = 0;
+  bool first = true;
+  for (;;) {
+    const double E = zig_exp(s, bad);
+    if (*bad) break;
+    const uint64_t g = grid_gap(E, d.SV);
+    const uint64_t nxt = first ? g - 1 : pos + g;
+    first = false;
+    if (nxt >= kTwo59) break;
+    pos = nxt;
+    const uint64_t pk = (pos << 3) | tag;
+    while (ia < nA && kpk(KA[ia]) < pk) ++ia;
+    while (ib < nB && kpk(KB[ib]) < pk) ++ib;
+    if (ia < nA && kpk(KA[ia]) == pk && kab(KA[ia]) != kbl(KA[ia])) continue;  // a kink holds the point
+    const int na = nA ? kab(KA[ia ? ia - 1 : nA - 1]) : cnt_base(ca);
+    const int nb = nB ? kab(KB[ib ? ib - 1 : nB - 1]) : cnt_base(cb);
+    const int si = na | (nb << 1);
+    if (d.TV[si] < kTwo32) {
+      const uint64_t w = s.word();
+      if ((w >> 32) >= d.TV[si]) continue;
+    }
+    if (n >= cap) { *bad = PMWA_ECAPACITY; break; }
+    buf[n++] = (pk << 2) | uint64_t(na) | (uint64_t(nb) << 1);
+  }
+  return n;
+}
+
+// old event kept by Step 3: a kink, or any leg of a bond between domains
+__device__ __forceinline__ bool kept_leg(const Dev& d, int s, uint64_t k) {
+  if (kworm(k)) return false;
+  if (kab(k) != kbl(k)) return true;
+  int dir;
+  const int a = leg_lower(d, s, ktag(k), &dir);
+  return boundary_bond(d, a, dir);
+}
+
+// the four bonds of local site li: (s,x) (s,y) with s the lower site, then
+// (s-x,x) (s-y,y) with s the upper site; local bond id or -1 (between domains)
+__device__ __forceinline__ void site_bonds(const Tile& T, int li, int lb[4]) {
+  const Dev& d = *T.d;
+  const int s = T.gsite(li);
+  for (int j = 0; j < 4; ++j) {
+    const int dir = j & 1;
+    const int a = (j < 2) ? s : site_step(d, s, dir, -1);
+    lb[j] = boundary_bond(d, a, dir) ? -1 : 2 * T.lsite(a) + dir;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// phase 4: one Step-5 move of worm seg[r] (its sub-block's worms are seg[0..n),
+// and only they can sit on the sub-block's sites).
+__device__ int leg_index(const Tile& T, int x, uint64_t pv) {
+  const int st = T.off[x], en = T.off[x + 1];
+  int lo = st, hi = en;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (kpk(T.leg[mid]) < pv) lo = mid + 1; else hi = mid;
+  }
+  return (lo < en && kpk(T.leg[lo]) == pv) ? lo : -1;
+}
+
+__device__ __forceinline__ uint32_t site_leg(const WormRec& w) {
+  return *reinterpret_cast<const uint32_t*>(&w.site);  // site | leg << 16
+}
+
+// The worm at (site li, interval above leg L) heading up or down: reverse at
+// another worm of its interval or at a vertex of an inactive bond; otherwise
+// enter the vertex v with probability L_min / L_i (word0 >> 32 against the
+// exact ratio), leave by leg j (threshold table, low half of word0), land on
+// a uniform worm grid point of leg j (mulhi of word1) heading away from v.
+// Leg l of v runs from v to the nearest event on its site and side (other
+// vertex leg or worm, the moving worm excluded; the whole circle if none).
+__device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q,
+                         uint64_t w0, uint64_t w1) {
+  WormRec& w = T.W[seg[r]];
+  const int li = w.site;
+  const uint64_t key = w.key;
+  const bool up = kdir(key);
+  const int st = T.off[li], en = T.off[li + 1];
+  if (st == en) { w.key = key ^ 2u; return PMWA_OK; }  // a site of worms only
+  const int L = w.leg;
+  const uint64_t pL = kpk(T.leg[L]);
+  const uint64_t my = (kpk(key) - pL) & kMask62;
+  const uint32_t self = uint32_t(li) | (uint32_t(L) << 16);
+  for (int k = 0; k < n; ++k) {
+    const WormRec& o = T.W[seg[k]];
+    if (k == r || site_leg(o) != self) continue;
+    const uint64_t off = (kpk(o.key) - pL) & kMask62;
+    if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
+  }
+  const int iv = up ? ((L + 1 == en) ? st : L + 1) : L;
+  const uint64_t pv = kpk(T.leg[iv]);
+  const int nb = T.nbr[li * 6 + ktag(T.leg[iv])];
+  if (nb < 0) { w.key = key ^ 2u; return PMWA_OK; }   // bond to another domain
+  const int pl = nb >> 1;
+  const bool li_a = nb & 1;                            // li is the bond's lower site
+  if (T.sub[li * 4 + q] != T.sub[pl * 4 + q]) { w.key = key ^ 2u; return PMWA_OK; }
+  const int ip = leg_index(T, pl, pv);
+  if (ip < 0) return PMWA_EINVARIANT;
+  const int al = li_a ? li : pl, bl = li_a ? pl : li;
+  const int ia = li_a ? iv : ip, ib = li_a ? ip : iv;
+  const int sa = T.off[al], ea = T.off[al + 1], sb = T.off[bl], eb = T.off[bl + 1];
+  const int ia_dn = (ia == sa) ? ea - 1 : ia - 1, ib_dn = (ib == sb) ? eb - 1 : ib - 1;
+  const int ia_up = (ia + 1 == ea) ? sa : ia + 1, ib_up = (ib + 1 == eb) ? sb : ib + 1;
+  const uint64_t pa_dn = kpk(T.leg[ia_dn]), pb_dn = kpk(T.leg[ib_dn]);
+  // offsets from v up to the nearest object above, and from the lower leg up
+  // to the highest worm of the interval below v
+  uint64_t ua = (ia_up == ia) ? kTwo62 : ((kpk(T.leg[ia_up]) - pv) & kMask62);
+  uint64_t ub = (ib_up == ib) ? kTwo62 : ((kpk(T.leg[ib_up]) - pv) & kMask62);
+  uint64_t da = 0, db = 0;
+  bool fa = false, fb = false;
+  const uint32_t ka_up = uint32_t(al) | (uint32_t(ia) << 16), kb_up = uint32_t(bl) | (uint32_t(ib) << 16);
+  const uint32_t ka_dn = uint32_t(al) | (uint32_t(ia_dn) << 16), kb_dn = uint32_t(bl) | (uint32_t(ib_dn) << 16);
+  for (int k = 0; k < n; ++k) {
+    if (k == r) continue;
+    const WormRec& o = T.W[seg[k]];
+    const uint32_t sl = site_leg(o);
+    if (sl != ka_up && sl != kb_up && sl != ka_dn && sl != kb_dn) continue;
+    const uint64_t po = kpk(o.key);
+    if (sl == ka_up) { const uint64_t x = (po - pv) & kMask62; if (x < ua) ua = x; }
+    if (sl == kb_up) { const uint64_t x = (po - pv) & kMask62; if (x < ub) ub = x; }
+    if (sl == ka_dn) { const uint64_t x = (po - pa_dn) & kMask62; if (!fa || x > da) { da = x; fa = true; } }
+    if (sl == kb_dn) { const uint64_t x = (po - pb_dn) & kMask62; if (!fb || x > db) { db = x; fb = true; } }
+  }
+  const uint64_t L2 = wpts(pv, (pv + ua) & kMask62);
+  const uint64_t L3 = wpts(pv, (pv + ub) & kMask62);
+  const uint64_t L0 = wpts(fa ? ((pa_dn + da) & kMask62) : pa_dn, pv);
+  const uint64_t L1 = wpts(fb ? ((pb_dn + db) & kMask62) : pb_dn, pv);
+  const int i = li_a ? (up ? 0 : 2) : (up ? 1 : 3);
+  const uint64_t Li = (i == 0) ? L0 : (i == 1) ? L1 : (i == 2) ? L2 : L3;
+  const uint64_t Lmin = min(min(L0, L1), min(L2, L3));
+  // enter iff z1 * L_i < L_min * 2^32 (96-bit comparison)
+  const uint64_t z1 = w0 >> 32, z0 = w0 & 0xffffffffull;
+  const uint64_t ph = __umul64hi(z1, Li), plo = z1 * Li;
+  const uint64_t qh = Lmin >> 32, ql = Lmin << 32;
+  if (!(ph < qh || (ph == qh && plo < ql))) { w.key = key ^ 2u; return PMWA_OK; }
+  const uint64_t va = T.leg[ia], vb = T.leg[ib];
+  const int S = kbl(va) | (kbl(vb) << 1) | (kab(va) << 2) | (kab(vb) << 3);
+  const uint64_t* th = T.th + (S * 4 + i) * 4;
+  int j = 0;
+  while (j < 3 && !(z0 < th[j])) ++j;
+  T.leg[(i & 1) ? ib : ia] ^= (i < 2) ? 2u : 1u;
+  T.leg[(j & 1) ? ib : ia] ^= (j < 2) ? 2u : 1u;
+  const int ix = (j & 1) ? ib : ia;
+  const uint64_t vx = T.leg[ix];
+  const uint64_t Lj = (j == 0) ? L0 : (j == 1) ? L1 : (j == 2) ? L2 : L3;
+  const uint64_t o = __umul64hi(w1, Lj);
+  if (j >= 2) {
+    w.key = wkey((wm_above(pv) + o) & (kTwo59 - 1), 1, kab(vx) ^ 1);
+    w.leg = uint16_t(ix);
+  } else {
+    w.key = wkey((wm_below(pv) + kTwo59 - o) & (kTwo59 - 1), 0, kbl(vx));
+    w.leg = uint16_t((j & 1) ? ib_dn : ia_dn);
+  }
+  w.site = uint16_t((j & 1) ? bl : al);
+  return PMWA_OK;
+}
+
+// per-phase cycle counters (profiling only): thread 0 adds the cycles since
+// the last tick to counter k
+__device__ __forceinline__ void phase_tick(const Dev& d, int k, long long& t) {
+  if (d.phase_cycles && threadIdx.x == 0) {
+    const long long now = clock64();
+    atomicAdd(d.phase_cycles + k, (unsigned long long)(now - t));
+    t = now;
+  }
+}
+
+__device__ __forceinline__ bool worm_less(const WormRec& a, const WormRec& b) {
+  if (a.lab != b.lab) return a.lab < b.lab;
+  if (a.site != b.site) return a.site < b.site;
+  return a.key < b.key;
+}
+
+__device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t blo, uint64_t bhi) {
+  const uint64_t s = lo + blo;
+  hi += bhi + (s < lo ? 1 : 0);
+  lo = s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Dev d, int stop) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int wsum[32];
+  Tile T;
+  T.d = &d;
+  T.th = reinterpret_cast<uint64_t*>(sm + d.sm_th);
+  T.off = reinterpret_cast<int*>(sm + d.sm_off);
+  T.base = reinterpret_cast<uint8_t*>(sm + d.sm_base);
+  T.bcnt = reinterpret_cast<int*>(sm + d.sm_bcnt);
+  T.boff = reinterpret_cast<int*>(sm + d.sm_boff);
+  T.misc = reinterpret_cast<Misc*>(sm + d.sm_misc);
+  T.leg = reinterpret_cast<uint64_t*>(sm + d.sm_leg);
+  T.pool = reinterpret_cast<uint64_t*>(sm + d.sm_pool);
+  T.W = reinterpret_cast<WormRec*>(sm + d.sm_worm);
+  T.idx = reinterpret_cast<uint16_t*>(sm + d.sm_idx);
+  T.posu = reinterpret_cast<uint16_t*>(sm + d.sm_posu);
+  T.rw = reinterpret_cast<uint64_t*>(sm + d.sm_rw);
+  T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
+  T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
+  T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
+  T.sub = reinterpret_cast<uint16_t*>(sm + d.sm_sub);
+  const int dom = blockIdx.x;
+  T.x0 = (dom % d.ndx) * d.dom_x;
+  T.y0 = (dom / d.ndx) * d.dom_y;
+  T.nds = d.dom_x * d.dom_y;
+  T.nsub = sb_slots(d.dom_x, d.sub_block, d.ndx) * sb_slots(d.dom_y, d.sub_block, d.ndy);
+  const int tid = threadIdx.x, NT = blockDim.x, nds = T.nds;
+  Misc* misc = T.misc;
+
+  long long tclk = clock64();
+  for (int k = tid; k < 256; k += NT) T.th[k] = d.TH[k];
+  if (tid == 0) { misc->pool_used = 0; misc->nworms = 0; misc->err = 0; misc->where = 0; }
+  // per-site tables: bond partners by leg tag, sub-blocks by offset pattern
+  for (int li = tid; li < nds; li += NT) {
+    for (int t = 0; t < 6; ++t) T.nbr[li * 6 + t] = -1;
+    const int s = T.gsite(li);
+    for (int j = 0; j < 4; ++j) {
+      const int dir = j & 1;
+      const int a = (j < 2) ? s : site_step(d, s, dir, -1);
+      if (boundary_bond(d, a, dir)) continue;
+      const int other = (j < 2) ? site_step(d, s, dir, +1) : a;
+      T.nbr[li * 6 + bond_tag(d, a, dir)] = int16_t((T.lsite(other) << 1) | (j < 2 ? 1 : 0));
+    }
+    for (int q = 0; q < 4; ++q) T.sub[li * 4 + q] = uint16_t(T.sub_of(li, q));
+  }
+  __syncthreads();
+
+  // ---- phase 1: Step 3 candidates per bond
+  for (int lb = tid; lb < 2 * nds; lb += NT) {
+    const int li = lb >> 1, dir = lb & 1;
+    const int a = T.gsite(li);
+    uint64_t buf[kMaxCandPerBond];
+    int n = 0, bad = 0;
+    if (d.has_vertices && !boundary_bond(d, a, dir))
+      n = bond_candidates(d, a, dir, buf, min(d.capb, kMaxCandPerBond), &bad);
+    if (bad) { tile_fail(misc, bad, 31); n = 0; }
+    int o = 0;
+    if (n) {
+      o = atomicAdd(&misc->pool_used, n);
+      if (o + n > d.poolcap) { tile_fail(misc, PMWA_ECAPACITY, 32); n = 0; }
+      else for (int k = 0; k < n; ++k) T.pool[o + k] = buf[k];
+    }
+    T.bcnt[lb] = n;
+    T.boff[lb] = o;
+  }
+  __syncthreads();
+  phase_tick(d, 0, tclk);
+  if (misc->err) goto fail;
+
+  // ---- phase 2: kept legs + new legs per site, merged in time order
+  for (int li = tid; li < nds; li += NT) {
+    const int s = T.gsite(li);
+    const uint64_t* KO = d.keyA + size_t(s) * d.cap;
+    const int nO = cnt_n(d.cntA[s]);
+    int c = 0;
+    for (int k = 0; k < nO; ++k) c += kept_leg(d, s, KO[k]);
+    int lb[4];
+    site_bonds(T, li, lb);
+    for (int j = 0; j < 4; ++j) if (lb[j] >= 0) c += T.bcnt[lb[j]];
+    T.off[li] = c;
+  }
+  __syncthreads();
+  if (block_scan(T.off, nds, wsum) > d.legcap) { if (tid == 0) tile_fail(misc, PMWA_ECAPACITY, 33); }
+  __syncthreads();
+  if (misc->err) goto fail;
+  for (int li = tid; li < nds; li += NT) {
+    const int s = T.gsite(li);
+    const uint64_t* KO = d.keyA + size_t(s) * d.cap;
+    const int nO = cnt_n(d.cntA[s]);
+    int lb[4], ci[4] = {0, 0, 0, 0}, cn[4];
+    site_bonds(T, li, lb);
+    for (int j = 0; j < 4; ++j) cn[j] = lb[j] >= 0 ? T.bcnt[lb[j]] : 0;
+    int io = 0, o = T.off[li];
+    for (;;) {
+      while (io < nO && !kept_leg(d, s, KO[io])) ++io;
+      uint64_t best = ~0ull;
+      int src = -1;
+      if (io < nO) { best = kpk(KO[io]); src = 4; }
+      for (int j = 0; j < 4; ++j)
+        if (ci[j] < cn[j]) {
+          const uint64_t p = T.pool[T.boff[lb[j]] + ci[j]] >> 2;
+          if (p < best) { best = p; src = j; }
+        }
+      if (src < 0) break;
+      uint64_t key;
+      if (src == 4) key = KO[io++];
+      else {
+        const uint64_t c = T.pool[T.boff[lb[src]] + ci[src]++];
+        const uint64_t st = (c >> (src < 2 ? 0 : 1)) & 1;
+        key = ((c >> 2) << 2) | (st << 1) | st;
+      }
+      T.leg[o++] = key;
+    }
+  }
+  __syncthreads();
+  phase_tick(d, 1, tclk);
+
+  if (stop >= 4) {
+    // ---- phase 3: Step 4, worms of every interval (the pool is dead now)
+    for (int li = tid; li < nds; li += NT) {
+      const int s = T.gsite(li);
+      const int st = T.off[li], nl = T.off[li + 1] - st;
+      Stream rs;
+      rs.init(d.key0, d.key1, uint32_t(s), c2_word(kRegen, 0, d.replica), d.sweep);
+      uint64_t offs[kMaxWormsPerInterval];
+      int bad = 0;
+      if (nl == 0) {
+        const int s0 = int(rs.word() >> 63);
+        T.base[li] = uint8_t(s0);
+        const int n = sample_worms<kMaxWormsPerInterval>(rs, kTwo59, 0, d.SW, d.SWI, offs, &bad);
+        if (!bad && n > 0) {
+          const int o = atomicAdd(&misc->nworms, n);
+          if (o + n > d.wcap) bad = PMWA_ECAPACITY;
+          for (int k = 0; k < n && !bad; ++k) {
+            const uint64_t w = rs.word();
+            T.W[o + k] = WormRec{wkey(offs[k], int(w & 1), s0 ^ 1 ^ (k & 1)), w >> 1, uint16_t(li), kNone, 0u};
+          }
+        }
+      } else {
+        T.base[li] = 0;
+        for (int k = 0; k < nl && !bad; ++k) {
+          const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
+          const uint64_t M = wpts(kpk(lo), kpk(hi));
+          const int p = kab(lo), sigma = p ^ kbl(hi);
+          const int n = sample_worms<kMaxWormsPerInterval>(rs, M, sigma, d.SW, d.SWI, offs, &bad);
+          if (bad || n <= 0) continue;
+          const int o = atomicAdd(&misc->nworms, n);
+          if (o + n > d.wcap) { bad = PMWA_ECAPACITY; break; }
+          const uint64_t m0 = wm_above(kpk(lo));
+          for (int j = 0; j < n; ++j) {
+            const uint64_t w = rs.word();
+            T.W[o + j] = WormRec{wkey((m0 + offs[j]) & (kTwo59 - 1), int(w & 1), p ^ 1 ^ (j & 1)), w >> 1,
+                                 uint16_t(li), uint16_t(st + k), 0u};
+          }
+        }
+      }
+      if (bad) tile_fail(misc, bad, 4);
+    }
+    __syncthreads();
+    phase_tick(d, 2, tclk);
+    if (misc->err) goto fail;
+
+    // ---- phase 4: Step 5
+    if (stop >= 5) {
+      const int nw = misc->nworms;
+      for (int pass = 0; pass < d.n_cycle; ++pass) {
+        for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
+        __syncthreads();
+        const int q = pass & 3;
+        for (int w = tid; w < nw; w += NT) atomicAdd(&T.bkt[T.sub[T.W[w].site * 4 + q]], 1);
+        __syncthreads();
+        block_scan(T.bkt, T.nsub, wsum);
+        for (int u = tid; u < T.nsub; u += NT) T.fill[u] = T.bkt[u];
+        __syncthreads();
+        for (int w = tid; w < nw; w += NT) {
+          const int u = T.sub[T.W[w].site * 4 + q];
+          const int at = atomicAdd(&T.fill[u], 1);
+          T.idx[at] = uint16_t(w);
+          T.posu[at] = uint16_t(u);
+        }
+        __syncthreads();
+        // label order inside every sub-block (ties: site, time)
+        for (int u = tid; u < T.nsub; u += NT) {
+          uint16_t* seg = T.idx + T.bkt[u];
+          const int n = T.bkt[u + 1] - T.bkt[u];
+          for (int p = 1; p < n; ++p) {
+            const uint16_t v = seg[p];
+            int r = p - 1;
+            while (r >= 0 && worm_less(T.W[v], T.W[seg[r]])) { seg[r + 1] = seg[r]; --r; }
+            seg[r + 1] = v;
+          }
+        }
+        // the r-th move of sub-block u draws Philox block r of stream
+        // (unit = domain * n_sub + u, scatter | pass): all of them up front
+        const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
+        for (int p = tid; p < nw; p += NT) {
+          const int u = T.posu[p];
+          const P4 b = philox(uint32_t(p - T.bkt[u]), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+          T.rw[2 * p] = uint64_t(b.x) | (uint64_t(b.y) << 32);
+          T.rw[2 * p + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+        }
+        __syncthreads();
+        for (int u = tid; u < T.nsub; u += NT) {
+          const int lo = T.bkt[u], n = T.bkt[u + 1] - lo;
+          const uint16_t* seg = T.idx + lo;
+          for (int r = 0; r < n; ++r) {
+            const int rc = tile_move(T, seg, n, r, q, T.rw[2 * (lo + r)], T.rw[2 * (lo + r) + 1]);
+            if (rc) { tile_fail(misc, rc, 5); break; }
+          }
+        }
+        __syncthreads();
+        if (misc->err) goto fail;
+      }
+      phase_tick(d, 3, tclk);
+    }
+  }
+
+  // ---- phase 5: next configuration + Step 6
+  {
+    const int nw = (stop >= 4) ? misc->nworms : 0;
+    if (stop >= 4) {
+      for (int li = tid; li <= nds; li += NT) T.bkt[li] = 0;
+      __syncthreads();
+      for (int w = tid; w < nw; w += NT) atomicAdd(&T.bkt[T.W[w].site], 1);
+      __syncthreads();
+      block_scan(T.bkt, nds, wsum);
+      for (int li = tid; li < nds; li += NT) T.fill[li] = T.bkt[li];
+      __syncthreads();
+      for (int w = tid; w < nw; w += NT) T.idx[atomicAdd(&T.fill[T.W[w].site], 1)] = uint16_t(w);
+      __syncthreads();
+    }
+    uint64_t nv = 0, nk = 0, nwc = 0, olo = 0, ohi = 0;
+    double q = 0.0;
+    for (int li = tid; li < nds; li += NT) {
+      const int s = T.gsite(li);
+      const int st = T.off[li], nl = T.off[li + 1] - st;
+      uint64_t* OUT = d.keyB + size_t(s) * d.cap;
+      const uint64_t* KO = d.keyA + size_t(s) * d.cap;
+      const int nO = cnt_n(d.cntA[s]);
+      uint16_t* seg = nullptr;
+      int nws = 0;
+      if (stop >= 4) {
+        seg = T.idx + T.bkt[li];
+        nws = T.bkt[li + 1] - T.bkt[li];
+        for (int p = 1; p < nws; ++p) {  // worms of the site in time order
+          const uint16_t v = seg[p];
+          int r = p - 1;
+          while (r >= 0 && T.W[v].key < T.W[seg[r]].key) { seg[r + 1] = seg[r]; --r; }
+          seg[r + 1] = v;
+        }
+      }
+      // merge legs with worms (stop 3: the old worms)
+      int il = 0, iw = 0, io = 0, no = 0;
+      bool bad = false;
+      for (;;) {
+        uint64_t wk = ~0ull;
+        if (stop >= 4) { if (iw < nws) wk = T.W[seg[iw]].key; }
+        else {
+          while (io < nO && !kworm(KO[io])) ++io;
+          if (io < nO) wk = KO[io];
+        }
+        const uint64_t lk = il < nl ? T.leg[st + il] : ~0ull;
+        if (lk == ~0ull && wk == ~0ull) break;
+        uint64_t key;
+        if (kpk(lk) < kpk(wk) || wk == ~0ull) { key = lk; ++il; }
+        else { key = wk; if (stop >= 4) ++iw; else ++io; }
+        if (no >= d.cap) { bad = true; break; }
+        OUT[no++] = key;
+      }
+      if (bad) { tile_fail(misc, PMWA_ECAPACITY, 6); continue; }
+      int base;
+      if (no) base = kab(OUT[no - 1]);
+      else base = (stop >= 4) ? T.base[li] : cnt_base(d.cntA[s]);
+      d.cntB[s] = uint32_t(no) | (uint32_t(base) << 31);
+      if (stop < 6) continue;
+      // Step 6 counters of this site
+      if (no == 0 && base) olo += kTwo62;
+      for (int k = 0; k < no; ++k) {
+        const uint64_t key = OUT[k];
+        const uint64_t nx = kpk(OUT[k + 1 == no ? 0 : k + 1]);
+        const uint64_t len = (no == 1) ? kTwo62 : ((nx - kpk(key)) & kMask62);
+        if (kab(key)) olo += len;
+      }
+      nwc += uint64_t(no - nl);
+      for (int k = 0; k < nl; ++k) {
+        const uint64_t key = T.leg[st + k];
+        int dir;
+        if (leg_lower(d, s, ktag(key), &dir) == s) { ++nv; if (kab(key) != kbl(key)) ++nk; }
+      }
+      if (nl == 0) {
+        q += xg_sigma(0, double(kTwo59) * d.XW);
+      } else {
+        double qs = 0.0;
+        for (int k = 0; k < nl; ++k) {
+          const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
+          qs += xg_sigma(kab(lo) ^ kbl(hi), __ull2double_rn(wpts(kpk(lo), kpk(hi))) * d.XW);
+        }
+        q += qs;
+      }
+    }
+    if (stop >= 6) {
+      for (int o = 16; o > 0; o >>= 1) {
+        nv += __shfl_down_sync(0xffffffffu, nv, o);
+        nk += __shfl_down_sync(0xffffffffu, nk, o);
+        nwc += __shfl_down_sync(0xffffffffu, nwc, o);
+        const uint64_t blo = __shfl_down_sync(0xffffffffu, olo, o);
+        const uint64_t bhi = __shfl_down_sync(0xffffffffu, ohi, o);
+        add128(olo, ohi, blo, bhi);
+        q += __shfl_down_sync(0xffffffffu, q, o);
+      }
+      if ((tid & 31) == 0) {
+        pmwa_row* r = d.rows + d.row;
+        if (nv) atomicAdd(reinterpret_cast<unsigned long long*>(&r->n_v), (unsigned long long)nv);
+        if (nk) atomicAdd(reinterpret_cast<unsigned long long*>(&r->n_k), (unsigned long long)nk);
+        if (nwc) atomicAdd(reinterpret_cast<unsigned long long*>(&r->n_w), (unsigned long long)nwc);
+        if (olo | ohi) {
+          const unsigned long long old =
+              atomicAdd(reinterpret_cast<unsigned long long*>(&r->occ_lo), (unsigned long long)olo);
+          const uint64_t carry = (old + olo < old) ? 1 : 0;
+          if (ohi + carry)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&r->occ_hi), (unsigned long long)(ohi + carry));
+        }
+        atomicAdd(&r->q_impr, q);
+      }
+      if (dom == 0 && tid == 0) d.rows[d.row].sweep = d.sweep;
+    }
+    __syncthreads();
+    phase_tick(d, 4, tclk);
+    if (misc->err) goto fail;
+  }
+  return;
+fail:
+  if (tid == 0) set_err(d.err, misc->err, misc->where);
+}
+
+// ---------------------------------------------------------------------------
+bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
+  const int nds = d->dom_x * d->dom_y;
+  const int nsub = sb_slots_host(d->dom_x, d->sub_block, d->ndx) * sb_slots_host(d->dom_y, d->sub_block, d->ndy);
+  const int nb = std::max(nsub, nds) + 1;
+  auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  size_t o = 0;
+  d->sm_th = int(o); o = up16(o + 256 * sizeof(uint64_t));
+  d->sm_off = int(o); o = up16(o + size_t(nds + 1) * sizeof(int));
+  d->sm_base = int(o); o = up16(o + size_t(nds));
+  d->sm_bcnt = int(o); o = up16(o + size_t(2 * nds) * sizeof(int));
+  d->sm_boff = int(o); o = up16(o + size_t(2 * nds) * sizeof(int));
+  d->sm_misc = int(o); o = up16(o + sizeof(Misc));
+  d->sm_nbr = int(o); o = up16(o + size_t(6 * nds) * sizeof(int16_t));
+  d->sm_sub = int(o); o = up16(o + size_t(4 * nds) * sizeof(uint16_t));
+  const size_t fixed = o;
+  // worm side of the union: table, index, two bucket arrays
+  const size_t worm_bytes = [&](int wcap) {
+    return up16(size_t(wcap) * sizeof(WormRec)) + 2 * up16(size_t(wcap) * 2) + up16(size_t(wcap) * 16) +
+           2 * up16(size_t(nb) * sizeof(int));
+  }(d->wcap);
+  const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
+  const size_t uni = std::max(worm_bytes, pool_bytes);
+  const long long room = (long long)kSmemLimit - 1024 - (long long)fixed - (long long)uni;
+  if (room < 8 * 64) return false;
+  const long long want = (long long)(1.1 * legs_per_site * nds) + 256;
+  d->legcap = int(std::min<long long>(std::min<long long>(want, room / 8), 65000));
+  d->sm_leg = int(o); o = up16(o + size_t(d->legcap) * sizeof(uint64_t));
+  d->sm_pool = int(o);
+  d->sm_worm = int(o);
+  size_t w = o + up16(size_t(d->wcap) * sizeof(WormRec));
+  d->sm_idx = int(w); w = up16(w + size_t(d->wcap) * 2);
+  d->sm_posu = int(w); w = up16(w + size_t(d->wcap) * 2);
+  d->sm_rw = int(w); w = up16(w + size_t(d->wcap) * 16);
+  d->sm_bkt = int(w); w = up16(w + size_t(nb) * sizeof(int));
+  d->sm_fill = int(w); w = up16(w + size_t(nb) * sizeof(int));
+  o = std::max(w, o + pool_bytes);
+  d->sm_total = int(o);
+  (void)cands_per_bond;
+  return d->sm_total <= kSmemLimit - 1024;
+}
+
+int upload_zig_tile(const Zig& z) { return upload_constants(z); }
+
+int launch_tile(const Dev& d, int stop, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+  if (e) return int(e);
+  k_tile<<<d.ndom, kTileThreads, d.sm_total, cudaStream_t(stream)>>>(d, stop);
+  return int(cudaGetLastError());
+}
+
+}  // namespace pmwa

@@ -189,7 +189,8 @@ def pmwa_profile_read(h):
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
 
 
-PHASES = ("vertex_candidates", "leg_merge", "worm_creation", "scatter", "output_measure")
+PHASES = ("vertex_candidates", "leg_merge", "worm_creation", "scatter", "output_measure",
+          "scatter_pass_setup", "scatter_moves")
 
 
 def pmwa_profile_phases(h):

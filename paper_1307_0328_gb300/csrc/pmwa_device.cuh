@@ -151,23 +151,46 @@ __device__ inline double xg_sigma(int sigma, double x) {
 }
 
 // ---------------------------------------------------------------------------
+// Ziggurat tables as seen by a kernel: a copy in shared memory, because the
+// strip index differs from lane to lane (constant memory would serialise).
+struct ZigTab {
+  const double* W;             // [256] strip width / 2^53
+  const unsigned long long* K; // [256] inner-rectangle threshold
+  const double* F;             // [257] e^-X at the strip edges
+  double R;                    // start of the tail
+};
+constexpr int kZigBytes = 256 * 8 + 256 * 8 + 257 * 8;
+
+// copy the tables into `buf` (kZigBytes, 8-byte aligned); all threads
+// participate; the caller synchronises before use
+__device__ inline ZigTab zig_stage(unsigned char* buf) {
+  double* W = reinterpret_cast<double*>(buf);
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(buf + 256 * 8);
+  double* F = reinterpret_cast<double*>(buf + 512 * 8);
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) {
+    if (i < 256) { W[i] = c_zW[i]; K[i] = c_zK[i]; }
+    F[i] = c_zF[i];
+  }
+  return ZigTab{W, K, F, c_zR};
+}
+
 // Unit exponential from the ziggurat of Marsaglia and Tsang (2000): strip i
 // from the low 8 bits of a word, a 53-bit uniform u from its high bits,
 // x = u W[i]; accept when u < K[i]; strip 0 past R restarts at R + new
 // deviate; else a wedge test y < e^-x with a second word.  <= 64 words.
-__device__ inline double zig_exp(Stream& s, int* bad) {
+__device__ inline double zig_exp(const ZigTab& z, Stream& s, int* bad) {
   double acc = 0.0;
   for (int tries = 0; tries < 64; ++tries) {
     const uint64_t w = s.word();
     const unsigned i = unsigned(w & 255u);
     const uint64_t u = w >> 11;
-    const double x = __dmul_rn(__ull2double_rn(u), c_zW[i]);
-    if (u < c_zK[i]) return __dadd_rn(acc, x);
-    if (i == 0) { acc = __dadd_rn(acc, c_zR); continue; }
+    const double x = __dmul_rn(__ull2double_rn(u), z.W[i]);
+    if (u < z.K[i]) return __dadd_rn(acc, x);
+    if (i == 0) { acc = __dadd_rn(acc, z.R); continue; }
     const uint64_t w2 = s.word();
     const double t1 = __dmul_rn(__ull2double_rn(w2 >> 11), 0x1p-53);
-    const double t2 = __dsub_rn(c_zF[i + 1], c_zF[i]);
-    const double y = __dadd_rn(c_zF[i], __dmul_rn(t1, t2));
+    const double t2 = __dsub_rn(z.F[i + 1], z.F[i]);
+    const double y = __dadd_rn(z.F[i], __dmul_rn(t1, t2));
     if (y < exp_det(-x)) return __dadd_rn(acc, x);
   }
   *bad = PMWA_ETIMEOUT;
@@ -189,7 +212,7 @@ __device__ __forceinline__ uint64_t grid_gap(double E, double scale) {
 // odd, the extra worm uniform on the interval (a clash rejects).  Returns the
 // count (offsets sorted in offs[0..n)), or -1 with *bad set.
 template <int MAXN>
-__device__ int sample_worms(Stream& s, uint64_t M, int sigma, double SW, uint64_t SWI,
+__device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, double SW, uint64_t SWI,
                             uint64_t* offs, int* bad) {
   if (M == 0) { if (sigma) { *bad = PMWA_EINVARIANT; return -1; } return 0; }
   for (int tries = 0; tries < 128; ++tries) {
@@ -197,7 +220,7 @@ __device__ int sample_worms(Stream& s, uint64_t M, int sigma, double SW, uint64_
     bool first = true;
     uint64_t pos = 0;
     for (;;) {
-      const double E = zig_exp(s, bad);
+      const double E = zig_exp(z, s, bad);
       const uint64_t g = grid_gap(E, SW);
       const uint64_t nxt = first ? g - 1 : pos + g;
       first = false;

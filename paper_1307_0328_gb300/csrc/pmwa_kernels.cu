@@ -90,7 +90,7 @@ __device__ __forceinline__ void aslot_insert(uint64_t* K, int n, int at, uint64_
 
 // erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
 // and draw new ones with end states p (above lo) and q (below hi).
-__device__ int regen_interval(const Dev& d, Stream& st, int x, uint64_t lo, uint64_t hi, int p, int q) {
+__device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, int x, uint64_t lo, uint64_t hi, int p, int q) {
   uint64_t* K = d.keyA + size_t(x) * d.cap;
   int n = cnt_n(d.cntA[x]);
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
@@ -101,7 +101,7 @@ __device__ int regen_interval(const Dev& d, Stream& st, int x, uint64_t lo, uint
   }
   uint64_t offs[kMaxWormsPerInterval];
   int bad = 0;
-  const int nw = sample_worms<kMaxWormsPerInterval>(st, wpts(lo, hi), p ^ q, d.SW, d.SWI, offs, &bad);
+  const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SW, d.SWI, offs, &bad);
   if (bad) { d.cntA[x] = cnt_make(n, cnt_base(d.cntA[x])); return bad; }
   const uint64_t m0 = wm_above(lo);
   for (int k = 0; k < nw; ++k) {
@@ -120,6 +120,9 @@ __device__ __forceinline__ double em1_of(uint64_t I, double XW) {
 }
 
 __global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
+  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
+  const ZigTab Z = zig_stage(zbuf);
+  __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   int a;
   if (dir == 0) {
@@ -183,12 +186,12 @@ __global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
       KA[ka] = (KA[ka] & ~3ull) | (uint64_t(s0) << 1) | uint64_t(s2);
       KB[kb] = (KB[kb] & ~3ull) | (uint64_t(s1) << 1) | uint64_t(s3);
     }
-    if (!La.single) rc = regen_interval(d, st, a, La.plo, pv, La.far_dn, s0);
-    if (!rc && !Lb.single) rc = regen_interval(d, st, b, Lb.plo, pv, Lb.far_dn, s1);
-    if (!rc) rc = La.single ? regen_interval(d, st, a, pv, pv, s2, s0)
-                            : regen_interval(d, st, a, pv, La.phi, s2, La.far_up);
-    if (!rc) rc = Lb.single ? regen_interval(d, st, b, pv, pv, s3, s1)
-                            : regen_interval(d, st, b, pv, Lb.phi, s3, Lb.far_up);
+    if (!La.single) rc = regen_interval(d, Z, st, a, La.plo, pv, La.far_dn, s0);
+    if (!rc && !Lb.single) rc = regen_interval(d, Z, st, b, Lb.plo, pv, Lb.far_dn, s1);
+    if (!rc) rc = La.single ? regen_interval(d, Z, st, a, pv, pv, s2, s0)
+                            : regen_interval(d, Z, st, a, pv, La.phi, s2, La.far_up);
+    if (!rc) rc = Lb.single ? regen_interval(d, Z, st, b, pv, pv, s3, s1)
+                            : regen_interval(d, Z, st, b, pv, Lb.phi, s3, Lb.far_up);
     if (rc) break;
   }
   // Step 3 on this bond: erase its diagonal vertices, lay new ones
@@ -210,7 +213,7 @@ __global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
       const int baseA = cnt_base(d.cntA[a]), baseB = cnt_base(d.cntA[b]);
       int bad = 0;
       for (;;) {
-        const double E = zig_exp(sv, &bad);
+        const double E = zig_exp(Z, sv, &bad);
         if (bad) { rc = bad; break; }
         const uint64_t g = grid_gap(E, d.SV);
         const uint64_t nxt = first ? g - 1 : pos + g;

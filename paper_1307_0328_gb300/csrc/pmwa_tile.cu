@@ -99,6 +99,7 @@ struct Tile {
   int* boff;       // [2 nds] their start in pool[]
   Misc* misc;
   uint64_t* leg;   // [legcap]
+  uint8_t* wcnt;   // [legcap] worms in the interval just above each leg
   uint64_t* pool;  // [poolcap] (aliases the worm table)
   WormRec* W;      // [wcap]
   uint16_t* idx;   // [wcap]
@@ -107,6 +108,7 @@ struct Tile {
   int* bkt;        // [max(nsub, nds) + 1]
   int* fill;       // [max(nsub, nds)]
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
+  uint8_t* tinfo;  // [6 nds] per leg tag: 1 = lower site of the bond, 2 = bond leaves the domain
   uint16_t* sub;   // [4 nds] sub-block of each site for offset pattern pass & 3
   int x0, y0, nds, nsub;
 
@@ -124,7 +126,7 @@ struct Tile {
 
 // ---------------------------------------------------------------------------
 // phase 1: Step 3 candidates of bond (a, dir) from the current configuration
-__device__ int bond_candidates(const Dev& d, int a, int dir, uint64_t* buf, int cap, int* bad) {
+__device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, uint64_t* buf, int cap, int* bad) {
   const int b = site_step(d, a, dir, +1);
   const uint64_t tag = uint64_t(bond_tag(d, a, dir));
   const uint64_t* KA = d.keyA + size_t(a) * d.cap;
@@ -137,7 +139,7 @@ __device__ int bond_candidates(const Dev& d, int a, int dir, uint64_t* buf, int 
   uint64_t pos = 0;
   bool first = true;
   for (;;) {
-    const double E = zig_exp(s, bad);
+    const double E = zig_exp(z, s, bad);
     if (*bad) break;
     const uint64_t g = grid_gap(E, d.SV);
     const uint64_t nxt = first ? g - 1 : pos + g;
@@ -162,12 +164,10 @@ __device__ int bond_candidates(const Dev& d, int a, int dir, uint64_t* buf, int 
 }
 
 // old event kept by Step 3: a kink, or any leg of a bond between domains
-__device__ __forceinline__ bool kept_leg(const Dev& d, int s, uint64_t k) {
+__device__ __forceinline__ bool kept_leg(const uint8_t* tinfo6, uint64_t k) {
   if (kworm(k)) return false;
   if (kab(k) != kbl(k)) return true;
-  int dir;
-  const int a = leg_lower(d, s, ktag(k), &dir);
-  return boundary_bond(d, a, dir);
+  return (tinfo6[ktag(k)] & 2) != 0;
 }
 
 // the four bonds of local site li: (s,x) (s,y) with s the lower site, then
@@ -218,11 +218,13 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   const uint64_t pL = kpk(T.leg[L]);
   const uint64_t my = (kpk(key) - pL) & kMask62;
   const uint32_t self = uint32_t(li) | (uint32_t(L) << 16);
-  for (int k = 0; k < n; ++k) {
-    const WormRec& o = T.W[seg[k]];
-    if (k == r || site_leg(o) != self) continue;
-    const uint64_t off = (kpk(o.key) - pL) & kMask62;
-    if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
+  if (T.wcnt[L] > 1) {  // other worms share the interval: is one of them ahead?
+    for (int k = 0; k < n; ++k) {
+      const WormRec& o = T.W[seg[k]];
+      if (k == r || site_leg(o) != self) continue;
+      const uint64_t off = (kpk(o.key) - pL) & kMask62;
+      if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
+    }
   }
   const int iv = up ? ((L + 1 == en) ? st : L + 1) : L;
   const uint64_t pv = kpk(T.leg[iv]);
@@ -247,11 +249,14 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   bool fa = false, fb = false;
   const uint32_t ka_up = uint32_t(al) | (uint32_t(ia) << 16), kb_up = uint32_t(bl) | (uint32_t(ib) << 16);
   const uint32_t ka_dn = uint32_t(al) | (uint32_t(ia_dn) << 16), kb_dn = uint32_t(bl) | (uint32_t(ib_dn) << 16);
-  for (int k = 0; k < n; ++k) {
+  // worms (other than this one) in the four intervals around v?
+  int others = T.wcnt[ia] + T.wcnt[ib] + (ia_dn != ia ? T.wcnt[ia_dn] : 0) + (ib_dn != ib ? T.wcnt[ib_dn] : 0) - 1;
+  for (int k = 0; k < n && others > 0; ++k) {
     if (k == r) continue;
     const WormRec& o = T.W[seg[k]];
     const uint32_t sl = site_leg(o);
     if (sl != ka_up && sl != kb_up && sl != ka_dn && sl != kb_dn) continue;
+    --others;
     const uint64_t po = kpk(o.key);
     if (sl == ka_up) { const uint64_t x = (po - pv) & kMask62; if (x < ua) ua = x; }
     if (sl == kb_up) { const uint64_t x = (po - pv) & kMask62; if (x < ub) ub = x; }
@@ -281,6 +286,7 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   const uint64_t vx = T.leg[ix];
   const uint64_t Lj = (j == 0) ? L0 : (j == 1) ? L1 : (j == 2) ? L2 : L3;
   const uint64_t o = __umul64hi(w1, Lj);
+  T.wcnt[L] -= 1;
   if (j >= 2) {
     w.key = wkey((wm_above(pv) + o) & (kTwo59 - 1), 1, kab(vx) ^ 1);
     w.leg = uint16_t(ix);
@@ -288,6 +294,7 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
     w.key = wkey((wm_below(pv) + kTwo59 - o) & (kTwo59 - 1), 0, kbl(vx));
     w.leg = uint16_t((j & 1) ? ib_dn : ia_dn);
   }
+  T.wcnt[w.leg] += 1;
   w.site = uint16_t((j & 1) ? bl : al);
   return PMWA_OK;
 }
@@ -329,6 +336,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
   T.boff = reinterpret_cast<int*>(sm + d.sm_boff);
   T.misc = reinterpret_cast<Misc*>(sm + d.sm_misc);
   T.leg = reinterpret_cast<uint64_t*>(sm + d.sm_leg);
+  T.wcnt = reinterpret_cast<uint8_t*>(sm + d.sm_wcnt);
   T.pool = reinterpret_cast<uint64_t*>(sm + d.sm_pool);
   T.W = reinterpret_cast<WormRec*>(sm + d.sm_worm);
   T.idx = reinterpret_cast<uint16_t*>(sm + d.sm_idx);
@@ -337,6 +345,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
   T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
   T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
+  T.tinfo = reinterpret_cast<uint8_t*>(sm + d.sm_tinfo);
   T.sub = reinterpret_cast<uint16_t*>(sm + d.sm_sub);
   const int dom = blockIdx.x;
   T.x0 = (dom % d.ndx) * d.dom_x;
@@ -347,18 +356,22 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
   Misc* misc = T.misc;
 
   long long tclk = clock64();
+  const ZigTab Z = zig_stage(sm + d.sm_zig);
   for (int k = tid; k < 256; k += NT) T.th[k] = d.TH[k];
   if (tid == 0) { misc->pool_used = 0; misc->nworms = 0; misc->err = 0; misc->where = 0; }
   // per-site tables: bond partners by leg tag, sub-blocks by offset pattern
   for (int li = tid; li < nds; li += NT) {
-    for (int t = 0; t < 6; ++t) T.nbr[li * 6 + t] = -1;
+    for (int t = 0; t < 6; ++t) { T.nbr[li * 6 + t] = -1; T.tinfo[li * 6 + t] = 0; }
     const int s = T.gsite(li);
     for (int j = 0; j < 4; ++j) {
       const int dir = j & 1;
       const int a = (j < 2) ? s : site_step(d, s, dir, -1);
-      if (boundary_bond(d, a, dir)) continue;
+      const int tg = bond_tag(d, a, dir);
+      const bool out = boundary_bond(d, a, dir);
+      T.tinfo[li * 6 + tg] = uint8_t((j < 2 ? 1 : 0) | (out ? 2 : 0));
+      if (out) continue;
       const int other = (j < 2) ? site_step(d, s, dir, +1) : a;
-      T.nbr[li * 6 + bond_tag(d, a, dir)] = int16_t((T.lsite(other) << 1) | (j < 2 ? 1 : 0));
+      T.nbr[li * 6 + tg] = int16_t((T.lsite(other) << 1) | (j < 2 ? 1 : 0));
     }
     for (int q = 0; q < 4; ++q) T.sub[li * 4 + q] = uint16_t(T.sub_of(li, q));
   }
@@ -371,7 +384,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
     uint64_t buf[kMaxCandPerBond];
     int n = 0, bad = 0;
     if (d.has_vertices && !boundary_bond(d, a, dir))
-      n = bond_candidates(d, a, dir, buf, min(d.capb, kMaxCandPerBond), &bad);
+      n = bond_candidates(d, Z, a, dir, buf, min(d.capb, kMaxCandPerBond), &bad);
     if (bad) { tile_fail(misc, bad, 31); n = 0; }
     int o = 0;
     if (n) {
@@ -392,7 +405,8 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
     const uint64_t* KO = d.keyA + size_t(s) * d.cap;
     const int nO = cnt_n(d.cntA[s]);
     int c = 0;
-    for (int k = 0; k < nO; ++k) c += kept_leg(d, s, KO[k]);
+    const uint8_t* ti = T.tinfo + li * 6;
+    for (int k = 0; k < nO; ++k) c += kept_leg(ti, KO[k]);
     int lb[4];
     site_bonds(T, li, lb);
     for (int j = 0; j < 4; ++j) if (lb[j] >= 0) c += T.bcnt[lb[j]];
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
     for (int j = 0; j < 4; ++j) cn[j] = lb[j] >= 0 ? T.bcnt[lb[j]] : 0;
     int io = 0, o = T.off[li];
     for (;;) {
-      while (io < nO && !kept_leg(d, s, KO[io])) ++io;
+      while (io < nO && !kept_leg(T.tinfo + li * 6, KO[io])) ++io;
       uint64_t best = ~0ull;
       int src = -1;
       if (io < nO) { best = kpk(KO[io]); src = 4; }
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
       if (nl == 0) {
         const int s0 = int(rs.word() >> 63);
         T.base[li] = uint8_t(s0);
-        const int n = sample_worms<kMaxWormsPerInterval>(rs, kTwo59, 0, d.SW, d.SWI, offs, &bad);
+        const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, kTwo59, 0, d.SW, d.SWI, offs, &bad);
         if (!bad && n > 0) {
           const int o = atomicAdd(&misc->nworms, n);
           if (o + n > d.wcap) bad = PMWA_ECAPACITY;
@@ -461,7 +475,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
           const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
           const uint64_t M = wpts(kpk(lo), kpk(hi));
           const int p = kab(lo), sigma = p ^ kbl(hi);
-          const int n = sample_worms<kMaxWormsPerInterval>(rs, M, sigma, d.SW, d.SWI, offs, &bad);
+          const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, M, sigma, d.SW, d.SWI, offs, &bad);
+          T.wcnt[st + k] = uint8_t(n > 0 ? min(n, 255) : 0);
+          if (n > 255) bad = PMWA_ECAPACITY;
           if (bad || n <= 0) continue;
           const int o = atomicAdd(&misc->nworms, n);
           if (o + n > d.wcap) { bad = PMWA_ECAPACITY; break; }
@@ -519,6 +535,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
           T.rw[2 * p + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
         }
         __syncthreads();
+        phase_tick(d, 5, tclk);
         for (int u = tid; u < T.nsub; u += NT) {
           const int lo = T.bkt[u], n = T.bkt[u + 1] - lo;
           const uint16_t* seg = T.idx + lo;
@@ -528,6 +545,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
           }
         }
         __syncthreads();
+        phase_tick(d, 6, tclk);
         if (misc->err) goto fail;
       }
       phase_tick(d, 3, tclk);
@@ -603,8 +621,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
       nwc += uint64_t(no - nl);
       for (int k = 0; k < nl; ++k) {
         const uint64_t key = T.leg[st + k];
-        int dir;
-        if (leg_lower(d, s, ktag(key), &dir) == s) { ++nv; if (kab(key) != kbl(key)) ++nk; }
+        if (T.tinfo[li * 6 + ktag(key)] & 1) { ++nv; if (kab(key) != kbl(key)) ++nk; }
       }
       if (nl == 0) {
         q += xg_sigma(0, double(kTwo59) * d.XW);
@@ -660,6 +677,7 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
   size_t o = 0;
   d->sm_th = int(o); o = up16(o + 256 * sizeof(uint64_t));
+  d->sm_zig = int(o); o = up16(o + size_t(kZigBytes));
   d->sm_off = int(o); o = up16(o + size_t(nds + 1) * sizeof(int));
   d->sm_base = int(o); o = up16(o + size_t(nds));
   d->sm_bcnt = int(o); o = up16(o + size_t(2 * nds) * sizeof(int));
@@ -667,6 +685,7 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   d->sm_misc = int(o); o = up16(o + sizeof(Misc));
   d->sm_nbr = int(o); o = up16(o + size_t(6 * nds) * sizeof(int16_t));
   d->sm_sub = int(o); o = up16(o + size_t(4 * nds) * sizeof(uint16_t));
+  d->sm_tinfo = int(o); o = up16(o + size_t(6 * nds));
   const size_t fixed = o;
   // worm side of the union: table, index, two bucket arrays
   const size_t worm_bytes = [&](int wcap) {
@@ -678,8 +697,9 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   const long long room = (long long)kSmemLimit - 1024 - (long long)fixed - (long long)uni;
   if (room < 8 * 64) return false;
   const long long want = (long long)(1.1 * legs_per_site * nds) + 256;
-  d->legcap = int(std::min<long long>(std::min<long long>(want, room / 8), 65000));
+  d->legcap = int(std::min<long long>(std::min<long long>(want, room / 9 - 16), 65000));
   d->sm_leg = int(o); o = up16(o + size_t(d->legcap) * sizeof(uint64_t));
+  d->sm_wcnt = int(o); o = up16(o + size_t(d->legcap));
   d->sm_pool = int(o);
   d->sm_worm = int(o);
   size_t w = o + up16(size_t(d->wcap) * sizeof(WormRec));

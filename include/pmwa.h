@@ -122,6 +122,19 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
    legs) that holds tau_k on site i.  host_out holds N*K doubles. */
 int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out);
 
+/* The same values as pmwa_rho_slices, for callers that cannot allocate
+   device memory while they run (for example a serving loop whose memory is
+   owned by another allocator, or one that has promised its pool no new
+   blocks): the device scratch of this call is a fixed array inside the
+   library, not the caller's arena, and nothing is allocated or freed.  The
+   paper has no counterpart.  Limit: N*K <= 2^20 doubles (8 MiB, held on every
+   GPU that loads the library until exit); larger requests return
+   PMWA_EINVAL.  The handle's device must be current.  The first call on a
+   device looks up the array's device address; make that first call before
+   any stream capture.  Calls that overlap on the GPU share the array and
+   race; each call overwrites every value it returns. */
+int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out);
+
 /* Canonical configuration (format in the header comment) to / from host
    memory.  pmwa_export_bytes gives the size; pmwa_import checks the
    invariants and the per-site capacity. */

@@ -62,6 +62,7 @@ def load(build=True):
         "pmwa_tile": (C.c_int, [vp, C.c_int32]),
         "pmwa_measure": (C.c_int, [vp, vp, C.c_int64, P(C.c_int64)]),
         "pmwa_rho_slices": (C.c_int, [vp, C.c_int32, vp]),
+        "pmwa_rho_slices_static": (C.c_int, [vp, C.c_int32, vp]),
         "pmwa_export_bytes": (C.c_int, [vp, P(sz)]),
         "pmwa_export": (C.c_int, [vp, vp, sz]),
         "pmwa_import": (C.c_int, [vp, vp, sz]),
@@ -140,6 +141,13 @@ def pmwa_measure(h, max_rows=1 << 20):
 def pmwa_rho_slices(h, N, K):
     out = np.zeros((N, K), dtype=np.float64)
     _check("pmwa_rho_slices", load().pmwa_rho_slices(h, K, out.ctypes.data))
+    return out
+
+
+def pmwa_rho_slices_static(h, N, K):
+    """rho slices with the library's own fixed device scratch (no allocation)."""
+    out = np.zeros((N, K), dtype=np.float64)
+    _check("pmwa_rho_slices_static", load().pmwa_rho_slices_static(h, K, out.ctypes.data))
     return out
 
 

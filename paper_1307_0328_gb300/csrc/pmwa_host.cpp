@@ -30,6 +30,7 @@ struct pmwa_handle {
   uint64_t TH[256];
   DevErr* err;
   unsigned long long* phase;  // device phase-cycle counters
+  int device;                 // CUDA device current at pmwa_create
   bool profiling = false;
   std::vector<Timed> timed;            // events of launches not yet read
   std::vector<cudaEvent_t> event_pool;  // spare events
@@ -357,6 +358,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   h->p = *p;
   h->stream = static_cast<cudaStream_t>(stream);
   h->sweep = 0;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return PMWA_ECUDA; }
   h->rows_cap = p->rows_cap ? p->rows_cap : 4096;
   h->rows_pending = 0;
   std::memcpy(h->TH, g.TH, sizeof g.TH);
@@ -537,6 +539,15 @@ int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
   if (cudaMemcpy(host_out, dev, size_t(h->d.N) * size_t(K) * sizeof(double), cudaMemcpyDeviceToHost))
     return PMWA_ECUDA;
   return PMWA_OK;
+}
+
+int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out) {
+  if (!h) return PMWA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PMWA_ECUDA;
+  if (dev != h->device) return PMWA_EINVAL;  // the handle's device must be current
+  if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
+  return rho_slices_static(h->d, K, host_out, h->stream);
 }
 
 int pmwa_get_sweep(pmwa_handle* h, uint64_t* s) {

@@ -71,6 +71,8 @@ int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_tile(const Dev& d, int stop, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
+// rho slices through the library's own static device scratch (no allocation)
+int rho_slices_static(const Dev& d, int K, double* host_out, void* stream);
 // shared-memory plan of the tile kernel for this instance (fills the sm_*
 // offsets); returns false if a domain cannot fit in shared memory.
 bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond);

@@ -10,6 +10,8 @@
 // of 64-bit event keys sorted in time, and cnt[i] = count | base << 31.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "pmwa_device.cuh"
 
 namespace pmwa {
@@ -253,6 +255,48 @@ int launch_boundary(const Dev& d, int dir, void* stream) {
   if ((dir == 0 && d.ndx < 2) || (dir == 1 && d.ndy < 2)) return 0;
   k_boundary<<<blocks_for(n, 64), 64, 0, cudaStream_t(stream)>>>(d, dir);
   return int(cudaGetLastError());
+}
+
+// Scratch of pmwa_rho_slices_static: the rho values of one call live here
+// between the kernel and the copy to the host, instead of in the caller's
+// arena.  Every GPU that loads the library holds this array until the
+// process exits.  Calls that overlap on the GPU share it and race; each call
+// overwrites all N*K values it returns, so nothing needs clearing between
+// calls (the array keeps the last call's contents).
+constexpr size_t kRhoStaticMax = size_t(1) << 20;  // doubles (8 MiB)
+static __device__ __align__(256) double g_rho_scratch[kRhoStaticMax];
+
+// Device address of g_rho_scratch on the current device, looked up once per
+// device (in host code the symbol is only a host-side stand-in).
+static double* rho_scratch_address(int* status) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static double* addr[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { *status = PMWA_ECUDA; return nullptr; }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_rho_scratch) != cudaSuccess || !p) { *status = PMWA_ECUDA; return nullptr; }
+    addr[dev] = static_cast<double*>(p);
+  }
+  *status = PMWA_OK;
+  return addr[dev];
+}
+
+int rho_slices_static(const Dev& d, int K, double* host_out, void* stream) {
+  if (K < 1 || !host_out) return PMWA_EINVAL;
+  if (size_t(d.N) * size_t(K) > kRhoStaticMax) return PMWA_EINVAL;
+  int st = PMWA_OK;
+  double* scratch = rho_scratch_address(&st);
+  if (!scratch) return st;
+  k_rho<<<blocks_for(d.N, 128), 128, 0, cudaStream_t(stream)>>>(d, K, scratch);
+  if (cudaGetLastError() != cudaSuccess) return PMWA_ECUDA;
+  if (cudaMemcpyAsync(host_out, scratch, size_t(d.N) * size_t(K) * sizeof(double), cudaMemcpyDeviceToHost,
+                      cudaStream_t(stream)) != cudaSuccess)
+    return PMWA_ECUDA;
+  if (cudaStreamSynchronize(cudaStream_t(stream)) != cudaSuccess) return PMWA_ECUDA;
+  return PMWA_OK;
 }
 
 int launch_rho(const Dev& d, int K, double* out, void* stream) {

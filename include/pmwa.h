@@ -149,6 +149,36 @@ int pmwa_set_sweep(pmwa_handle* h, uint64_t sweep);
 /* Release the handle (the arena stays the caller's). */
 int pmwa_destroy(pmwa_handle* h);
 
+/* Change N_cycle (Step 6 of the pseudo code: Step 5 is repeated N_cycle
+   times) of an instance, 0..4095. */
+int pmwa_set_n_cycle(pmwa_handle* h, int32_t n_cycle);
+
+/* ---- batches: many independent instances, one launch per kernel per sweep.
+   Each instance keeps exactly the configuration it would have alone: every
+   random draw is keyed by its own seed, replica id, sweep and unit, so a
+   batched sweep and n plain sweeps give identical bytes.  No paper
+   counterpart (the paper runs one instance on many processors); this is the
+   replica-batching pattern.  p points to n parameter sets; the arena holds
+   the batch tables and every instance's own arena. */
+typedef struct pmwa_batch pmwa_batch;
+size_t pmwa_batch_footprint(const pmwa_params* p, int32_t n);
+int pmwa_batch_create(const pmwa_params* p, int32_t n, void* dev_arena, size_t arena_bytes,
+                      void* stream, pmwa_batch** out);
+/* n_sweeps MC steps of every active instance (one measurement row each). */
+int pmwa_batch_sweep(pmwa_batch* b, int64_t n_sweeps);
+/* Capture `sweeps` batched sweeps in a CUDA graph (0 = no graph); later
+   pmwa_batch_sweep calls whose count is a multiple of it replay the graph. */
+int pmwa_batch_graph(pmwa_batch* b, int32_t sweeps);
+/* The instance's handle (for pmwa_measure, pmwa_export, pmwa_import, ...;
+   pmwa_sweep on it advances that instance alone: the plain path). */
+int pmwa_batch_instance(pmwa_batch* b, int32_t i, pmwa_handle** h);
+/* An inactive instance is skipped by pmwa_batch_sweep. */
+int pmwa_batch_set_active(pmwa_batch* b, int32_t i, int32_t on);
+int pmwa_batch_set_n_cycle(pmwa_batch* b, int32_t i, int32_t n_cycle);
+/* Device time (CUDA events on the stream) of the last pmwa_batch_sweep. */
+int pmwa_batch_last_ms(pmwa_batch* b, double* ms);
+int pmwa_batch_destroy(pmwa_batch* b);
+
 /* Host tables derived from p, for comparison with an independent
    implementation: d4[4] diagonal vertex weights d(s) = C - E(s); *D = max d;
    tv4[4] thinning thresholds floor(d/D 2^32); th256[16*4*4] directed-loop
@@ -158,6 +188,11 @@ int pmwa_destroy(pmwa_handle* h);
 int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4,
                 uint64_t* th256, double* sv, double* sw,
                 double* zig_x, double* zig_f, double* zig_w, uint64_t* zig_k);
+
+/* Shared memory (bytes) the sweep kernel needs per domain for these
+   parameters, 0 if a domain does not fit on one SM (a domain-shape tuner
+   uses it).  Host only. */
+int32_t pmwa_tile_smem(const pmwa_params* p);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
    every launch (enable = 1 turns it on, 0 off and clears).  pmwa_profile_read

@@ -72,6 +72,17 @@ def load(build=True):
         "pmwa_tables": (C.c_int, [P(Params)] + [vp] * 10),
         "pmwa_strerror": (C.c_char_p, [C.c_int]),
         "pmwa_profile": (C.c_int, [vp, C.c_int32]),
+        "pmwa_set_n_cycle": (C.c_int, [vp, C.c_int32]),
+        "pmwa_tile_smem": (C.c_int32, [P(Params)]),
+        "pmwa_batch_footprint": (sz, [vp, C.c_int32]),
+        "pmwa_batch_create": (C.c_int, [vp, C.c_int32, vp, sz, vp, P(vp)]),
+        "pmwa_batch_sweep": (C.c_int, [vp, C.c_int64]),
+        "pmwa_batch_graph": (C.c_int, [vp, C.c_int32]),
+        "pmwa_batch_instance": (C.c_int, [vp, C.c_int32, P(vp)]),
+        "pmwa_batch_set_active": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "pmwa_batch_set_n_cycle": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "pmwa_batch_last_ms": (C.c_int, [vp, P(C.c_double)]),
+        "pmwa_batch_destroy": (C.c_int, [vp]),
         "pmwa_profile_read": (C.c_int, [vp, vp, vp, C.c_int32]),
         "pmwa_profile_phases": (C.c_int, [vp, vp, C.c_int32]),
     }
@@ -179,6 +190,14 @@ def pmwa_set_sweep(h, s):
     _check("pmwa_set_sweep", load().pmwa_set_sweep(h, s))
 
 
+def pmwa_tile_smem(**kw):
+    return int(load().pmwa_tile_smem(C.byref(make_params(**kw))))
+
+
+def pmwa_set_n_cycle(h, n):
+    _check("pmwa_set_n_cycle", load().pmwa_set_n_cycle(h, n))
+
+
 def pmwa_destroy(h):
     _check("pmwa_destroy", load().pmwa_destroy(h))
 
@@ -275,6 +294,70 @@ class Sim:
     @sweep_index.setter
     def sweep_index(self, s):
         pmwa_set_sweep(self.h, s)
+
+
+class Batch:
+    """Many independent instances advanced together, one launch per kernel
+    per sweep (pmwa_batch_*).  Instance i is exposed as a handle for the
+    per-instance calls (rows, export, import, plain sweeps)."""
+
+    def __init__(self, params_list, device="cuda", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: libpmwa has no CPU path")
+        self.params = [make_params(**kw) for kw in params_list]
+        n = len(self.params)
+        arr = (Params * n)(*self.params)
+        self._arr = arr
+        nbytes = load().pmwa_batch_footprint(arr, n)
+        if nbytes == 0:
+            raise PmwaError("pmwa_batch_footprint", PMWA_EINVAL)
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        b = C.c_void_p()
+        _check("pmwa_batch_create", load().pmwa_batch_create(arr, n, self.arena.data_ptr(), nbytes,
+                                                             self.stream.cuda_stream, C.byref(b)))
+        self.b = b
+        self.n = n
+        self.handles = []
+        for i in range(n):
+            h = C.c_void_p()
+            _check("pmwa_batch_instance", load().pmwa_batch_instance(b, i, C.byref(h)))
+            self.handles.append(h)
+
+    def sweep(self, n=1):
+        _check("pmwa_batch_sweep", load().pmwa_batch_sweep(self.b, n))
+
+    def graph(self, sweeps):
+        _check("pmwa_batch_graph", load().pmwa_batch_graph(self.b, sweeps))
+
+    def set_active(self, i, on):
+        _check("pmwa_batch_set_active", load().pmwa_batch_set_active(self.b, i, 1 if on else 0))
+
+    def set_n_cycle(self, i, n):
+        _check("pmwa_batch_set_n_cycle", load().pmwa_batch_set_n_cycle(self.b, i, n))
+
+    def last_ms(self):
+        v = C.c_double()
+        _check("pmwa_batch_last_ms", load().pmwa_batch_last_ms(self.b, C.byref(v)))
+        return v.value
+
+    def rows(self, i):
+        return pmwa_measure(self.handles[i])
+
+    def export(self, i):
+        return pmwa_export(self.handles[i])
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().pmwa_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def observables(rows, p):

@@ -1,0 +1,77 @@
+"""Domain-shape tuning and the synthetic replica sets of the batched workloads.
+
+The tuner picks, per instance, the domain edge and the Step-5 sub-block edge:
+the largest square domain that divides L and whose shared-memory plan
+(pmwa_tile_smem) fits two CTAs per SM, at least 4 sites wide when the lattice
+allows it, with 2x2 shifted sub-blocks.  Results are cached per
+(L, beta, t, V, mu, eta, c_off) class.  N_cycle follows the rule "every
+vertex leg reached once per sweep on average", N_cycle = ceil(2 <n_v> / <n_w>),
+from a short pilot of the instance itself (see pilot_n_cycle).
+"""
+import math
+
+import numpy as np
+
+from . import _lib
+
+SMEM_TWO_PER_SM = 113 * 1024
+_cache = {}
+
+
+def _divisors(L):
+    return [s for s in range(L, 1, -1) if L % s == 0]
+
+
+def tune(p):
+    """dom_x, dom_y, sub_block for one parameter dict (square lattices)."""
+    key = tuple(round(float(p.get(k, d)), 9) for k, d in
+                [("Lx", 8), ("Ly", 8), ("beta", 2.0), ("t", 1.0), ("V", 0.0), ("mu", 0.0), ("eta", 0.2),
+                 ("c_off", -1.0)])
+    if key in _cache:
+        return dict(_cache[key])
+    Lx, Ly = int(p["Lx"]), int(p["Ly"])
+    best = None
+    for sx in _divisors(Lx):
+        if sx > 16 or (sx < Lx and sx < 2):
+            continue
+        sy = sx if Ly % sx == 0 else Lx if Lx == Ly else None
+        if sy is None or (sy < Ly and sy < 2):
+            continue
+        B = 2 if (sx % 2 == 0 and sy % 2 == 0 and min(sx, sy) >= 4) else 0
+        trial = dict(p, dom_x=sx, dom_y=sy, sub_block=B)
+        sm = _lib.pmwa_tile_smem(**{k: v for k, v in trial.items() if k in _lib.DEFAULTS})
+        if sm and sm <= SMEM_TWO_PER_SM:
+            best = dict(dom_x=sx, dom_y=sy, sub_block=B)
+            break
+        if sm and best is None:
+            best = dict(dom_x=sx, dom_y=sy, sub_block=B)  # fits one CTA per SM
+    if best is None:
+        raise ValueError("no domain shape fits shared memory for %r" % (p,))
+    _cache[key] = best
+    return dict(best)
+
+
+def n_cycle_rule(n_v, n_w):
+    return max(1, min(4095, int(math.ceil(2.0 * float(n_v) / max(float(n_w), 1.0)))))
+
+
+def replica_set(n=512, seed=3):
+    """The batched workload: n independent hard-core Bose-Hubbard instances,
+    L from {16, 24, 32, 48, 64}, beta t from {1, 2, 4, 8, 16}, mu uniform in
+    [-2, 2], V from {0, 1}, eta from {0.05, 0.1, 0.2}, drawn with numpy's
+    Philox generator keyed by `seed`; each instance gets its own Monte Carlo
+    seed and replica id and a half-filled random start."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    L = rng.choice([16, 24, 32, 48, 64], n)
+    beta = rng.choice([1.0, 2.0, 4.0, 8.0, 16.0], n)
+    mu = rng.uniform(-2.0, 2.0, n)
+    V = rng.choice([0.0, 1.0], n)
+    eta = rng.choice([0.05, 0.1, 0.2], n)
+    out = []
+    for i in range(n):
+        p = dict(Lx=int(L[i]), Ly=int(L[i]), beta=float(beta[i]), t=1.0, V=float(V[i]), mu=float(mu[i]),
+                 eta=float(eta[i]), seed=100000 + i, replica=i, init=1, init_seed=200000 + i,
+                 exchange_every=2, n_cycle=16)
+        p.update(tune(p))
+        out.append(p)
+    return out

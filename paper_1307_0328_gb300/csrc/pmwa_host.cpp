@@ -233,10 +233,7 @@ int run_tile(pmwa_handle* h, int stop, bool record) {
   d.sweep = uint32_t(h->sweep);
   cudaStream_t st = h->stream;
   const int eff = (stop == 6 && !record) ? 5 : stop;
-  if (eff == 6) {
-    d.row = h->rows_pending;
-    if (cudaMemsetAsync(d.rows + d.row, 0, sizeof(pmwa_row), st)) return PMWA_ECUDA;
-  }
+  if (eff == 6) d.row = h->rows_pending;  // rows past the pending ones are kept zeroed
   if (timed_launch(h, 1, [&] { return launch_tile(d, eff, st); })) return PMWA_ECUDA;
   if (eff == 6) h->rows_pending++;
   swap_buffers(d);
@@ -381,6 +378,9 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.cntB = reinterpret_cast<uint32_t*>(base + L.cntB);
   d.keyA = reinterpret_cast<uint64_t*>(base + L.keyA);
   d.keyB = reinterpret_cast<uint64_t*>(base + L.keyB);
+  d.bufk[0] = d.keyA; d.bufk[1] = d.keyB;
+  d.bufc[0] = d.cntA; d.bufc[1] = d.cntB;
+  d.exchange_every = p->exchange_every;
   h->err = d.err;
   h->phase = reinterpret_cast<unsigned long long*>(base + L.phase);
   d.phase_cycles = nullptr;
@@ -416,7 +416,8 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||
       cudaMemcpy(const_cast<uint64_t*>(d.TH), g.TH, sizeof g.TH, cudaMemcpyHostToDevice) ||
       cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ||
-      cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) {
+      cudaMemset(h->phase, 0, 8 * sizeof(uint64_t)) ||
+      cudaMemset(d.rows, 0, size_t(h->rows_cap) * sizeof(pmwa_row))) {
     delete h;
     return PMWA_ECUDA;
   }
@@ -431,6 +432,25 @@ int pmwa_destroy(pmwa_handle* h) {
   for (const Timed& t : h->timed) { cudaEventDestroy(t.start); cudaEventDestroy(t.stop); }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   delete h;
+  return PMWA_OK;
+}
+
+int32_t pmwa_tile_smem(const pmwa_params* p) {
+  if (validate(p)) return 0;
+  Derived g;
+  derive(p, &g);
+  Dev d;
+  std::memset(&d, 0, sizeof d);
+  d.Lx = p->Lx; d.Ly = p->Ly; d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy;
+  d.sub_block = p->sub_block; d.wcap = g.wcap; d.poolcap = g.poolcap;
+  if (!plan_tile_smem(&d, g.legs_per_site, g.mb)) return 0;
+  return d.sm_total;
+}
+
+int pmwa_set_n_cycle(pmwa_handle* h, int32_t n_cycle) {
+  if (!h || n_cycle < 0 || n_cycle > 4095) return PMWA_EINVAL;
+  h->d.n_cycle = n_cycle;
+  h->p.n_cycle = n_cycle;
   return PMWA_OK;
 }
 
@@ -526,6 +546,7 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
       return PMWA_ECUDA;
   }
   h->rows_pending = rest;
+  if (cudaMemset(h->d.rows + rest, 0, size_t(h->rows_cap - rest) * sizeof(pmwa_row))) return PMWA_ECUDA;
   *n_rows = n;
   return PMWA_OK;
 }
@@ -629,6 +650,294 @@ int pmwa_import(pmwa_handle* h, const void* buf, size_t bytes) {
       cudaMemcpy(h->d.cntA, cnt.data(), N * 4, cudaMemcpyHostToDevice) ||
       cudaMemcpy(h->d.keyA, keys.data(), N * cap * 8, cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many independent instances advanced by one launch per kernel.
+struct pmwa_batch {
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
+  std::vector<pmwa_handle*> h;
+  std::vector<int> active;
+  std::vector<BatchBase> hbase;
+  Dev* devs = nullptr;
+  BatchBase* base = nullptr;
+  DevErr* errs = nullptr;
+  int2* tile_work = nullptr;
+  int2* bwork[2] = {nullptr, nullptr};
+  int n_tile = 0, n_bwork[2] = {0, 0}, smem = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_sweeps = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.f;
+  bool dirty = false;  // instance parameters changed since the last upload
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t devs, base, errs, tile, bw[2], tables, total;
+  std::vector<size_t> inst_off, inst_bytes;
+  int n_tile, n_bw[2];
+};
+
+int boundary_bonds(const pmwa_params* p, const Derived& g, int dir) {
+  if (dir == 0) return g.ndx > 1 ? g.ndx * p->Ly : 0;
+  return g.ndy > 1 ? g.ndy * p->Lx : 0;
+}
+
+bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
+  if (n < 1 || n > 65536 || !p) return false;
+  L->n_tile = 0; L->n_bw[0] = L->n_bw[1] = 0;
+  L->inst_bytes.resize(size_t(n));
+  L->inst_off.resize(size_t(n));
+  for (int i = 0; i < n; ++i) {
+    if (validate(p + i)) return false;
+    Derived g;
+    derive(p + i, &g);
+    L->n_tile += g.ndom;
+    for (int dir = 0; dir < 2; ++dir)
+      L->n_bw[dir] += (boundary_bonds(p + i, g, dir) + kBoundaryThreads - 1) / kBoundaryThreads;
+    L->inst_bytes[size_t(i)] = layout(p + i, g).total;
+  }
+  size_t o = 0;
+  L->devs = o; o = align_up(o + size_t(n) * sizeof(Dev));
+  L->base = o; o = align_up(o + size_t(n) * sizeof(BatchBase));
+  L->errs = o; o = align_up(o + size_t(n) * sizeof(DevErr));
+  L->tile = o; o = align_up(o + size_t(std::max(1, L->n_tile)) * sizeof(int2));
+  for (int dir = 0; dir < 2; ++dir) { L->bw[dir] = o; o = align_up(o + size_t(std::max(1, L->n_bw[dir])) * sizeof(int2)); }
+  L->tables = o;
+  for (int i = 0; i < n; ++i) { L->inst_off[size_t(i)] = o; o = align_up(o + L->inst_bytes[size_t(i)]); }
+  L->total = o;
+  return true;
+}
+
+// work items in decreasing estimated cost, so the longest CTAs start first
+void build_tile_work(pmwa_batch* b, std::vector<int2>* work) {
+  std::vector<std::pair<double, int2>> items;
+  for (int i = 0; i < b->n; ++i) {
+    const Dev& d = b->h[size_t(i)]->d;
+    const double cost = double(d.dom_x * d.dom_y) * b->h[size_t(i)]->p.beta *
+                        (d.dvw[0] + d.tkink + 1.0) * double(d.n_cycle + 4);
+    for (int k = 0; k < d.ndom; ++k) items.push_back({cost, make_int2(i, k)});
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) { return x.first > y.first; });
+  work->clear();
+  for (const auto& it : items) work->push_back(it.second);
+}
+
+int batch_upload(pmwa_batch* b) {
+  std::vector<Dev> devs(size_t(b->n));
+  for (int i = 0; i < b->n; ++i) devs[size_t(i)] = b->h[size_t(i)]->d;
+  std::vector<int2> tw;
+  build_tile_work(b, &tw);
+  if ((int)tw.size() > b->n_tile) return PMWA_EINVAL;
+  if (cudaMemcpy(b->devs, devs.data(), devs.size() * sizeof(Dev), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(b->tile_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice))
+    return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+void batch_drop_graph(pmwa_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_sweeps = 0;
+}
+
+// one batched sweep at iteration `it` (boundary x, boundary y, tile)
+int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
+  for (int dir = 0; dir < 2; ++dir)
+    if (b->n_bwork[dir] && launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, st))
+      return PMWA_ECUDA;
+  if (launch_tile_batch(b->devs, b->base, b->tile_work, b->n_tile, b->smem, it, 6, st)) return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pmwa_batch_footprint(const pmwa_params* p, int32_t n) {
+  BatchLayout L;
+  return batch_layout(p, n, &L) ? L.total : 0;
+}
+
+int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes, void* stream, pmwa_batch** out) {
+  if (!out) return PMWA_EINVAL;
+  *out = nullptr;
+  BatchLayout L;
+  if (!batch_layout(p, n, &L)) return PMWA_EINVAL;
+  if (!arena || bytes < L.total || (reinterpret_cast<uintptr_t>(arena) & (kAlign - 1))) return PMWA_EINVAL;
+  pmwa_batch* b = new (std::nothrow) pmwa_batch();
+  if (!b) return PMWA_EINVAL;
+  b->n = n;
+  b->stream = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(arena);
+  b->devs = reinterpret_cast<Dev*>(base + L.devs);
+  b->base = reinterpret_cast<BatchBase*>(base + L.base);
+  b->errs = reinterpret_cast<DevErr*>(base + L.errs);
+  b->tile_work = reinterpret_cast<int2*>(base + L.tile);
+  b->bwork[0] = reinterpret_cast<int2*>(base + L.bw[0]);
+  b->bwork[1] = reinterpret_cast<int2*>(base + L.bw[1]);
+  b->n_tile = L.n_tile;
+  b->n_bwork[0] = L.n_bw[0];
+  b->n_bwork[1] = L.n_bw[1];
+  b->h.assign(size_t(n), nullptr);
+  b->active.assign(size_t(n), 1);
+  b->hbase.resize(size_t(n));
+  int rc = PMWA_OK;
+  for (int i = 0; i < n && rc == PMWA_OK; ++i) {
+    rc = pmwa_create(p + i, base + L.inst_off[size_t(i)], L.inst_bytes[size_t(i)], stream, &b->h[size_t(i)]);
+    if (rc) break;
+    pmwa_handle* hi = b->h[size_t(i)];
+    hi->err = hi->d.err = b->errs + i;  // one contiguous error array for the batch
+    b->smem = std::max(b->smem, hi->d.sm_total);
+  }
+  if (rc == PMWA_OK && cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK) {
+    std::vector<int2> bw;
+    for (int dir = 0; dir < 2 && rc == PMWA_OK; ++dir) {
+      bw.clear();
+      for (int i = 0; i < n; ++i) {
+        Derived g;
+        derive(p + i, &g);
+        const int nb = boundary_bonds(p + i, g, dir);
+        for (int t0 = 0; t0 < nb; t0 += kBoundaryThreads) bw.push_back(make_int2(i, t0));
+      }
+      if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
+        rc = PMWA_ECUDA;
+    }
+  }
+  if (rc == PMWA_OK) rc = batch_upload(b);
+  if (rc == PMWA_OK && prepare_tile_batch(b->smem)) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
+                        cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
+    rc = PMWA_ECUDA;
+  if (rc) {
+    for (pmwa_handle* hi : b->h) if (hi) pmwa_destroy(hi);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return PMWA_OK;
+}
+
+int pmwa_batch_instance(pmwa_batch* b, int32_t i, pmwa_handle** h) {
+  if (!b || !h || i < 0 || i >= b->n) return PMWA_EINVAL;
+  *h = b->h[size_t(i)];
+  return PMWA_OK;
+}
+
+int pmwa_batch_set_active(pmwa_batch* b, int32_t i, int32_t on) {
+  if (!b || i < 0 || i >= b->n) return PMWA_EINVAL;
+  b->active[size_t(i)] = on ? 1 : 0;
+  return PMWA_OK;
+}
+
+int pmwa_batch_set_n_cycle(pmwa_batch* b, int32_t i, int32_t n_cycle) {
+  if (!b || i < 0 || i >= b->n || n_cycle < 0 || n_cycle > 4095) return PMWA_EINVAL;
+  b->h[size_t(i)]->d.n_cycle = n_cycle;
+  b->h[size_t(i)]->p.n_cycle = n_cycle;
+  batch_drop_graph(b);
+  b->dirty = true;  // uploaded before the next batched sweep or capture
+  return PMWA_OK;
+}
+
+int pmwa_batch_graph(pmwa_batch* b, int32_t sweeps) {
+  if (!b || sweeps < 0 || sweeps > 4096) return PMWA_EINVAL;
+  batch_drop_graph(b);
+  if (sweeps == 0) return PMWA_OK;
+  if (b->dirty) {
+    if (cudaStreamSynchronize(b->stream)) return PMWA_ECUDA;
+    const int rc = batch_upload(b);
+    if (rc) return rc;
+    b->dirty = false;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) return PMWA_ECUDA;
+  int rc = PMWA_OK;
+  for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_sweep(b, it, b->cap);
+  if (rc == PMWA_OK && launch_advance(b->base, b->n, sweeps, b->cap)) rc = PMWA_ECUDA;
+  if (cudaStreamEndCapture(b->cap, &g) || rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc ? rc : PMWA_ECUDA;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e) { b->graph = nullptr; return PMWA_ECUDA; }
+  b->graph_sweeps = sweeps;
+  return PMWA_OK;
+}
+
+int pmwa_batch_sweep(pmwa_batch* b, int64_t n) {
+  if (!b || n < 0) return PMWA_EINVAL;
+  if (n == 0) return PMWA_OK;
+  for (int i = 0; i < b->n; ++i)
+    if (b->active[size_t(i)] && b->h[size_t(i)]->rows_pending + n > b->h[size_t(i)]->rows_cap) return PMWA_EROWS;
+  for (int i = 0; i < b->n; ++i) {
+    const pmwa_handle* hi = b->h[size_t(i)];
+    b->hbase[size_t(i)] = BatchBase{uint32_t(hi->sweep), hi->rows_pending,
+                                    hi->d.keyA == hi->d.bufk[1] ? 1 : 0, b->active[size_t(i)]};
+  }
+  if (cudaStreamSynchronize(b->stream)) return PMWA_ECUDA;
+  if (b->dirty) {
+    const int rc = batch_upload(b);
+    if (rc) return rc;
+    b->dirty = false;
+  }
+  if (cudaMemcpy(b->base, b->hbase.data(), b->hbase.size() * sizeof(BatchBase), cudaMemcpyHostToDevice))
+    return PMWA_ECUDA;
+  cudaEventRecord(b->ev0, b->stream);
+  if (b->graph && n % b->graph_sweeps == 0) {
+    for (int64_t r = 0; r < n / b->graph_sweeps; ++r)
+      if (cudaGraphLaunch(b->graph, b->stream)) return PMWA_ECUDA;
+  } else {
+    for (int64_t it = 0; it < n; ++it) {
+      const int rc = batch_launch_sweep(b, int(it), b->stream);
+      if (rc) return rc;
+    }
+  }
+  cudaEventRecord(b->ev1, b->stream);
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->active[size_t(i)]) continue;
+    pmwa_handle* hi = b->h[size_t(i)];
+    hi->sweep += uint64_t(n);
+    hi->rows_pending += int(n);
+    if (n & 1) swap_buffers(hi->d);
+  }
+  if (cudaStreamSynchronize(b->stream)) return PMWA_ECUDA;
+  cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1);
+  std::vector<DevErr> e(size_t(b->n));
+  if (cudaMemcpy(e.data(), b->errs, e.size() * sizeof(DevErr), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
+  for (const DevErr& x : e)
+    if (x.code) {
+      cudaMemset(b->errs, 0, e.size() * sizeof(DevErr));
+      return x.code;
+    }
+  return PMWA_OK;
+}
+
+int pmwa_batch_last_ms(pmwa_batch* b, double* ms) {
+  if (!b || !ms) return PMWA_EINVAL;
+  *ms = b->last_ms;
+  return PMWA_OK;
+}
+
+int pmwa_batch_destroy(pmwa_batch* b) {
+  if (!b) return PMWA_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (pmwa_handle* hi : b->h) pmwa_destroy(hi);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  delete b;
   return PMWA_OK;
 }
 

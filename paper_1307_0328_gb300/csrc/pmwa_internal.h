@@ -55,7 +55,36 @@ struct Dev {
   DevErr* err;
   pmwa_row* rows;
   int row;
+  // both configuration buffers (keyA/keyB above are the current selection)
+  uint64_t* bufk[2];
+  uint32_t* bufc[2];
+  int exchange_every;
 };
+
+// Per-instance state at the start of a batched call: the sweep index, the
+// next free measurement row, which buffer holds the current configuration,
+// and whether the instance takes part.
+struct BatchBase {
+  uint32_t sweep0;
+  int row0;
+  int flip;
+  int active;
+};
+
+// An instance's parameters advanced to sweep iteration `it` of a batched call
+__host__ __device__ inline Dev at_iteration(const Dev& d0, const BatchBase& b, int it) {
+  Dev d = d0;
+  const int cur = (b.flip + it) & 1;
+  d.keyA = d0.bufk[cur];
+  d.cntA = d0.bufc[cur];
+  d.keyB = d0.bufk[cur ^ 1];
+  d.cntB = d0.bufc[cur ^ 1];
+  d.sweep = b.sweep0 + uint32_t(it);
+  d.row = b.row0 + it;
+  return d;
+}
+
+constexpr int kBoundaryThreads = 64;
 
 // Exponential ziggurat tables, built on the host (pmwa_host.cpp).
 struct Zig {
@@ -70,6 +99,12 @@ int upload_zig(const Zig& z);       // constants of pmwa_kernels.cu
 int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_tile(const Dev& d, int stop, void* stream);
+int launch_tile_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem, int it,
+                      int stop, void* stream);
+int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
+                          void* stream);
+int prepare_tile_batch(int smem);
+int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
 // rho slices through the library's own static device scratch (no allocation)
 int rho_slices_static(const Dev& d, int K, double* host_out, void* stream);

@@ -121,19 +121,16 @@ __device__ __forceinline__ double em1_of(uint64_t I, double XW) {
   return expm1_det(__dmul_rn(-2.0, __dmul_rn(__ull2double_rn(I), XW)));
 }
 
-__global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
-  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
-  const ZigTab Z = zig_stage(zbuf);
-  __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ int boundary_count(const Dev& d, int dir) {
+  return dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
+}
+
+// Step 2 + Step 3 on boundary bond number t of direction dir
+__device__ void boundary_body(const Dev& d, int dir, int t, const ZigTab& Z) {
+  if (t >= boundary_count(d, dir)) return;
   int a;
-  if (dir == 0) {
-    if (t >= d.ndx * d.Ly) return;
-    a = ((t % d.ndx) * d.dom_x + d.dom_x - 1) + d.Lx * (t / d.ndx);
-  } else {
-    if (t >= d.ndy * d.Lx) return;
-    a = (t % d.Lx) + d.Lx * ((t / d.Lx) * d.dom_y + d.dom_y - 1);
-  }
+  if (dir == 0) a = ((t % d.ndx) * d.dom_x + d.dom_x - 1) + d.Lx * (t / d.ndx);
+  else a = (t % d.Lx) + d.Lx * ((t / d.Lx) * d.dom_y + d.dom_y - 1);
   const int b = site_step(d, a, dir, +1);
   const int tag = bond_tag(d, a, dir);
   const int bid = 2 * a + dir;
@@ -244,16 +241,61 @@ __global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
   if (rc) set_err(d.err, rc, 2);
 }
 
+__global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
+  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
+  const ZigTab Z = zig_stage(zbuf);
+  __syncthreads();
+  boundary_body(d, dir, int(blockIdx.x * blockDim.x + threadIdx.x), Z);
+}
+
+// Batched form: each block serves bonds [t0, t0 + blockDim) of one instance,
+// which takes part only when its boundary step is due at iteration `it`.
+__global__ void k_boundary_batch(const Dev* __restrict__ devs, const BatchBase* __restrict__ base,
+                                 const int2* __restrict__ work, int it, int dir) {
+  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
+  __shared__ Dev sd;
+  const int2 w = work[blockIdx.x];
+  const BatchBase b = base[w.x];
+  if (!b.active) return;
+  if (threadIdx.x == 0) sd = at_iteration(devs[w.x], b, it);
+  const ZigTab Z = zig_stage(zbuf);
+  __syncthreads();
+  if (sd.ndom < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
+  boundary_body(sd, dir, w.y + int(threadIdx.x), Z);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 static inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
 
 int upload_zig(const Zig& z) { return upload_constants(z); }
 
+// advance every instance's batch state by S sweeps (the tail of a captured
+// sequence of S sweeps, so that the next replay continues where it ended)
+__global__ void k_advance(BatchBase* base, int n, int S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !base[i].active) return;
+  base[i].sweep0 += uint32_t(S);
+  base[i].row0 += S;
+  base[i].flip ^= (S & 1);
+}
+
+int launch_advance(BatchBase* base, int n, int S, void* stream) {
+  k_advance<<<blocks_for(n, 128), 128, 0, cudaStream_t(stream)>>>(base, n, S);
+  return int(cudaGetLastError());
+}
+
+int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
+                          void* stream) {
+  if (n_work <= 0) return 0;
+  k_boundary_batch<<<n_work, kBoundaryThreads, 0, cudaStream_t(stream)>>>(devs, base, work, it, dir);
+  return int(cudaGetLastError());
+}
+
 int launch_boundary(const Dev& d, int dir, void* stream) {
   const long long n = dir == 0 ? (long long)d.ndx * d.Ly : (long long)d.ndy * d.Lx;
   if ((dir == 0 && d.ndx < 2) || (dir == 1 && d.ndy < 2)) return 0;
-  k_boundary<<<blocks_for(n, 64), 64, 0, cudaStream_t(stream)>>>(d, dir);
+  k_boundary<<<blocks_for(n, kBoundaryThreads), kBoundaryThreads, 0, cudaStream_t(stream)>>>(d, dir);
   return int(cudaGetLastError());
 }
 

@@ -324,9 +324,8 @@ __device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t blo,
 }  // namespace
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Dev d, int stop) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ int wsum[32];
+__device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int stop, unsigned char* sm,
+                                          int* wsum) {
   Tile T;
   T.d = &d;
   T.th = reinterpret_cast<uint64_t*>(sm + d.sm_th);
@@ -347,7 +346,6 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
   T.tinfo = reinterpret_cast<uint8_t*>(sm + d.sm_tinfo);
   T.sub = reinterpret_cast<uint16_t*>(sm + d.sm_sub);
-  const int dom = blockIdx.x;
   T.x0 = (dom % d.ndx) * d.dom_x;
   T.y0 = (dom / d.ndx) * d.dom_y;
   T.nds = d.dom_x * d.dom_y;
@@ -669,6 +667,28 @@ fail:
   if (tid == 0) set_err(d.err, misc->err, misc->where);
 }
 
+__global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Dev d, int stop) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int wsum[32];
+  tile_body(d, int(blockIdx.x), stop, sm, wsum);
+}
+
+// Batched form: one CTA per (instance, domain) work item; the instance's
+// parameters are copied into shared memory and advanced to sweep iteration
+// `it` of the current batch call (buffers, sweep index, row).
+__global__ void __launch_bounds__(kTileThreads) k_tile_batch(const Dev* __restrict__ devs,
+                                                             const BatchBase* __restrict__ base,
+                                                             const int2* __restrict__ work, int it, int stop) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int wsum[32];
+  __shared__ Dev sd;
+  const int2 w = work[blockIdx.x];
+  if (!base[w.x].active) return;
+  if (threadIdx.x == 0) sd = at_iteration(devs[w.x], base[w.x], it);
+  __syncthreads();
+  tile_body(sd, w.y, stop, sm, wsum);
+}
+
 // ---------------------------------------------------------------------------
 bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   const int nds = d->dom_x * d->dom_y;
@@ -715,6 +735,16 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
 }
 
 int upload_zig_tile(const Zig& z) { return upload_constants(z); }
+
+int prepare_tile_batch(int smem) {
+  return int(cudaFuncSetAttribute(k_tile_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+}
+
+int launch_tile_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem, int it,
+                      int stop, void* stream) {
+  k_tile_batch<<<n_work, kTileThreads, smem, cudaStream_t(stream)>>>(devs, base, work, it, stop);
+  return int(cudaGetLastError());
+}
 
 int launch_tile(const Dev& d, int stop, void* stream) {
   cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);

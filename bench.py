@@ -60,8 +60,9 @@ def peaks():
 
 def ncycle_rule(n_v, n_w):
     """Every vertex leg visited once per sweep on average: each move lands a
-    worm on one leg, a sweep has 2 n_v legs and n_w worms move per pass."""
-    return max(1, min(4095, int(math.ceil(2.0 * n_v / max(n_w, 1.0)))))
+    worm on one leg, a sweep has 2 n_v legs and n_w worms move per pass
+    (capped at 512 passes for instances with almost no worms)."""
+    return max(1, min(512, int(math.ceil(2.0 * n_v / max(n_w, 1.0)))))
 
 
 # --------------------------------------------------------------------------- clocks
@@ -153,6 +154,53 @@ def run_reference(args, wl, n_cycle):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------- batched leg
+def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=12):
+    """The 512-replica workload (L in {16..64}, beta t in {1..16}, mu in
+    [-2, 2], V in {0, 1}, eta in {0.05, 0.1, 0.2}; autotuned domains) swept
+    (a) batched: one launch per kernel per sweep, replayed from a CUDA graph,
+    and (b) plain: the same instances one after another, each with its own
+    launches.  Vertex updates/s from device time (CUDA events)."""
+    from paper_1307_0328_gb300 import autotune as A
+    reps = A.replica_set(n_reps)
+    batch = P.Batch(reps)
+    batch.sweep(pilot)
+    ncs = []
+    for i in range(batch.n):
+        r = batch.rows(i)
+        half = r[len(r) // 2:]
+        nc = A.n_cycle_rule(half["n_v"].mean(), half["n_w"].mean())
+        ncs.append(nc)
+        batch.set_n_cycle(i, nc)
+    G = graph_sweeps or steps
+    batch.graph(G)
+    batch.sweep(G * max(1, -(-warmup // G)))
+    for i in range(batch.n):
+        batch.rows(i)
+    batch.sweep(steps)
+    ms_b = batch.last_ms()
+    nv_b = sum(float(batch.rows(i)["n_v"].sum()) for i in range(batch.n))
+    # plain: each instance alone, its own launches, same number of sweeps
+    ms_p = 0.0
+    nv_p = 0.0
+    for i in range(batch.n):
+        h = batch.handles[i]
+        P.pmwa_profile(h, True)
+        P.pmwa_profile_read(h)
+        P.pmwa_sweep(h, steps)
+        ms_p += P.pmwa_profile_read(h)["sweep"][0]
+        P.pmwa_profile(h, False)
+        nv_p += float(P.pmwa_measure(h)["n_v"].sum())
+    out = dict(workload="%d replicas: L in {16,24,32,48,64}, beta*t in {1,2,4,8,16}, mu in [-2,2], "
+                        "V in {0,1}, eta in {0.05,0.1,0.2}, autotuned domains, CUDA graph" % n_reps,
+               value=nv_b / (ms_b / 1000.0), unit=UNIT, ms_per_step=ms_b / steps, graph_sweeps=G,
+               plain_value=nv_p / (ms_p / 1000.0), plain_ms_per_step=ms_p / steps,
+               speedup=(nv_b / ms_b) / (nv_p / ms_p), vertices_per_sweep=nv_b / steps,
+               n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=batch.arena.numel() / 1e9)
+    batch.close()
+    return out
+
+
 # --------------------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -165,6 +213,7 @@ def main():
     ap.add_argument("--n-cycle", type=int, default=0, help="fix N_cycle instead of the pilot rule")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-replica comparison")
     args = ap.parse_args()
     wl = args.workload
     args.warmup = max(args.warmup, 3)
@@ -303,6 +352,8 @@ def main():
             gpu_launches=int(sum(v["launches"] for k, v in kernels.items() if k != "sweep")),
             clocks=clk, wall_s=wall,
         )
+        if not args.no_batch:
+            line["batched"] = batched_vs_plain(P, args.steps, args.warmup)
         if not args.no_cpu:
             rate, steps, el = oracle_rate(wl, nc, args.cpu_seconds, warmup=1)
             line["cpu_baseline"] = dict(value=rate, unit=UNIT, cores=1, kind="oracle",

@@ -6,7 +6,7 @@ the largest square domain that divides L and whose shared-memory plan
 allows it, with 2x2 shifted sub-blocks.  Results are cached per
 (L, beta, t, V, mu, eta, c_off) class.  N_cycle follows the rule "every
 vertex leg reached once per sweep on average", N_cycle = ceil(2 <n_v> / <n_w>),
-from a short pilot of the instance itself (see pilot_n_cycle).
+from a short pilot of the instance itself, capped at 512.
 """
 import math
 
@@ -52,7 +52,11 @@ def tune(p):
 
 
 def n_cycle_rule(n_v, n_w):
-    return max(1, min(4095, int(math.ceil(2.0 * float(n_v) / max(float(n_w), 1.0)))))
+    """ceil(2 <n_v> / <n_w>), capped at 512 passes: an instance with almost no
+    worms (small beta eta on a small lattice) is far outside the regime of
+    O(10)-O(100) worms per domain that the method is made for, and more
+    passes would only repeat moves of the same few worms."""
+    return max(1, min(512, int(math.ceil(2.0 * float(n_v) / max(float(n_w), 1.0)))))
 
 
 def replica_set(n=512, seed=3):

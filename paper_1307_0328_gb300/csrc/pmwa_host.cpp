@@ -669,7 +669,7 @@ struct pmwa_batch {
   DevErr* errs = nullptr;
   int2* tile_work = nullptr;
   int2* bwork[2] = {nullptr, nullptr};
-  int n_tile = 0, n_bwork[2] = {0, 0}, smem = 0;
+  int n_tile = 0, n_bwork[2] = {0, 0}, smem = 0, cap_max = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_sweeps = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -701,7 +701,7 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
     derive(p + i, &g);
     L->n_tile += g.ndom;
     for (int dir = 0; dir < 2; ++dir)
-      L->n_bw[dir] += (boundary_bonds(p + i, g, dir) + kBoundaryThreads - 1) / kBoundaryThreads;
+      L->n_bw[dir] += boundary_bonds(p + i, g, dir);  // upper bound: one bond per block
     L->inst_bytes[size_t(i)] = layout(p + i, g).total;
   }
   size_t o = 0;
@@ -752,7 +752,8 @@ void batch_drop_graph(pmwa_batch* b) {
 // one batched sweep at iteration `it` (boundary x, boundary y, tile)
 int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
   for (int dir = 0; dir < 2; ++dir)
-    if (b->n_bwork[dir] && launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, st))
+    if (b->n_bwork[dir] &&
+        launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, b->cap_max, st))
       return PMWA_ECUDA;
   if (launch_tile_batch(b->devs, b->base, b->tile_work, b->n_tile, b->smem, it, 6, st)) return PMWA_ECUDA;
   return PMWA_OK;
@@ -797,24 +798,27 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     pmwa_handle* hi = b->h[size_t(i)];
     hi->err = hi->d.err = b->errs + i;  // one contiguous error array for the batch
     b->smem = std::max(b->smem, hi->d.sm_total);
+    b->cap_max = std::max(b->cap_max, hi->d.cap);
   }
   if (rc == PMWA_OK && cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
   if (rc == PMWA_OK) {
     std::vector<int2> bw;
     for (int dir = 0; dir < 2 && rc == PMWA_OK; ++dir) {
       bw.clear();
+      const int bpb = boundary_bonds_per_block(b->cap_max);
       for (int i = 0; i < n; ++i) {
         Derived g;
         derive(p + i, &g);
         const int nb = boundary_bonds(p + i, g, dir);
-        for (int t0 = 0; t0 < nb; t0 += kBoundaryThreads) bw.push_back(make_int2(i, t0));
+        for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
       }
+      b->n_bwork[dir] = int(bw.size());
       if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
         rc = PMWA_ECUDA;
     }
   }
   if (rc == PMWA_OK) rc = batch_upload(b);
-  if (rc == PMWA_OK && prepare_tile_batch(b->smem)) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (prepare_tile_batch(b->smem) || prepare_boundary(b->cap_max))) rc = PMWA_ECUDA;
   if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
                         cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
     rc = PMWA_ECUDA;

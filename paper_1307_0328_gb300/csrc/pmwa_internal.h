@@ -84,7 +84,6 @@ __host__ __device__ inline Dev at_iteration(const Dev& d0, const BatchBase& b, i
   return d;
 }
 
-constexpr int kBoundaryThreads = 64;
 
 // Exponential ziggurat tables, built on the host (pmwa_host.cpp).
 struct Zig {
@@ -102,7 +101,9 @@ int launch_tile(const Dev& d, int stop, void* stream);
 int launch_tile_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem, int it,
                       int stop, void* stream);
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
-                          void* stream);
+                          int cap, void* stream);
+int boundary_bonds_per_block(int cap);
+int prepare_boundary(int cap);
 int prepare_tile_batch(int smem);
 int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);

@@ -16,6 +16,8 @@
 
 namespace pmwa {
 
+static inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
+
 constexpr int kMaxWormsPerInterval = 128;
 constexpr uint32_t kCntMask = 0x7fffffffu;
 
@@ -91,28 +93,32 @@ __device__ __forceinline__ void aslot_insert(uint64_t* K, int n, int at, uint64_
 }
 
 // erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
-// and draw new ones with end states p (above lo) and q (below hi).
-__device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, int x, uint64_t lo, uint64_t hi, int p, int q) {
-  uint64_t* K = d.keyA + size_t(x) * d.cap;
-  int n = cnt_n(d.cntA[x]);
+// and draw new ones with end states p (above lo) and q (below hi); K holds
+// n events (capacity cap).
+__device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_t* K, int& n,
+                              uint64_t lo, uint64_t hi, int p, int q) {
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
-  for (int k = n - 1; k >= 0; --k) {
-    if (!kworm(K[k])) continue;
-    const uint64_t off = (kpk(K[k]) + kTwo62 - lo) & (kTwo62 - 1);
-    if (off > 0 && off < span) { aslot_erase(K, n, k); --n; }
+  int w = 0;
+  for (int k = 0; k < n; ++k) {  // compact away the worms of the interval
+    const uint64_t key = K[k];
+    if (kworm(key)) {
+      const uint64_t off = (kpk(key) + kTwo62 - lo) & (kTwo62 - 1);
+      if (off > 0 && off < span) continue;
+    }
+    K[w++] = key;
   }
+  n = w;
   uint64_t offs[kMaxWormsPerInterval];
   int bad = 0;
   const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SW, d.SWI, offs, &bad);
-  if (bad) { d.cntA[x] = cnt_make(n, cnt_base(d.cntA[x])); return bad; }
+  if (bad) return bad;
   const uint64_t m0 = wm_above(lo);
   for (int k = 0; k < nw; ++k) {
-    if (n >= d.cap) { d.cntA[x] = cnt_make(n, cnt_base(d.cntA[x])); return PMWA_ECAPACITY; }
+    if (n >= d.cap) return PMWA_ECAPACITY;
     const uint64_t key = wkey((m0 + offs[k]) & (kTwo59 - 1), 0, p ^ 1 ^ (k & 1));
     aslot_insert(K, n, slot_lower(K, n, kpk(key)), key);
     ++n;
   }
-  d.cntA[x] = cnt_make(n, n ? kab(K[n - 1]) : cnt_base(d.cntA[x]));
   return PMWA_OK;
 }
 
@@ -125,17 +131,18 @@ __device__ __forceinline__ int boundary_count(const Dev& d, int dir) {
   return dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
 }
 
-// Step 2 + Step 3 on boundary bond number t of direction dir
-__device__ void boundary_body(const Dev& d, int dir, int t, const ZigTab& Z) {
-  if (t >= boundary_count(d, dir)) return;
-  int a;
-  if (dir == 0) a = ((t % d.ndx) * d.dom_x + d.dom_x - 1) + d.Lx * (t / d.ndx);
-  else a = (t % d.Lx) + d.Lx * ((t / d.Lx) * d.dom_y + d.dom_y - 1);
-  const int b = site_step(d, a, dir, +1);
+// lower site of boundary bond number t of direction dir
+__device__ __forceinline__ int boundary_site(const Dev& d, int dir, int t) {
+  if (dir == 0) return ((t % d.ndx) * d.dom_x + d.dom_x - 1) + d.Lx * (t / d.ndx);
+  return (t % d.Lx) + d.Lx * ((t / d.Lx) * d.dom_y + d.dom_y - 1);
+}
+
+// Step 2 + Step 3 on the boundary bond (a, dir) whose two site lists are
+// staged in KA (nA events) and KB (nB events); returns a status.
+__device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, int& nA, int& baseA,
+                                    uint64_t* KB, int& nB, int& baseB, const ZigTab& Z) {
   const int tag = bond_tag(d, a, dir);
   const int bid = 2 * a + dir;
-  uint64_t* KA = d.keyA + size_t(a) * d.cap;
-  uint64_t* KB = d.keyA + size_t(b) * d.cap;
   Stream st;
   st.init(d.key0, d.key1, uint32_t(bid), c2_word(dir ? kBy : kBx, 0, d.replica), d.sweep);
   int rc = PMWA_OK;
@@ -143,17 +150,14 @@ __device__ void boundary_body(const Dev& d, int dir, int t, const ZigTab& Z) {
   uint64_t last = 0;
   bool any = false;
   for (;;) {
-    const int nA = cnt_n(d.cntA[a]);
     int k = any ? slot_lower(KA, nA, last + 1) : 0;
     while (k < nA && ktag(KA[k]) != tag) ++k;
     if (k >= nA) break;
     const uint64_t pv = kpk(KA[k]);
-    last = pv; any = true;
+    last = pv;
+    any = true;
     Legs La, Lb;
-    if (!site_legs(KA, nA, pv, &La) || !site_legs(KB, cnt_n(d.cntA[b]), pv, &Lb)) {
-      rc = PMWA_EINVARIANT;
-      break;
-    }
+    if (!site_legs(KA, nA, pv, &La) || !site_legs(KB, nB, pv, &Lb)) return PMWA_EINVARIANT;
     double ea_dn = 0.0, eb_dn = 0.0, ea_up, eb_up;
     if (La.single) ea_up = em1_of(kTwo59, d.XW);
     else { ea_dn = em1_of(La.Idn, d.XW); ea_up = em1_of(La.Iup, d.XW); }
@@ -174,99 +178,160 @@ __device__ void boundary_body(const Dev& d, int dir, int t, const ZigTab& Z) {
       tot = __dadd_rn(tot, w);
       cum[S] = tot;
     }
-    if (lastS < 0) { rc = PMWA_EINVARIANT; break; }
+    if (lastS < 0) return PMWA_EINVARIANT;
     const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
     int Sn = lastS;
     for (int S = 0; S < 16; ++S) if (u < cum[S]) { Sn = S; break; }
     const int s0 = Sn & 1, s1 = (Sn >> 1) & 1, s2 = (Sn >> 2) & 1, s3 = (Sn >> 3) & 1;
     {
-      const int ka = slot_find(KA, cnt_n(d.cntA[a]), pv), kb = slot_find(KB, cnt_n(d.cntA[b]), pv);
-      if (ka < 0 || kb < 0) { rc = PMWA_EINVARIANT; break; }
+      const int ka = slot_find(KA, nA, pv), kb = slot_find(KB, nB, pv);
+      if (ka < 0 || kb < 0) return PMWA_EINVARIANT;
       KA[ka] = (KA[ka] & ~3ull) | (uint64_t(s0) << 1) | uint64_t(s2);
       KB[kb] = (KB[kb] & ~3ull) | (uint64_t(s1) << 1) | uint64_t(s3);
     }
-    if (!La.single) rc = regen_interval(d, Z, st, a, La.plo, pv, La.far_dn, s0);
-    if (!rc && !Lb.single) rc = regen_interval(d, Z, st, b, Lb.plo, pv, Lb.far_dn, s1);
-    if (!rc) rc = La.single ? regen_interval(d, Z, st, a, pv, pv, s2, s0)
-                            : regen_interval(d, Z, st, a, pv, La.phi, s2, La.far_up);
-    if (!rc) rc = Lb.single ? regen_interval(d, Z, st, b, pv, pv, s3, s1)
-                            : regen_interval(d, Z, st, b, pv, Lb.phi, s3, Lb.far_up);
-    if (rc) break;
+    if (!La.single) rc = regen_interval(d, Z, st, KA, nA, La.plo, pv, La.far_dn, s0);
+    if (!rc && !Lb.single) rc = regen_interval(d, Z, st, KB, nB, Lb.plo, pv, Lb.far_dn, s1);
+    if (!rc) rc = La.single ? regen_interval(d, Z, st, KA, nA, pv, pv, s2, s0)
+                            : regen_interval(d, Z, st, KA, nA, pv, La.phi, s2, La.far_up);
+    if (!rc) rc = Lb.single ? regen_interval(d, Z, st, KB, nB, pv, pv, s3, s1)
+                            : regen_interval(d, Z, st, KB, nB, pv, Lb.phi, s3, Lb.far_up);
+    if (rc) return rc;
   }
+  if (st.pos >= (uint64_t(1) << 33)) return PMWA_ETIMEOUT;
+  // states at the start of the circles after Step 2 (used if a list empties)
+  if (nA) baseA = kab(KA[nA - 1]);
+  if (nB) baseB = kab(KB[nB - 1]);
   // Step 3 on this bond: erase its diagonal vertices, lay new ones
-  if (!rc) {
-    int nA = cnt_n(d.cntA[a]), nB = cnt_n(d.cntA[b]);
-    for (int k = nA - 1; k >= 0; --k) {
+  {
+    int wa = 0;
+    for (int k = 0; k < nA; ++k) {
       const uint64_t key = KA[k];
-      if (ktag(key) != tag || kab(key) != kbl(key)) continue;
-      const int kb = slot_find(KB, nB, kpk(key));
-      aslot_erase(KA, nA, k); --nA;
-      if (kb < 0) { rc = PMWA_EINVARIANT; break; }
-      aslot_erase(KB, nB, kb); --nB;
+      if (ktag(key) == uint64_t(tag) && kab(key) == kbl(key)) continue;
+      KA[wa++] = key;
     }
-    if (!rc && d.has_vertices) {
-      Stream sv;
-      sv.init(d.key0, d.key1, uint32_t(bid), c2_word(kVertex, 0, d.replica), d.sweep);
-      uint64_t pos = 0;
-      bool first = true;
-      const int baseA = cnt_base(d.cntA[a]), baseB = cnt_base(d.cntA[b]);
-      int bad = 0;
-      for (;;) {
-        const double E = zig_exp(Z, sv, &bad);
-        if (bad) { rc = bad; break; }
-        const uint64_t g = grid_gap(E, d.SV);
-        const uint64_t nxt = first ? g - 1 : pos + g;
-        first = false;
-        if (nxt >= kTwo59) break;
-        pos = nxt;
-        const uint64_t pk = (pos << 3) | uint64_t(tag);
-        if (slot_find(KA, nA, pk) >= 0) continue;
-        const int na = slot_state(KA, nA, baseA, pk), nb = slot_state(KB, nB, baseB, pk);
-        const int si = na | (nb << 1);
-        if (d.TV[si] < kTwo32) {
-          const uint64_t w = sv.word();
-          if ((w >> 32) >= d.TV[si]) continue;
-        }
-        if (nA >= d.cap || nB >= d.cap) { rc = PMWA_ECAPACITY; break; }
-        aslot_insert(KA, nA, slot_lower(KA, nA, pk), (pk << 2) | (uint64_t(na) << 1) | uint64_t(na));
-        ++nA;
-        aslot_insert(KB, nB, slot_lower(KB, nB, pk), (pk << 2) | (uint64_t(nb) << 1) | uint64_t(nb));
-        ++nB;
-      }
+    const int removed = nA - wa;
+    nA = wa;
+    int wb = 0, gone = 0;
+    for (int k = 0; k < nB; ++k) {
+      const uint64_t key = KB[k];
+      if (ktag(key) == uint64_t(tag) && kab(key) == kbl(key)) { ++gone; continue; }
+      KB[wb++] = key;
     }
-    d.cntA[a] = cnt_make(nA, nA ? kab(KA[nA - 1]) : cnt_base(d.cntA[a]));
-    d.cntA[b] = cnt_make(nB, nB ? kab(KB[nB - 1]) : cnt_base(d.cntA[b]));
+    nB = wb;
+    if (gone != removed) return PMWA_EINVARIANT;
   }
-  if (!rc && st.pos >= (uint64_t(1) << 33)) rc = PMWA_ETIMEOUT;
-  if (rc) set_err(d.err, rc, 2);
+  if (!d.has_vertices) return PMWA_OK;
+  Stream sv;
+  sv.init(d.key0, d.key1, uint32_t(bid), c2_word(kVertex, 0, d.replica), d.sweep);
+  uint64_t pos = 0;
+  bool first = true;
+  int bad = 0;
+  for (;;) {
+    const double E = zig_exp(Z, sv, &bad);
+    if (bad) return bad;
+    const uint64_t g = grid_gap(E, d.SV);
+    const uint64_t nxt = first ? g - 1 : pos + g;
+    first = false;
+    if (nxt >= kTwo59) break;
+    pos = nxt;
+    const uint64_t pk = (pos << 3) | uint64_t(tag);
+    if (slot_find(KA, nA, pk) >= 0) continue;
+    const int na = slot_state(KA, nA, baseA, pk), nb = slot_state(KB, nB, baseB, pk);
+    const int si = na | (nb << 1);
+    if (d.TV[si] < kTwo32) {
+      const uint64_t w = sv.word();
+      if ((w >> 32) >= d.TV[si]) continue;
+    }
+    if (nA >= d.cap || nB >= d.cap) return PMWA_ECAPACITY;
+    aslot_insert(KA, nA, slot_lower(KA, nA, pk), (pk << 2) | (uint64_t(na) << 1) | uint64_t(na));
+    ++nA;
+    aslot_insert(KB, nB, slot_lower(KB, nB, pk), (pk << 2) | (uint64_t(nb) << 1) | uint64_t(nb));
+    ++nB;
+  }
+  return PMWA_OK;
 }
 
-__global__ void k_boundary(const __grid_constant__ Dev d, int dir) {
-  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
-  const ZigTab Z = zig_stage(zbuf);
-  __syncthreads();
-  boundary_body(d, dir, int(blockIdx.x * blockDim.x + threadIdx.x), Z);
+// One block of 32 threads serves `bpb` boundary bonds t0 .. t0 + bpb - 1 of
+// one instance.  The two site lists of every bond are copied into shared
+// memory by the whole warp (coalesced), updated there by the bond's own
+// thread, and copied back.  stage: 2 * bpb * cap event keys.
+__device__ void boundary_block(const Dev& d, int dir, int t0, int bpb, uint64_t* stage, const ZigTab& Z) {
+  const int lane = threadIdx.x;
+  const int nbonds = boundary_count(d, dir);
+  const bool mine = lane < bpb && t0 + lane < nbonds;
+  int a = 0, b = 0, nA = 0, nB = 0, baseA = 0, baseB = 0;
+  if (mine) {
+    a = boundary_site(d, dir, t0 + lane);
+    b = site_step(d, a, dir, +1);
+    const uint32_t ca = d.cntA[a], cb = d.cntA[b];
+    nA = cnt_n(ca); baseA = cnt_base(ca);
+    nB = cnt_n(cb); baseB = cnt_base(cb);
+  }
+  // copy in: for every bond of the block, the warp reads its two lists
+  for (int j = 0; j < bpb; ++j) {
+    const int aj = __shfl_sync(0xffffffffu, a, j), bj = __shfl_sync(0xffffffffu, b, j);
+    const int naj = __shfl_sync(0xffffffffu, nA, j), nbj = __shfl_sync(0xffffffffu, nB, j);
+    const uint64_t* ga = d.keyA + size_t(aj) * d.cap;
+    const uint64_t* gb = d.keyA + size_t(bj) * d.cap;
+    uint64_t* sa = stage + size_t(2 * j) * d.cap;
+    uint64_t* sb = sa + d.cap;
+    for (int k = lane; k < naj; k += 32) sa[k] = ga[k];
+    for (int k = lane; k < nbj; k += 32) sb[k] = gb[k];
+  }
+  __syncwarp();
+  int rc = PMWA_OK;
+  if (mine) {
+    uint64_t* sa = stage + size_t(2 * lane) * d.cap;
+    rc = boundary_bond_update(d, a, dir, sa, nA, baseA, sa + d.cap, nB, baseB, Z);
+  }
+  __syncwarp();
+  if (mine && rc) set_err(d.err, rc, 2);
+  const int ok = mine && rc == PMWA_OK;
+  // copy out the updated lists of the bonds that succeeded
+  for (int j = 0; j < bpb; ++j) {
+    if (!__shfl_sync(0xffffffffu, ok, j)) continue;
+    const int aj = __shfl_sync(0xffffffffu, a, j), bj = __shfl_sync(0xffffffffu, b, j);
+    const int naj = __shfl_sync(0xffffffffu, nA, j), nbj = __shfl_sync(0xffffffffu, nB, j);
+    uint64_t* ga = d.keyA + size_t(aj) * d.cap;
+    uint64_t* gb = d.keyA + size_t(bj) * d.cap;
+    const uint64_t* sa = stage + size_t(2 * j) * d.cap;
+    const uint64_t* sb = sa + d.cap;
+    for (int k = lane; k < naj; k += 32) ga[k] = sa[k];
+    for (int k = lane; k < nbj; k += 32) gb[k] = sb[k];
+  }
+  if (ok) {
+    const uint64_t* sa = stage + size_t(2 * lane) * d.cap;
+    d.cntA[a] = cnt_make(nA, nA ? kab(sa[nA - 1]) : baseA);
+    d.cntA[b] = cnt_make(nB, nB ? kab(sa[d.cap + nB - 1]) : baseB);
+  }
 }
 
-// Batched form: each block serves bonds [t0, t0 + blockDim) of one instance,
-// which takes part only when its boundary step is due at iteration `it`.
-__global__ void k_boundary_batch(const Dev* __restrict__ devs, const BatchBase* __restrict__ base,
-                                 const int2* __restrict__ work, int it, int dir) {
-  __shared__ __align__(16) unsigned char zbuf[kZigBytes];
+__global__ void __launch_bounds__(32) k_boundary(const __grid_constant__ Dev d, int dir, int bpb) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const ZigTab Z = zig_stage(bsm);
+  __syncwarp();
+  boundary_block(d, dir, int(blockIdx.x) * bpb, bpb, reinterpret_cast<uint64_t*>(bsm + kZigBytes), Z);
+}
+
+// Batched form: each block serves one instance's bonds from t0, when that
+// instance's boundary step is due at iteration `it`.
+__global__ void __launch_bounds__(32) k_boundary_batch(const Dev* __restrict__ devs,
+                                                       const BatchBase* __restrict__ base,
+                                                       const int2* __restrict__ work, int it, int dir, int bpb) {
+  extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ Dev sd;
   const int2 w = work[blockIdx.x];
-  const BatchBase b = base[w.x];
-  if (!b.active) return;
-  if (threadIdx.x == 0) sd = at_iteration(devs[w.x], b, it);
-  const ZigTab Z = zig_stage(zbuf);
-  __syncthreads();
+  const BatchBase bb = base[w.x];
+  if (!bb.active) return;
+  if (threadIdx.x == 0) sd = at_iteration(devs[w.x], bb, it);
+  const ZigTab Z = zig_stage(bsm);
+  __syncwarp();
   if (sd.ndom < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
-  boundary_body(sd, dir, w.y + int(threadIdx.x), Z);
+  boundary_block(sd, dir, w.y, bpb, reinterpret_cast<uint64_t*>(bsm + kZigBytes), Z);
 }
 
 // ---------------------------------------------------------------------------
 // Launchers.
-static inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
 
 int upload_zig(const Zig& z) { return upload_constants(z); }
 
@@ -285,17 +350,38 @@ int launch_advance(BatchBase* base, int n, int S, void* stream) {
   return int(cudaGetLastError());
 }
 
+// bonds per block of the boundary kernels for a per-site capacity `cap`
+int boundary_bonds_per_block(int cap) {
+  const int room = (200 * 1024 - kZigBytes) / (16 * cap);
+  return room < 1 ? 1 : (room > 32 ? 32 : room);
+}
+
+size_t boundary_smem(int cap, int bpb) { return size_t(kZigBytes) + size_t(2 * bpb) * size_t(cap) * 8; }
+
+int prepare_boundary(int cap) {
+  const int bpb = boundary_bonds_per_block(cap);
+  cudaError_t e = cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, int(boundary_smem(cap, bpb)));
+  if (e) return int(e);
+  return int(cudaFuncSetAttribute(k_boundary_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(boundary_smem(cap, bpb))));
+}
+
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
-                          void* stream) {
+                          int cap, void* stream) {
   if (n_work <= 0) return 0;
-  k_boundary_batch<<<n_work, kBoundaryThreads, 0, cudaStream_t(stream)>>>(devs, base, work, it, dir);
+  const int bpb = boundary_bonds_per_block(cap);
+  k_boundary_batch<<<n_work, 32, boundary_smem(cap, bpb), cudaStream_t(stream)>>>(devs, base, work, it, dir, bpb);
   return int(cudaGetLastError());
 }
 
 int launch_boundary(const Dev& d, int dir, void* stream) {
   const long long n = dir == 0 ? (long long)d.ndx * d.Ly : (long long)d.ndy * d.Lx;
   if ((dir == 0 && d.ndx < 2) || (dir == 1 && d.ndy < 2)) return 0;
-  k_boundary<<<blocks_for(n, kBoundaryThreads), kBoundaryThreads, 0, cudaStream_t(stream)>>>(d, dir);
+  const int bpb = boundary_bonds_per_block(d.cap);
+  cudaError_t e = cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(boundary_smem(d.cap, bpb)));
+  if (e) return int(e);
+  k_boundary<<<blocks_for(n, bpb), 32, boundary_smem(d.cap, bpb), cudaStream_t(stream)>>>(d, dir, bpb);
   return int(cudaGetLastError());
 }
 

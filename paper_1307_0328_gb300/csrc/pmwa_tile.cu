@@ -496,7 +496,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     // ---- phase 4: Step 5
     if (stop >= 5) {
       const int nw = misc->nworms;
-      for (int pass = 0; pass < d.n_cycle; ++pass) {
+      for (int pass = 0; pass < (nw > 0 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
         __syncthreads();
         const int q = pass & 3;

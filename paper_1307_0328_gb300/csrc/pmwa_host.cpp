@@ -667,9 +667,10 @@ struct pmwa_batch {
   Dev* devs = nullptr;
   BatchBase* base = nullptr;
   DevErr* errs = nullptr;
-  int2* tile_work = nullptr;
+  int2* tile_work = nullptr;  // grouped by CTA-size class
   int2* bwork[2] = {nullptr, nullptr};
-  int n_tile = 0, n_bwork[2] = {0, 0}, smem = 0, cap_max = 0;
+  int n_tile = 0, n_bwork[2] = {0, 0}, cap_max = 0;
+  int cls_off[3] = {0, 0, 0}, cls_n[3] = {0, 0, 0}, cls_smem[3] = {0, 0, 0};
   cudaGraphExec_t graph = nullptr;
   int graph_sweeps = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -716,19 +717,28 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   return true;
 }
 
-// work items in decreasing estimated cost, so the longest CTAs start first
+// work items grouped by CTA-size class, each group in decreasing estimated
+// cost, so that the longest CTAs start first
 void build_tile_work(pmwa_batch* b, std::vector<int2>* work) {
-  std::vector<std::pair<double, int2>> items;
-  for (int i = 0; i < b->n; ++i) {
-    const Dev& d = b->h[size_t(i)]->d;
-    const double cost = double(d.dom_x * d.dom_y) * b->h[size_t(i)]->p.beta *
-                        (d.dvw[0] + d.tkink + 1.0) * double(d.n_cycle + 4);
-    for (int k = 0; k < d.ndom; ++k) items.push_back({cost, make_int2(i, k)});
-  }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) { return x.first > y.first; });
   work->clear();
-  for (const auto& it : items) work->push_back(it.second);
+  for (int c = 0; c < 3; ++c) {
+    std::vector<std::pair<double, int2>> items;
+    int smem = 0;
+    for (int i = 0; i < b->n; ++i) {
+      const Dev& d = b->h[size_t(i)]->d;
+      if (tile_class(d.dom_x * d.dom_y) != c) continue;
+      smem = std::max(smem, d.sm_total);
+      const double cost = double(d.dom_x * d.dom_y) * b->h[size_t(i)]->p.beta *
+                          (d.dvw[0] + d.tkink + 1.0) * double(d.n_cycle + 4);
+      for (int k = 0; k < d.ndom; ++k) items.push_back({cost, make_int2(i, k)});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) { return x.first > y.first; });
+    b->cls_off[c] = int(work->size());
+    b->cls_n[c] = int(items.size());
+    b->cls_smem[c] = smem;
+    for (const auto& it : items) work->push_back(it.second);
+  }
 }
 
 int batch_upload(pmwa_batch* b) {
@@ -740,6 +750,8 @@ int batch_upload(pmwa_batch* b) {
   if (cudaMemcpy(b->devs, devs.data(), devs.size() * sizeof(Dev), cudaMemcpyHostToDevice) ||
       cudaMemcpy(b->tile_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
+  for (int c = 0; c < 3; ++c)
+    if (b->cls_n[c] && prepare_tile_batch(c, b->cls_smem[c])) return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -755,7 +767,10 @@ int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
     if (b->n_bwork[dir] &&
         launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, b->cap_max, st))
       return PMWA_ECUDA;
-  if (launch_tile_batch(b->devs, b->base, b->tile_work, b->n_tile, b->smem, it, 6, st)) return PMWA_ECUDA;
+  for (int c = 2; c >= 0; --c)
+    if (b->cls_n[c] && launch_tile_batch(c, b->devs, b->base, b->tile_work + b->cls_off[c], b->cls_n[c],
+                                         b->cls_smem[c], it, 6, st))
+      return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -797,7 +812,6 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     if (rc) break;
     pmwa_handle* hi = b->h[size_t(i)];
     hi->err = hi->d.err = b->errs + i;  // one contiguous error array for the batch
-    b->smem = std::max(b->smem, hi->d.sm_total);
     b->cap_max = std::max(b->cap_max, hi->d.cap);
   }
   if (rc == PMWA_OK && cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
@@ -818,7 +832,7 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     }
   }
   if (rc == PMWA_OK) rc = batch_upload(b);
-  if (rc == PMWA_OK && (prepare_tile_batch(b->smem) || prepare_boundary(b->cap_max))) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
   if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
                         cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
     rc = PMWA_ECUDA;

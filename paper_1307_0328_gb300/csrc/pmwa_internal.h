@@ -98,13 +98,14 @@ int upload_zig(const Zig& z);       // constants of pmwa_kernels.cu
 int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_tile(const Dev& d, int stop, void* stream);
-int launch_tile_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem, int it,
-                      int stop, void* stream);
+int tile_class(int domain_sites);
+int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem,
+                      int it, int stop, void* stream);
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
                           int cap, void* stream);
 int boundary_bonds_per_block(int cap);
 int prepare_boundary(int cap);
-int prepare_tile_batch(int smem);
+int prepare_tile_batch(int cls, int smem);
 int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
 // rho slices through the library's own static device scratch (no allocation)

@@ -158,14 +158,23 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
     any = true;
     Legs La, Lb;
     if (!site_legs(KA, nA, pv, &La) || !site_legs(KB, nB, pv, &Lb)) return PMWA_EINVARIANT;
-    double ea_dn = 0.0, eb_dn = 0.0, ea_up, eb_up;
-    if (La.single) ea_up = em1_of(kTwo59, d.XW);
-    else { ea_dn = em1_of(La.Idn, d.XW); ea_up = em1_of(La.Iup, d.XW); }
-    if (Lb.single) eb_up = em1_of(kTwo59, d.XW);
-    else { eb_dn = em1_of(Lb.Idn, d.XW); eb_up = em1_of(Lb.Iup, d.XW); }
-    double cum[16], tot = 0.0;
-    int lastS = -1;
-    for (int S = 0; S < 16; ++S) {
+    // heat-bath over the root states (Eq. 4), one lane per leg factor and one
+    // lane per state; the weights are summed in the fixed order S = 0..15
+    const int lane = threadIdx.x & 31;
+    double e4 = 0.0;
+    if (lane < 4) {
+      uint64_t I;
+      if (lane == 0) I = La.single ? kTwo59 : La.Idn;
+      else if (lane == 1) I = Lb.single ? kTwo59 : Lb.Idn;
+      else if (lane == 2) I = La.single ? kTwo59 : La.Iup;
+      else I = Lb.single ? kTwo59 : Lb.Iup;
+      e4 = em1_of(I, d.XW);
+    }
+    const double ea_dn = __shfl_sync(0xffffffffu, e4, 0), eb_dn = __shfl_sync(0xffffffffu, e4, 1);
+    const double ea_up = __shfl_sync(0xffffffffu, e4, 2), eb_up = __shfl_sync(0xffffffffu, e4, 3);
+    double wS = 0.0;
+    if (lane < 16) {
+      const int S = lane;
       double w = vweight(d, S);
       if (w > 0.0) {
         const int s0 = S & 1, s1 = (S >> 1) & 1, s2 = (S >> 2) & 1, s3 = (S >> 3) & 1;
@@ -173,15 +182,20 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
         if (!Lb.single) w = __dmul_rn(w, fsig(Lb.far_dn ^ s1, eb_dn));
         w = __dmul_rn(w, La.single ? fsig(s2 ^ s0, ea_up) : fsig(s2 ^ La.far_up, ea_up));
         w = __dmul_rn(w, Lb.single ? fsig(s3 ^ s1, eb_up) : fsig(s3 ^ Lb.far_up, eb_up));
-        if (w > 0.0) lastS = S;
       }
-      tot = __dadd_rn(tot, w);
-      cum[S] = tot;
+      wS = w;
     }
-    if (lastS < 0) return PMWA_EINVARIANT;
+    double tot = 0.0, cumS = 0.0;
+    for (int S = 0; S < 16; ++S) {
+      tot = __dadd_rn(tot, __shfl_sync(0xffffffffu, wS, S));
+      if (lane == S) cumS = tot;
+    }
+    const unsigned pos = __ballot_sync(0xffffffffu, lane < 16 && wS > 0.0);
+    if (!pos) return PMWA_EINVARIANT;
+    const int lastS = 31 - __clz(int(pos));
     const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
-    int Sn = lastS;
-    for (int S = 0; S < 16; ++S) if (u < cum[S]) { Sn = S; break; }
+    const unsigned hit = __ballot_sync(0xffffffffu, lane < 16 && u < cumS);
+    const int Sn = hit ? (__ffs(int(hit)) - 1) : lastS;
     const int s0 = Sn & 1, s1 = (Sn >> 1) & 1, s2 = (Sn >> 2) & 1, s3 = (Sn >> 3) & 1;
     {
       const int ka = slot_find(KA, nA, pv), kb = slot_find(KB, nB, pv);
@@ -251,73 +265,58 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
   return PMWA_OK;
 }
 
-// One block of 32 threads serves `bpb` boundary bonds t0 .. t0 + bpb - 1 of
-// one instance.  The two site lists of every bond are copied into shared
-// memory by the whole warp (coalesced), updated there by the bond's own
-// thread, and copied back.  stage: 2 * bpb * cap event keys.
-__device__ void boundary_block(const Dev& d, int dir, int t0, int bpb, uint64_t* stage, const ZigTab& Z) {
-  const int lane = threadIdx.x;
-  const int nbonds = boundary_count(d, dir);
-  const bool mine = lane < bpb && t0 + lane < nbonds;
-  int a = 0, b = 0, nA = 0, nB = 0, baseA = 0, baseB = 0;
-  if (mine) {
-    a = boundary_site(d, dir, t0 + lane);
-    b = site_step(d, a, dir, +1);
-    const uint32_t ca = d.cntA[a], cb = d.cntA[b];
-    nA = cnt_n(ca); baseA = cnt_base(ca);
-    nB = cnt_n(cb); baseB = cnt_base(cb);
-  }
-  // copy in: for every bond of the block, the warp reads its two lists
-  for (int j = 0; j < bpb; ++j) {
-    const int aj = __shfl_sync(0xffffffffu, a, j), bj = __shfl_sync(0xffffffffu, b, j);
-    const int naj = __shfl_sync(0xffffffffu, nA, j), nbj = __shfl_sync(0xffffffffu, nB, j);
-    const uint64_t* ga = d.keyA + size_t(aj) * d.cap;
-    const uint64_t* gb = d.keyA + size_t(bj) * d.cap;
-    uint64_t* sa = stage + size_t(2 * j) * d.cap;
-    uint64_t* sb = sa + d.cap;
-    for (int k = lane; k < naj; k += 32) sa[k] = ga[k];
-    for (int k = lane; k < nbj; k += 32) sb[k] = gb[k];
-  }
+// One warp per boundary bond.  The warp copies the bond's two site lists
+// into its shared-memory stage (coalesced), every lane then runs the same
+// update on the same data (so nothing diverges; lanes split only the
+// heat-bath arithmetic), and the warp copies the lists back.  stage: 2 * cap
+// event keys for this warp.
+__device__ void boundary_warp(const Dev& d, int dir, int t, uint64_t* stage, const ZigTab& Z) {
+  const int lane = threadIdx.x & 31;
+  if (t >= boundary_count(d, dir)) return;
+  const int a = boundary_site(d, dir, t);
+  const int b = site_step(d, a, dir, +1);
+  const uint32_t ca = d.cntA[a], cb = d.cntA[b];
+  int nA = cnt_n(ca), baseA = cnt_base(ca), nB = cnt_n(cb), baseB = cnt_base(cb);
+  const uint64_t* ga = d.keyA + size_t(a) * d.cap;
+  const uint64_t* gb = d.keyA + size_t(b) * d.cap;
+  uint64_t* sa = stage;
+  uint64_t* sb = stage + d.cap;
+  for (int k = lane; k < nA; k += 32) sa[k] = ga[k];
+  for (int k = lane; k < nB; k += 32) sb[k] = gb[k];
   __syncwarp();
-  int rc = PMWA_OK;
-  if (mine) {
-    uint64_t* sa = stage + size_t(2 * lane) * d.cap;
-    rc = boundary_bond_update(d, a, dir, sa, nA, baseA, sa + d.cap, nB, baseB, Z);
-  }
+  const int rc = boundary_bond_update(d, a, dir, sa, nA, baseA, sb, nB, baseB, Z);
   __syncwarp();
-  if (mine && rc) set_err(d.err, rc, 2);
-  const int ok = mine && rc == PMWA_OK;
-  // copy out the updated lists of the bonds that succeeded
-  for (int j = 0; j < bpb; ++j) {
-    if (!__shfl_sync(0xffffffffu, ok, j)) continue;
-    const int aj = __shfl_sync(0xffffffffu, a, j), bj = __shfl_sync(0xffffffffu, b, j);
-    const int naj = __shfl_sync(0xffffffffu, nA, j), nbj = __shfl_sync(0xffffffffu, nB, j);
-    uint64_t* ga = d.keyA + size_t(aj) * d.cap;
-    uint64_t* gb = d.keyA + size_t(bj) * d.cap;
-    const uint64_t* sa = stage + size_t(2 * j) * d.cap;
-    const uint64_t* sb = sa + d.cap;
-    for (int k = lane; k < naj; k += 32) ga[k] = sa[k];
-    for (int k = lane; k < nbj; k += 32) gb[k] = sb[k];
+  if (rc) {
+    if (lane == 0) set_err(d.err, rc, 2);
+    return;
   }
-  if (ok) {
-    const uint64_t* sa = stage + size_t(2 * lane) * d.cap;
+  uint64_t* wa = d.keyA + size_t(a) * d.cap;
+  uint64_t* wb = d.keyA + size_t(b) * d.cap;
+  for (int k = lane; k < nA; k += 32) wa[k] = sa[k];
+  for (int k = lane; k < nB; k += 32) wb[k] = sb[k];
+  if (lane == 0) {
     d.cntA[a] = cnt_make(nA, nA ? kab(sa[nA - 1]) : baseA);
-    d.cntA[b] = cnt_make(nB, nB ? kab(sa[d.cap + nB - 1]) : baseB);
+    d.cntA[b] = cnt_make(nB, nB ? kab(sb[nB - 1]) : baseB);
   }
 }
 
-__global__ void __launch_bounds__(32) k_boundary(const __grid_constant__ Dev d, int dir, int bpb) {
+constexpr int kBoundaryWarps = 4;  // bonds (warps) per block
+
+__global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary(const __grid_constant__ Dev d, int dir) {
   extern __shared__ __align__(16) unsigned char bsm[];
   const ZigTab Z = zig_stage(bsm);
-  __syncwarp();
-  boundary_block(d, dir, int(blockIdx.x) * bpb, bpb, reinterpret_cast<uint64_t*>(bsm + kZigBytes), Z);
+  __syncthreads();
+  const int wid = threadIdx.x >> 5;
+  uint64_t* stage = reinterpret_cast<uint64_t*>(bsm + kZigBytes) + size_t(2 * wid) * d.cap;
+  boundary_warp(d, dir, int(blockIdx.x) * kBoundaryWarps + wid, stage, Z);
 }
 
-// Batched form: each block serves one instance's bonds from t0, when that
-// instance's boundary step is due at iteration `it`.
-__global__ void __launch_bounds__(32) k_boundary_batch(const Dev* __restrict__ devs,
-                                                       const BatchBase* __restrict__ base,
-                                                       const int2* __restrict__ work, int it, int dir, int bpb) {
+// Batched form: each block serves bonds t0 .. t0 + kBoundaryWarps - 1 of one
+// instance, when that instance's boundary step is due at iteration `it`.
+__global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary_batch(const Dev* __restrict__ devs,
+                                                                        const BatchBase* __restrict__ base,
+                                                                        const int2* __restrict__ work, int it,
+                                                                        int dir, int cap) {
   extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ Dev sd;
   const int2 w = work[blockIdx.x];
@@ -325,9 +324,11 @@ __global__ void __launch_bounds__(32) k_boundary_batch(const Dev* __restrict__ d
   if (!bb.active) return;
   if (threadIdx.x == 0) sd = at_iteration(devs[w.x], bb, it);
   const ZigTab Z = zig_stage(bsm);
-  __syncwarp();
+  __syncthreads();
   if (sd.ndom < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
-  boundary_block(sd, dir, w.y, bpb, reinterpret_cast<uint64_t*>(bsm + kZigBytes), Z);
+  const int wid = threadIdx.x >> 5;
+  uint64_t* stage = reinterpret_cast<uint64_t*>(bsm + kZigBytes) + size_t(2 * wid) * cap;
+  boundary_warp(sd, dir, w.y + wid, stage, Z);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,38 +351,33 @@ int launch_advance(BatchBase* base, int n, int S, void* stream) {
   return int(cudaGetLastError());
 }
 
-// bonds per block of the boundary kernels for a per-site capacity `cap`
-int boundary_bonds_per_block(int cap) {
-  const int room = (200 * 1024 - kZigBytes) / (16 * cap);
-  return room < 1 ? 1 : (room > 32 ? 32 : room);
-}
+// bonds per block of the boundary kernels (one warp each)
+int boundary_bonds_per_block(int cap) { (void)cap; return kBoundaryWarps; }
 
-size_t boundary_smem(int cap, int bpb) { return size_t(kZigBytes) + size_t(2 * bpb) * size_t(cap) * 8; }
+size_t boundary_smem(int cap) { return size_t(kZigBytes) + size_t(2 * kBoundaryWarps) * size_t(cap) * 8; }
 
 int prepare_boundary(int cap) {
-  const int bpb = boundary_bonds_per_block(cap);
-  cudaError_t e = cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, int(boundary_smem(cap, bpb)));
+  cudaError_t e = cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize, int(boundary_smem(cap)));
   if (e) return int(e);
   return int(cudaFuncSetAttribute(k_boundary_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(boundary_smem(cap, bpb))));
+                                  int(boundary_smem(cap))));
 }
 
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,
                           int cap, void* stream) {
   if (n_work <= 0) return 0;
-  const int bpb = boundary_bonds_per_block(cap);
-  k_boundary_batch<<<n_work, 32, boundary_smem(cap, bpb), cudaStream_t(stream)>>>(devs, base, work, it, dir, bpb);
+  k_boundary_batch<<<n_work, 32 * kBoundaryWarps, boundary_smem(cap), cudaStream_t(stream)>>>(devs, base, work, it,
+                                                                                            dir, cap);
   return int(cudaGetLastError());
 }
 
 int launch_boundary(const Dev& d, int dir, void* stream) {
   const long long n = dir == 0 ? (long long)d.ndx * d.Ly : (long long)d.ndy * d.Lx;
   if ((dir == 0 && d.ndx < 2) || (dir == 1 && d.ndy < 2)) return 0;
-  const int bpb = boundary_bonds_per_block(d.cap);
   cudaError_t e = cudaFuncSetAttribute(k_boundary, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(boundary_smem(d.cap, bpb)));
+                                       int(boundary_smem(d.cap)));
   if (e) return int(e);
-  k_boundary<<<blocks_for(n, bpb), 32, boundary_smem(d.cap, bpb), cudaStream_t(stream)>>>(d, dir, bpb);
+  k_boundary<<<blocks_for(n, kBoundaryWarps), 32 * kBoundaryWarps, boundary_smem(d.cap), cudaStream_t(stream)>>>(d, dir);
   return int(cudaGetLastError());
 }
 

@@ -667,7 +667,8 @@ fail:
   if (tid == 0) set_err(d.err, misc->err, misc->where);
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ Dev d, int stop) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ Dev d, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wsum[32];
   tile_body(d, int(blockIdx.x), stop, sm, wsum);
@@ -676,9 +677,10 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ D
 // Batched form: one CTA per (instance, domain) work item; the instance's
 // parameters are copied into shared memory and advanced to sweep iteration
 // `it` of the current batch call (buffers, sweep index, row).
-__global__ void __launch_bounds__(kTileThreads) k_tile_batch(const Dev* __restrict__ devs,
-                                                             const BatchBase* __restrict__ base,
-                                                             const int2* __restrict__ work, int it, int stop) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
+                                                   const BatchBase* __restrict__ base,
+                                                   const int2* __restrict__ work, int it, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wsum[32];
   __shared__ Dev sd;
@@ -736,20 +738,53 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
 
 int upload_zig_tile(const Zig& z) { return upload_constants(z); }
 
-int prepare_tile_batch(int smem) {
-  return int(cudaFuncSetAttribute(k_tile_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+// CTA sizes of the sweep kernel: small domains take small CTAs, so that many
+// of them share an SM (class 0: 64 threads, 1: 128, 2: 256)
+int tile_class(int domain_sites) { return domain_sites <= 32 ? 0 : (domain_sites <= 96 ? 1 : 2); }
+static constexpr int kClassThreads[3] = {64, 128, 256};
+
+int prepare_tile_batch(int cls, int smem) {
+  cudaError_t e;
+  switch (cls) {
+    case 0: e = cudaFuncSetAttribute(k_tile_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 1: e = cudaFuncSetAttribute(k_tile_batch<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    default: e = cudaFuncSetAttribute(k_tile_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+  }
+  return int(e);
 }
 
-int launch_tile_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem, int it,
-                      int stop, void* stream) {
-  k_tile_batch<<<n_work, kTileThreads, smem, cudaStream_t(stream)>>>(devs, base, work, it, stop);
+int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem,
+                      int it, int stop, void* stream) {
+  if (n_work <= 0) return 0;
+  const cudaStream_t st = cudaStream_t(stream);
+  switch (cls) {
+    case 0: k_tile_batch<64><<<n_work, 64, smem, st>>>(devs, base, work, it, stop); break;
+    case 1: k_tile_batch<128><<<n_work, 128, smem, st>>>(devs, base, work, it, stop); break;
+    default: k_tile_batch<256><<<n_work, 256, smem, st>>>(devs, base, work, it, stop); break;
+  }
   return int(cudaGetLastError());
 }
 
 int launch_tile(const Dev& d, int stop, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+  const int cls = tile_class(d.dom_x * d.dom_y);
+  const cudaStream_t st = cudaStream_t(stream);
+  cudaError_t e;
+  switch (cls) {
+    case 0:
+      e = cudaFuncSetAttribute(k_tile<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+      if (!e) k_tile<64><<<d.ndom, 64, d.sm_total, st>>>(d, stop);
+      break;
+    case 1:
+      e = cudaFuncSetAttribute(k_tile<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+      if (!e) k_tile<128><<<d.ndom, 128, d.sm_total, st>>>(d, stop);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+      if (!e) k_tile<256><<<d.ndom, 256, d.sm_total, st>>>(d, stop);
+      break;
+  }
   if (e) return int(e);
-  k_tile<<<d.ndom, kTileThreads, d.sm_total, cudaStream_t(stream)>>>(d, stop);
+  (void)kClassThreads;
   return int(cudaGetLastError());
 }
 

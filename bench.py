@@ -201,6 +201,22 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=12):
     return out
 
 
+# --------------------------------------------------------------------------- serving leg
+def serving_run(n_jobs, scale, budget_gb=64.0):
+    """The first n_jobs of the serving trace (Poisson arrivals at 20 jobs/s, L
+    in {32..1024 step 32}, beta t in {2,4,8,16}, mu in [-1,1], eta = 0.1),
+    each job's 10^3..10^4 sweeps scaled by `scale`, served in real time by
+    the continuous-batching loop with a 64 GB device budget."""
+    from paper_1307_0328_gb300 import serve
+    jobs = serve.poisson_trace(n=n_jobs, rate=20.0, seed=5, sweep_scale=scale)
+    out = serve.run_trace(jobs, int(budget_gb * 1e9), max_jobs=64, chunk=8, realtime=True)
+    return dict(workload="first %d jobs of the 400-job Poisson trace (20 jobs/s, seed 5), sweeps x %g, "
+                         "%g GB budget, continuous batching" % (n_jobs, scale, budget_gb),
+                jobs=out["jobs"], p50_s=out["p50_s"], p99_s=out["p99_s"], wall_s=out["wall_s"],
+                value=out["vertex_updates_per_s"], unit=UNIT,
+                sweeps=int(sum(j.sweeps for j in out["finished"])))
+
+
 # --------------------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -214,6 +230,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-replica comparison")
+    ap.add_argument("--serve-jobs", type=int, default=40, help="jobs of the serving trace to run (0: skip)")
+    ap.add_argument("--serve-scale", type=float, default=0.005, help="factor on each job's sweep count")
     args = ap.parse_args()
     wl = args.workload
     args.warmup = max(args.warmup, 3)
@@ -354,6 +372,8 @@ def main():
         )
         if not args.no_batch:
             line["batched"] = batched_vs_plain(P, args.steps, args.warmup)
+        if args.serve_jobs > 0:
+            line["serving"] = serving_run(args.serve_jobs, args.serve_scale)
         if not args.no_cpu:
             rate, steps, el = oracle_rate(wl, nc, args.cpu_seconds, warmup=1)
             line["cpu_baseline"] = dict(value=rate, unit=UNIT, cores=1, kind="oracle",

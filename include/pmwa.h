@@ -122,6 +122,16 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
    legs) that holds tau_k on site i.  host_out holds N*K doubles. */
 int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out);
 
+/* Equal-time Green functions of Q from the worm densities (Supplement S-I:
+   <prod_k Q(X_k)> = eta^-n <prod_k rho(X_k)> when no two X_k share an
+   interval, which holds for distinct sites at equal time), averaged over
+   sites and the K slices tau_k = k beta / K of the current configuration:
+   gx[r-1] = <Q_i Q_{i+r x}>, gy[r-1] = <Q_i Q_{i+r y}> for r = 1..rmax
+   (rmax <= min(Lx, Ly)/2), and *plaq = <Q_i Q_{i+x} Q_{i+y} Q_{i+x+y}>, the
+   4-point function on a plaquette.  Host outputs; uses the arena's idle
+   next-configuration slots as scratch. */
+int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, double* plaq);
+
 /* The same values as pmwa_rho_slices, for callers that cannot allocate
    device memory while they run (for example a serving loop whose memory is
    owned by another allocator, or one that has promised its pool no new
@@ -178,6 +188,15 @@ int pmwa_batch_set_n_cycle(pmwa_batch* b, int32_t i, int32_t n_cycle);
 /* Device time (CUDA events on the stream) of the last pmwa_batch_sweep. */
 int pmwa_batch_last_ms(pmwa_batch* b, double* ms);
 int pmwa_batch_destroy(pmwa_batch* b);
+/* A batch over existing handles (each created by pmwa_create in its own
+   arena): the configurations stay where they are, so the set of instances
+   advanced together can change between calls without moving any state (the
+   serving pattern).  The arena holds only the batch tables,
+   pmwa_batch_tables_bytes(hs, n) bytes.  Destroying such a batch leaves the
+   handles to the caller. */
+size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n);
+int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* dev_arena, size_t arena_bytes,
+                            void* stream, pmwa_batch** out);
 
 /* Host tables derived from p, for comparison with an independent
    implementation: d4[4] diagonal vertex weights d(s) = C - E(s); *D = max d;

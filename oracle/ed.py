@@ -54,7 +54,8 @@ def hamiltonians(Lx, Ly, t, V, mu, eta):
 
 def thermal(Lx, Ly, beta, t, V, mu, eta, slices_r=True):
     """Exact thermal averages: E/N (of H), <n>, <Q>/N, <b+b+h.c.> per bond,
-    and G_QQ(r) = <Q_i Q_{i+r x^}> averaged over i, r = 1..Lx-1."""
+    G_QQ(r) = <Q_i Q_{i+r x^}> averaged over i, r = 1..Lx-1, and the plaquette
+    4-point function <Q_i Q_{i+x} Q_{i+y} Q_{i+x+y}> averaged over i."""
     N = Lx * Ly
     H, Q = hamiltonians(Lx, Ly, t, V, mu, eta)
     Heta = H - eta * Q
@@ -79,6 +80,16 @@ def thermal(Lx, Ly, beta, t, V, mu, eta, slices_r=True):
             A = np.zeros((dim, dim))
             A[states ^ (1 << i), states] = 1.0
             Qi.append(A)
+        # 4-point function on a plaquette: <Q_i Q_{i+x} Q_{i+y} Q_{i+x+y}>
+        acc = 0.0
+        for y in range(Ly):
+            for x in range(Lx):
+                s0 = x + Lx * y
+                s1 = (x + 1) % Lx + Lx * y
+                s2 = x + Lx * ((y + 1) % Ly)
+                s3 = (x + 1) % Lx + Lx * ((y + 1) % Ly)
+                acc += avg(Qi[s0] @ Qi[s1] @ Qi[s2] @ Qi[s3])
+        out["plaq"] = acc / N
         for r in range(1, Lx):
             acc = 0.0
             for y in range(Ly):

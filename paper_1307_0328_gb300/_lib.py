@@ -63,6 +63,7 @@ def load(build=True):
         "pmwa_measure": (C.c_int, [vp, vp, C.c_int64, P(C.c_int64)]),
         "pmwa_rho_slices": (C.c_int, [vp, C.c_int32, vp]),
         "pmwa_rho_slices_static": (C.c_int, [vp, C.c_int32, vp]),
+        "pmwa_green": (C.c_int, [vp, C.c_int32, C.c_int32, vp, vp, vp]),
         "pmwa_export_bytes": (C.c_int, [vp, P(sz)]),
         "pmwa_export": (C.c_int, [vp, vp, sz]),
         "pmwa_import": (C.c_int, [vp, vp, sz]),
@@ -83,6 +84,8 @@ def load(build=True):
         "pmwa_batch_set_n_cycle": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "pmwa_batch_last_ms": (C.c_int, [vp, P(C.c_double)]),
         "pmwa_batch_destroy": (C.c_int, [vp]),
+        "pmwa_batch_tables_bytes": (sz, [vp, C.c_int32]),
+        "pmwa_batch_from_handles": (C.c_int, [vp, C.c_int32, vp, sz, vp, P(vp)]),
         "pmwa_profile_read": (C.c_int, [vp, vp, vp, C.c_int32]),
         "pmwa_profile_phases": (C.c_int, [vp, vp, C.c_int32]),
     }
@@ -153,6 +156,16 @@ def pmwa_rho_slices(h, N, K):
     out = np.zeros((N, K), dtype=np.float64)
     _check("pmwa_rho_slices", load().pmwa_rho_slices(h, K, out.ctypes.data))
     return out
+
+
+def pmwa_green(h, K, rmax):
+    """Equal-time <Q_i Q_{i+r}> along x and y (r = 1..rmax) and the plaquette
+    4-point function, from the worm densities of the current configuration."""
+    gx = np.zeros(rmax)
+    gy = np.zeros(rmax)
+    pl = C.c_double()
+    _check("pmwa_green", load().pmwa_green(h, K, rmax, gx.ctypes.data, gy.ctypes.data, C.byref(pl)))
+    return gx, gy, pl.value
 
 
 def pmwa_rho_slices_static(h, N, K):

@@ -562,6 +562,30 @@ int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
   return PMWA_OK;
 }
 
+int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, double* plaq) {
+  if (!h || K < 1 || rmax < 0 || !gx || !gy || !plaq) return PMWA_EINVAL;
+  if (rmax > std::min(h->p.Lx, h->p.Ly) / 2) return PMWA_EINVAL;
+  const size_t N = size_t(h->d.N);
+  // scratch: the idle next-configuration slots hold rho, then the sums
+  if (N * size_t(K) + size_t(2 * rmax + 1) > N * size_t(h->d.cap)) return PMWA_EINVAL;
+  double* rho = reinterpret_cast<double*>(h->d.keyB);
+  double* sums = rho + N * size_t(K);
+  if (launch_rho(h->d, K, rho, h->stream)) return PMWA_ECUDA;
+  if (cudaMemsetAsync(sums, 0, size_t(2 * rmax + 1) * sizeof(double), h->stream)) return PMWA_ECUDA;
+  if (launch_green(h->p.Lx, h->p.Ly, K, rmax, rho, sums, h->stream)) return PMWA_ECUDA;
+  std::vector<double> out(size_t(2 * rmax + 1));
+  if (cudaStreamSynchronize(h->stream) ||
+      cudaMemcpy(out.data(), sums, out.size() * sizeof(double), cudaMemcpyDeviceToHost))
+    return PMWA_ECUDA;
+  const double eta = h->p.eta, norm = double(N) * double(K);
+  for (int r = 0; r < rmax; ++r) {
+    gx[r] = out[size_t(r)] / norm / (eta * eta);
+    gy[r] = out[size_t(rmax + r)] / norm / (eta * eta);
+  }
+  *plaq = out[size_t(2 * rmax)] / norm / (eta * eta * eta * eta);
+  return PMWA_OK;
+}
+
 int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out) {
   if (!h) return PMWA_EINVAL;
   int dev = -1;
@@ -676,6 +700,8 @@ struct pmwa_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
   bool dirty = false;  // instance parameters changed since the last upload
+  bool borrowed = false;               // instances belong to the caller
+  std::vector<DevErr*> own_err;        // their error words, restored at destroy
 };
 
 namespace {
@@ -846,6 +872,87 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
   return PMWA_OK;
 }
 
+size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n) {
+  if (!hs || n < 1 || n > 65536) return 0;
+  int n_tile = 0, n_bw[2] = {0, 0};
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return 0;
+    const Dev& d = hs[i]->d;
+    n_tile += d.ndom;
+    n_bw[0] += d.ndx > 1 ? d.ndx * d.Ly : 0;
+    n_bw[1] += d.ndy > 1 ? d.ndy * d.Lx : 0;
+  }
+  size_t o = 0;
+  o = align_up(o + size_t(n) * sizeof(Dev));
+  o = align_up(o + size_t(n) * sizeof(BatchBase));
+  o = align_up(o + size_t(n) * sizeof(DevErr));
+  o = align_up(o + size_t(std::max(1, n_tile)) * sizeof(int2));
+  for (int dir = 0; dir < 2; ++dir) o = align_up(o + size_t(std::max(1, n_bw[dir])) * sizeof(int2));
+  return o;
+}
+
+int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* arena, size_t bytes, void* stream,
+                            pmwa_batch** out) {
+  if (!out) return PMWA_EINVAL;
+  *out = nullptr;
+  const size_t need = pmwa_batch_tables_bytes(hs, n);
+  if (!need || !arena || bytes < need || (reinterpret_cast<uintptr_t>(arena) & (kAlign - 1))) return PMWA_EINVAL;
+  pmwa_batch* b = new (std::nothrow) pmwa_batch();
+  if (!b) return PMWA_EINVAL;
+  b->n = n;
+  b->borrowed = true;
+  b->stream = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(arena);
+  size_t o = 0;
+  b->devs = reinterpret_cast<Dev*>(base + o); o = align_up(o + size_t(n) * sizeof(Dev));
+  b->base = reinterpret_cast<BatchBase*>(base + o); o = align_up(o + size_t(n) * sizeof(BatchBase));
+  b->errs = reinterpret_cast<DevErr*>(base + o); o = align_up(o + size_t(n) * sizeof(DevErr));
+  int n_tile = 0;
+  for (int i = 0; i < n; ++i) n_tile += hs[i]->d.ndom;
+  b->tile_work = reinterpret_cast<int2*>(base + o); o = align_up(o + size_t(std::max(1, n_tile)) * sizeof(int2));
+  b->n_tile = n_tile;
+  b->h.assign(hs, hs + n);
+  b->active.assign(size_t(n), 1);
+  b->hbase.resize(size_t(n));
+  int rc = PMWA_OK;
+  for (int i = 0; i < n; ++i) {
+    b->own_err.push_back(hs[i]->d.err);
+    hs[i]->err = hs[i]->d.err = b->errs + i;
+    b->cap_max = std::max(b->cap_max, hs[i]->d.cap);
+  }
+  if (cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
+  std::vector<int2> bw;
+  for (int dir = 0; dir < 2 && rc == PMWA_OK; ++dir) {
+    b->bwork[dir] = reinterpret_cast<int2*>(base + o);
+    bw.clear();
+    const int bpb = boundary_bonds_per_block(b->cap_max);
+    int nb_total = 0;
+    for (int i = 0; i < n; ++i) {
+      const Dev& d = hs[i]->d;
+      const int nb = dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
+      nb_total += nb;
+      for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
+    }
+    o = align_up(o + size_t(std::max(1, nb_total)) * sizeof(int2));
+    b->n_bwork[dir] = int(bw.size());
+    if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
+      rc = PMWA_ECUDA;
+  }
+  if (rc == PMWA_OK) rc = batch_upload(b);
+  if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
+                        cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
+    rc = PMWA_ECUDA;
+  if (rc) {
+    for (int i = 0; i < n; ++i) hs[i]->err = hs[i]->d.err = b->own_err[size_t(i)];
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return PMWA_OK;
+}
+
 int pmwa_batch_instance(pmwa_batch* b, int32_t i, pmwa_handle** h) {
   if (!b || !h || i < 0 || i >= b->n) return PMWA_EINVAL;
   *h = b->h[size_t(i)];
@@ -951,7 +1058,11 @@ int pmwa_batch_destroy(pmwa_batch* b) {
   if (!b) return PMWA_OK;
   cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
-  for (pmwa_handle* hi : b->h) pmwa_destroy(hi);
+  if (b->borrowed) {
+    for (size_t i = 0; i < b->h.size(); ++i) b->h[i]->err = b->h[i]->d.err = b->own_err[i];
+  } else {
+    for (pmwa_handle* hi : b->h) pmwa_destroy(hi);
+  }
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);

@@ -108,6 +108,7 @@ int prepare_boundary(int cap);
 int prepare_tile_batch(int cls, int smem);
 int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
+int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sums, void* stream);
 // rho slices through the library's own static device scratch (no allocation)
 int rho_slices_static(const Dev& d, int K, double* host_out, void* stream);
 // shared-memory plan of the tile kernel for this instance (fills the sm_*

@@ -423,6 +423,46 @@ int rho_slices_static(const Dev& d, int K, double* host_out, void* stream) {
   return PMWA_OK;
 }
 
+// Supplement S-I equal-time correlators from the worm densities rho[i*K+k]:
+// blockIdx.y = r - 1 (r = 1..rmax) accumulates sum_{i,k} rho_i rho_{i+r x}
+// into sums[r-1] and rho_i rho_{i+r y} into sums[rmax + r - 1]; blockIdx.y =
+// rmax accumulates the plaquette product rho_i rho_{i+x} rho_{i+y}
+// rho_{i+x+y} into sums[2 rmax].  Sites strided over blockIdx.x.
+__global__ void k_green(int Lx, int Ly, int K, int rmax, const double* __restrict__ rho, double* sums) {
+  const int N = Lx * Ly;
+  const int r = int(blockIdx.y) + 1;
+  double ax = 0.0, ay = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int x = i % Lx, y = i / Lx;
+    const double* ri = rho + size_t(i) * K;
+    if (r <= rmax) {
+      const double* rx = rho + size_t((x + r) % Lx + Lx * y) * K;
+      const double* ry = rho + size_t(x + Lx * ((y + r) % Ly)) * K;
+      for (int k = 0; k < K; ++k) { ax = fma(ri[k], rx[k], ax); ay = fma(ri[k], ry[k], ay); }
+    } else {
+      const double* r1 = rho + size_t((x + 1) % Lx + Lx * y) * K;
+      const double* r2 = rho + size_t(x + Lx * ((y + 1) % Ly)) * K;
+      const double* r3 = rho + size_t((x + 1) % Lx + Lx * ((y + 1) % Ly)) * K;
+      for (int k = 0; k < K; ++k) ax = fma(ri[k] * r1[k], r2[k] * r3[k], ax);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (r <= rmax) { atomicAdd(sums + (r - 1), ax); atomicAdd(sums + rmax + r - 1, ay); }
+    else atomicAdd(sums + 2 * rmax, ax);
+  }
+}
+
+int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sums, void* stream) {
+  const int N = Lx * Ly;
+  const int bx = N < 256 * 152 ? blocks_for(N, 256) : 152;
+  k_green<<<dim3(bx, rmax + 1), 256, 0, cudaStream_t(stream)>>>(Lx, Ly, K, rmax, rho, sums);
+  return int(cudaGetLastError());
+}
+
 int launch_rho(const Dev& d, int K, double* out, void* stream) {
   k_rho<<<blocks_for(d.N, 128), 128, 0, cudaStream_t(stream)>>>(d, K, out);
   return int(cudaGetLastError());

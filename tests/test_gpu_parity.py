@@ -98,6 +98,29 @@ def test_rho_slices_match():
     assert np.allclose(g.rho_slices(8), o.rho_slices(8), rtol=REL, atol=0)
 
 
+def test_green_functions_match_oracle_densities():
+    """pmwa_green against the same correlators taken in numpy from the CPU
+    oracle's worm densities of the same configuration (within 1e-12)."""
+    kw = dict(Lx=12, Ly=8, beta=3.0, eta=0.3, V=0.5, mu=0.2, dom_x=6, dom_y=4, sub_block=2, n_cycle=4, seed=31)
+    g, o = _pair(kw)
+    o.sweep(4)
+    g.sweep(4)
+    K, rmax = 5, 4
+    gx, gy, pl = P.pmwa_green(g.h, K, rmax)
+    r = o.rho_slices(K)
+    Lx, Ly = kw["Lx"], kw["Ly"]
+    idx = np.arange(Lx * Ly)
+    x, y = idx % Lx, idx // Lx
+    eta = kw["eta"]
+    for d in range(1, rmax + 1):
+        ex = (r * r[(x + d) % Lx + Lx * y]).mean() / eta ** 2
+        ey = (r * r[x + Lx * ((y + d) % Ly)]).mean() / eta ** 2
+        assert gx[d - 1] == pytest.approx(ex, rel=1e-12)
+        assert gy[d - 1] == pytest.approx(ey, rel=1e-12)
+    p4 = (r * r[(x + 1) % Lx + Lx * y] * r[x + Lx * ((y + 1) % Ly)] * r[(x + 1) % Lx + Lx * ((y + 1) % Ly)]).mean()
+    assert pl == pytest.approx(p4 / eta ** 4, rel=1e-12)
+
+
 def test_many_sweeps_config1_shape():
     """Config-1 shape over 200 sweeps: configuration identical at the end."""
     kw = dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=8, seed=1, init=1, init_seed=1)

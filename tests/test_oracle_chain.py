@@ -122,6 +122,32 @@ def test_green_function_two_point():
     assert abs(m - ex["G"][0]) < Z * s, (m, s, ex["G"][0])
 
 
+def test_green_function_four_point_plaquette():
+    """Supplement S-I for n = 4: <Q_i Q_{i+x} Q_{i+y} Q_{i+x+y}> =
+    <rho rho rho rho> / eta^4 (four distinct sites at equal time), against
+    ED on 3x3."""
+    Lx = Ly = 3
+    beta, eta = 2.0, 0.4
+    ex = ed.thermal(Lx, Ly, beta, 1.0, 0.0, 0.0, eta)
+    idx = np.arange(Lx * Ly)
+    x, y = idx % Lx, idx // Lx
+    s1 = (x + 1) % Lx + Lx * y
+    s2 = x + Lx * ((y + 1) % Ly)
+    s3 = (x + 1) % Lx + Lx * ((y + 1) % Ly)
+    means = []
+    for rep in range(16):
+        o = O.Oracle(Lx=Lx, Ly=Ly, beta=beta, eta=eta, n_cycle=8, seed=300 + rep)
+        o.sweep(500)
+        vals = []
+        for _ in range(4000):
+            o.sweep(1)
+            r = o.rho_slices(4)
+            vals.append((r * r[s1] * r[s2] * r[s3]).mean() / eta ** 4)
+        means.append(np.mean(vals))
+    m, s = _mean_err(np.array(means))
+    assert abs(m - ex["plaq"]) < Z * s, (m, s, ex["plaq"])
+
+
 def test_eta_to_zero_quadratic_extrapolation():
     """Eq. 6: the O(eta) term of <H>_eta vanishes, so E(eta) = a + b eta^2 +
     c eta^4; the weighted fit of Monte Carlo energies at four eta reaches the

@@ -139,6 +139,18 @@ def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
     return float(r["n_v"].sum()) / el, steps, el
 
 
+def oracle_pilot_n_cycle(wl, pilot):
+    """The same N_cycle rule as the GPU arm, from a pilot run of the oracle:
+    N_cycle = ceil(2 <n_v> / <n_w>) over the second half of `pilot` sweeps
+    at 16 passes."""
+    from oracle import oracle as O
+    o = O.Oracle(n_cycle=16, **WORKLOADS[wl])
+    o.sweep(max(2, pilot))
+    r = o.rows()
+    half = r[len(r) // 2:]
+    return ncycle_rule(float(half["n_v"].mean()), float(half["n_w"].mean()))
+
+
 def run_reference(args, wl, n_cycle):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -230,14 +242,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-replica comparison")
-    ap.add_argument("--serve-jobs", type=int, default=40, help="jobs of the serving trace to run (0: skip)")
-    ap.add_argument("--serve-scale", type=float, default=0.005, help="factor on each job's sweep count")
+    ap.add_argument("--serve-jobs", type=int, default=24, help="jobs of the serving trace to run (0: skip)")
+    ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on each job's sweep count")
     args = ap.parse_args()
     wl = args.workload
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
-        nc = args.n_cycle or {"config2": 86, "config4": 60, "config1": 8}[wl]
+        nc = args.n_cycle or oracle_pilot_n_cycle(wl, args.pilot)
         run_reference(args, wl, nc)
         return
 

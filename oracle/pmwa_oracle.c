@@ -144,7 +144,7 @@ static double coth_det(double x) { double e = or_expm1_det(-2.0 * x); return (2.
    R is found by bisection so that the top strip closes with area v.         */
 typedef struct {
   double X[257], F[257], W[256];
-  uint64_t K[256];
+  uint64_t K[256], XF[256], RF;
   double R, v;
 } zig_t;
 
@@ -171,7 +171,9 @@ static int zig_lay(double R, zig_t* z) {
     for (int i = 0; i < 256; i++) {
       z->K[i] = (uint64_t)floor(X[i + 1] / X[i] * 0x1p53);
       z->W[i] = X[i] * 0x1p-53;
+      z->XF[i] = (uint64_t)(X[i] * 0x1p58);  /* exact: X[i] has 53 bits, X[i] >= 2^-5 */
     }
+    z->RF = (uint64_t)(R * 0x1p58);
   }
   return 1;
 }
@@ -194,43 +196,66 @@ void or_zig_tables(double* X, double* F, double* W, uint64_t* K, double* R, doub
   *R = z.R; *v = z.v;
 }
 
-/* One unit exponential deviate.  A word gives the strip i (low 8 bits) and a
-   53-bit uniform u (high bits), x = u W[i].  Inside the inner rectangle the
-   point is accepted at once; strip 0 beyond R restarts at R + (new deviate)
-   (memorylessness); otherwise a second word places y in the strip and the
-   point is kept if y < e^-x.  At most 64 words.                            */
-static double zig_exp(const zig_t* z, stream_t* s) {
-  double acc = 0.0;
+/* One unit exponential deviate E, returned in fixed point as floor-ish
+   E 2^58 (u64; E < 64).  A word gives the strip i (low 8 bits) and a 53-bit
+   uniform u (high bits); the point is x = u X[i] / 2^53, in fixed point
+   (u XF[i]) >> 53 with XF[i] = X[i] 2^58 (exact, 128-bit product).  Inside
+   the inner rectangle (u < K[i]) it is accepted at once; strip 0 beyond R
+   restarts at R + (new deviate) (memorylessness); otherwise a second word
+   places y in the strip and the point is kept if y < e^-x, a binary64 test
+   (rare: about 1 % of the words).  At most 64 words.                       */
+static uint64_t zfix_add(uint64_t a, uint64_t b) { return (a > UINT64_MAX - b) ? UINT64_MAX : a + b; }
+
+static uint64_t zig_exp(const zig_t* z, stream_t* s) {
+  uint64_t acc = 0;
   for (int tries = 0; tries < 64; tries++) {
     uint64_t w = s_word(s);
     unsigned i = (unsigned)(w & 255u);
     uint64_t u = w >> 11;
+    uint64_t xf = (uint64_t)(((u128)u * z->XF[i]) >> 53);
+    if (u < z->K[i]) return zfix_add(acc, xf);
+    if (i == 0) { acc = zfix_add(acc, z->RF); continue; }
     double x = (double)u * z->W[i];
-    if (u < z->K[i]) return acc + x;
-    if (i == 0) { acc = acc + z->R; continue; }
     uint64_t w2 = s_word(s);
     double t1 = (double)(w2 >> 11) * 0x1p-53;
     double t2 = z->F[i + 1] - z->F[i];
     double y = z->F[i] + t1 * t2;
-    if (y < or_exp_det(-x)) return acc + x;
+    if (y < or_exp_det(-x)) return zfix_add(acc, xf);
   }
   s->err = OR_ETIMEOUT;
-  return 0.0;
+  return 0;
 }
 
 int or_exp_deviates(uint64_t seed, uint32_t unit, uint32_t c2, uint32_t sweep,
                     int64_t n, double* out) {
   zig_t z; zig_build(&z);
   stream_t s; s_init(&s, seed, unit, c2, sweep);
-  for (int64_t k = 0; k < n; k++) out[k] = zig_exp(&z, &s);
+  for (int64_t k = 0; k < n; k++) out[k] = (double)zig_exp(&z, &s) * 0x1p-58;
   return s.err;
 }
 
-/* Gap of a Bernoulli process on an integer grid with mean spacing scale:
-   1 + floor(E * scale), E a unit exponential; saturates at 2^62.           */
-static uint64_t grid_gap(double E, double scale) {
-  double g = E * scale;
-  if (!(g < 0x1p62)) return TWO62;
+/* A grid scale S (the mean spacing of a Bernoulli process, in grid points)
+   as S = m 2^(sh - 122) ... written so that, with E in fixed point (E 2^58),
+   E S = (E 2^58) m / 2^sh: m in [2^63, 2^64) is the 53-bit binary64 mantissa
+   of S moved to the top of a u64 and sh = 121 - floor(log2 S).  Parameters
+   keep S in [2^39, 2^99], so sh stays in [22, 82].                          */
+typedef struct { uint64_t m; int sh; } scale_t;
+
+static scale_t scale_of(double S) {
+  scale_t r;
+  int e;
+  double f = frexp(S, &e);          /* S = f 2^e, f in [0.5, 1) */
+  r.m = (uint64_t)ldexp(f, 64);     /* exact: f has 53 bits      */
+  r.sh = 122 - e;                   /* floor(log2 S) = e - 1     */
+  return r;
+}
+
+/* Gap of a Bernoulli process on an integer grid with mean spacing S:
+   1 + floor(E S) for a unit exponential E (fixed point, 2^-58), from the
+   exact 128-bit product; saturates at 2^62.                               */
+static uint64_t grid_gap(uint64_t Ef, scale_t S) {
+  u128 g = ((u128)Ef * S.m) >> S.sh;
+  if (g >= (u128)TWO62) return TWO62;
   return 1 + (uint64_t)g;
 }
 
@@ -250,13 +275,13 @@ static uint64_t grid_gap(double E, double scale) {
        rejection).  This gives x^n/n! for odd n; acceptance >= 0.43.
    At most 128 proposals.  Offsets (0 <= off < M) are written sorted.       */
 static int sample_worms(const zig_t* z, stream_t* s, uint64_t M, int sigma,
-                        double SW, uint64_t SWI, uint64_t* offs, int max) {
+                        scale_t SW, uint64_t SWI, uint64_t* offs, int max) {
   if (M == 0) { if (sigma) { s->err = OR_EINVARIANT; return -1; } return 0; }
   for (int tries = 0; tries < 128; tries++) {
     int n = 0, first = 1;
     uint64_t pos = 0;
     for (;;) {
-      double E = zig_exp(z, s);
+      uint64_t E = zig_exp(z, s);
       uint64_t g = grid_gap(E, SW);
       uint64_t nxt = first ? g - 1 : pos + g;
       first = 0;
@@ -295,7 +320,7 @@ int or_sample_worms(uint64_t seed, uint32_t unit, uint32_t c2, uint32_t sweep,
   static int built = 0;
   if (!built) { zig_build(&z); built = 1; }
   stream_t s; s_init(&s, seed, unit, c2, sweep);
-  int n = sample_worms(&z, &s, M, sigma, SW, swi_of(SW), offs, max);
+  int n = sample_worms(&z, &s, M, sigma, scale_of(SW), swi_of(SW), offs, max);
   return s.err ? -1 : n;
 }
 
@@ -314,6 +339,7 @@ struct or_handle {
   or_params p;
   int N, Lx, Ly, ndx, ndy, ndom, K;
   double d[4], D, C, SV, SW;
+  scale_t SVs, SWs;
   uint64_t TV[4], SWI;
   uint64_t TH[16][4][4];
   zig_t z;
@@ -504,6 +530,8 @@ static int derive(or_handle* h) {
   h->SV = (h->D > 0.0) ? 0x1p59 / (p->beta * h->D) : INFINITY;
   h->SW = 0x1p59 / (p->beta * p->eta);
   h->SWI = swi_of(h->SW);
+  h->SWs = scale_of(h->SW);
+  if (h->D > 0.0) h->SVs = scale_of(h->SV);
   for (int S = 0; S < 16; S++)
     for (int i = 0; i < 4; i++) {
       double wi = vweight(h, S);
@@ -560,8 +588,8 @@ static int step3_bond(or_handle* h, int a, int d) {
   uint64_t pos = 0;
   int first = 1;
   for (;;) {
-    double E = zig_exp(&h->z, &s);
-    uint64_t g = grid_gap(E, h->SV);
+    uint64_t E = zig_exp(&h->z, &s);
+    uint64_t g = grid_gap(E, h->SVs);
     uint64_t nxt = first ? g - 1 : pos + g;
     first = 0;
     if (nxt >= TWO59) break;
@@ -606,7 +634,7 @@ static int step4_site(or_handle* h, int si) {
   int no = 0;
   if (nl == 0) {
     int s0 = (int)(s_word(&st) >> 63);
-    int n = sample_worms(&h->z, &st, TWO59, 0, h->SW, h->SWI, offs, MAXW);
+    int n = sample_worms(&h->z, &st, TWO59, 0, h->SWs, h->SWI, offs, MAXW);
     if (n < 0) { free(out); return st.err ? st.err : OR_ETIMEOUT; }
     for (int k = 0; k < n; k++) {
       uint64_t w = s_word(&st);
@@ -621,7 +649,7 @@ static int step4_site(or_handle* h, int si) {
       out[no].key = lo; out[no].lab = 0; no++;
       uint64_t M = wpts(kpk(lo), kpk(hi));
       int p = kab(lo), sigma = p ^ kbl(hi);
-      int n = sample_worms(&h->z, &st, M, sigma, h->SW, h->SWI, offs, MAXW);
+      int n = sample_worms(&h->z, &st, M, sigma, h->SWs, h->SWI, offs, MAXW);
       if (n < 0) { free(out); return st.err ? st.err : OR_ETIMEOUT; }
       uint64_t m0 = wm_above(kpk(lo));
       for (int j = 0; j < n; j++) {
@@ -853,7 +881,7 @@ static int regen_interval(or_handle* h, stream_t* st, int x, uint64_t lo, uint64
     if (off > 0 && off < span) site_erase(S, k);
   }
   static uint64_t offs[MAXW];
-  int n = sample_worms(&h->z, st, wpts(lo, hi), p ^ q, h->SW, h->SWI, offs, MAXW);
+  int n = sample_worms(&h->z, st, wpts(lo, hi), p ^ q, h->SWs, h->SWI, offs, MAXW);
   if (n < 0) return st->err ? st->err : OR_ETIMEOUT;
   uint64_t m0 = wm_above(lo);
   for (int k = 0; k < n; k++) site_add(S, wkey((m0 + offs[k]) & (TWO59 - 1), 0, p ^ 1 ^ (k & 1)), 0);
@@ -977,6 +1005,12 @@ static int validate(const or_params* p) {
   if (B && B < p->dom_x && p->dom_x % B) return OR_EINVAL;
   if (B && B < p->dom_y && p->dom_y % B) return OR_EINVAL;
   if (p->replica >= 65536) return OR_EINVAL;
+  /* the grid scales 2^59/(beta eta) and 2^59/(beta D) must lie in [2^39, 2^99] */
+  if (!(p->beta * p->eta >= 0x1p-40 && p->beta * p->eta <= 0x1p20)) return OR_EINVAL;
+  {
+    or_handle t; memset(&t, 0, sizeof t); t.p = *p; derive(&t);
+    if (t.D > 0.0 && !(p->beta * t.D >= 0x1p-40 && p->beta * t.D <= 0x1p20)) return OR_EINVAL;
+  }
   return OR_OK;
 }
 

@@ -17,6 +17,8 @@ __constant__ double c_zX[257];
 __constant__ double c_zF[257];
 __constant__ double c_zW[256];
 __constant__ unsigned long long c_zK[256];
+__constant__ unsigned long long c_zXF[256];
+__constant__ unsigned long long c_zRF;
 __constant__ double c_zR;
 // Taylor coefficients 1/n!, n = 0..24: the correctly rounded quotients
 // 1.0 / n! of exact factorials, computed on the host.
@@ -32,6 +34,8 @@ static int upload_constants(const Zig& z) {
   if ((e = cudaMemcpyToSymbol(c_zW, z.W, sizeof z.W))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zK, z.K, sizeof z.K))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zR, &z.R, sizeof z.R))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zXF, z.XF, sizeof z.XF))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zRF, &z.RF, sizeof z.RF))) return int(e);
   double inv_fact[25];
   double fact = 1.0;
   for (int n = 0; n <= 24; ++n) {
@@ -150,59 +154,122 @@ __device__ inline double xg_sigma(int sigma, double x) {
   return p * y;
 }
 
+// The same two series in fixed point, for the per-interval terms of the
+// estimator: coefficients a_n 2^62 and b_n 2^62 rounded to nearest (exact
+// rationals from the Bernoulli numbers), Horner's rule on signed 64-bit
+// words with y 2^64 = (x 2^64)^2 / 2^64.  The terms kept (5, 8 or 19 for
+// tanh and 5, 7 or 13 for coth as x < 2^-5, 2^-3, 2^-1) leave a truncation
+// below 2^-63; each product is floored, so a term is within (n + 1) 2^-62
+// of x g_sigma(x).  No floating point is used, so the sum of the terms of a
+// site is exact and independent of the order of summation.
+__constant__ long long c_xtanh_fx[19] = {
+    4611686018427387904ll, -1537228672809129301ll, 614891469123651721ll, -248884642264335220ll,
+    100855214512344991ll, -40874459371278820ll, 16565766642662335ll, -6713851087910371ll,
+    2721021299897250ll, -1102788392755917ll, 446943300930299ll, -181139297079955ll,
+    73412991936897ll, -29753164951077ll, 12058503559795ll, -4887127414535ll,
+    1980678137006ll, -802738613024ll, 325337705708ll};
+__constant__ long long c_xcoth_fx[13] = {
+    4611686018427387904ll, 1537228672809129301ll, -102481911520608620ll, 9760182049581773ll,
+    -976018204958177ll, 98587697470523ll, -9981552960019ll, 1011155871493ll,
+    -102446800762ll, 10379912109ll, -1051701970ll, 106559612ll, -10796744ll};
+
+// x g_sigma(x) 2^62 for x = I beta eta / 2^59 (XQ: beta eta 2^5 as a grid
+// scale, so that x 2^64 = (I m) >> sh); false when x >= 1/2, where the
+// caller uses the binary64 form.
+__device__ __forceinline__ bool xg_fix(int sigma, uint64_t I, GridScale XQ, uint64_t& out) {
+  const uint64_t hi = __umul64hi(I, XQ.m), lo = I * XQ.m;
+  uint64_t X;
+  if (XQ.sh >= 64) {
+    X = hi >> (XQ.sh - 64);
+  } else {
+    if (hi >> XQ.sh) return false;
+    X = (hi << (64 - XQ.sh)) | (lo >> XQ.sh);
+  }
+  if (X >= (1ull << 63)) return false;
+  const long long Y = (long long)__umul64hi(X, X);
+  const int band = (X < (1ull << 59)) ? 0 : (X < (1ull << 61)) ? 1 : 2;
+  long long p;
+  if (sigma) {
+    const int n = band == 0 ? 5 : band == 1 ? 7 : 13;
+    p = c_xcoth_fx[n - 1];
+    for (int k = n - 2; k >= 0; --k) p = c_xcoth_fx[k] + __mul64hi(p, Y);
+    out = uint64_t(p);
+  } else {
+    const int n = band == 0 ? 5 : band == 1 ? 8 : 19;
+    p = c_xtanh_fx[n - 1];
+    for (int k = n - 2; k >= 0; --k) p = c_xtanh_fx[k] + __mul64hi(p, Y);
+    out = uint64_t(__mul64hi(p, Y));
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
-// Ziggurat tables as seen by a kernel: a copy in shared memory, because the
-// strip index differs from lane to lane (constant memory would serialise).
+// Ziggurat tables as seen by a kernel: the two tables of the fast path (the
+// inner-rectangle thresholds K and the fixed-point strip edges XF) copied
+// into shared memory, because the strip index differs from lane to lane
+// (constant memory would serialise); the wedge test (about 1 % of the words)
+// reads W and F from constant memory.
 struct ZigTab {
-  const double* W;             // [256] strip width / 2^53
-  const unsigned long long* K; // [256] inner-rectangle threshold
-  const double* F;             // [257] e^-X at the strip edges
-  double R;                    // start of the tail
+  const unsigned long long* K;   // [256] inner-rectangle threshold
+  const unsigned long long* XF;  // [256] X[i] 2^58
 };
-constexpr int kZigBytes = 256 * 8 + 256 * 8 + 257 * 8;
+constexpr int kZigBytes = 256 * 8 + 256 * 8;
 
 // copy the tables into `buf` (kZigBytes, 8-byte aligned); all threads
 // participate; the caller synchronises before use
 __device__ inline ZigTab zig_stage(unsigned char* buf) {
-  double* W = reinterpret_cast<double*>(buf);
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(buf + 256 * 8);
-  double* F = reinterpret_cast<double*>(buf + 512 * 8);
-  for (int i = threadIdx.x; i < 257; i += blockDim.x) {
-    if (i < 256) { W[i] = c_zW[i]; K[i] = c_zK[i]; }
-    F[i] = c_zF[i];
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(buf);
+  unsigned long long* XF = reinterpret_cast<unsigned long long*>(buf + 256 * 8);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    K[i] = c_zK[i];
+    XF[i] = c_zXF[i];
   }
-  return ZigTab{W, K, F, c_zR};
+  return ZigTab{K, XF};
 }
 
-// Unit exponential from the ziggurat of Marsaglia and Tsang (2000): strip i
-// from the low 8 bits of a word, a 53-bit uniform u from its high bits,
-// x = u W[i]; accept when u < K[i]; strip 0 past R restarts at R + new
-// deviate; else a wedge test y < e^-x with a second word.  <= 64 words.
-__device__ inline double zig_exp(const ZigTab& z, Stream& s, int* bad) {
-  double acc = 0.0;
+__device__ __forceinline__ uint64_t zfix_add(uint64_t a, uint64_t b) { return (a > ~0ull - b) ? ~0ull : a + b; }
+
+// Unit exponential E from the ziggurat of Marsaglia and Tsang (2000), in
+// fixed point E 2^58: strip i from the low 8 bits of a word, a 53-bit
+// uniform u from its high bits, the point x = u X[i] / 2^53 as the exact
+// product (u XF[i]) >> 53; accept when u < K[i]; strip 0 past R restarts at
+// R + new deviate; else a binary64 wedge test y < e^-x with a second word.
+// <= 64 words.
+__device__ inline uint64_t zig_exp(const ZigTab& z, Stream& s, int* bad) {
+  uint64_t acc = 0;
   for (int tries = 0; tries < 64; ++tries) {
     const uint64_t w = s.word();
     const unsigned i = unsigned(w & 255u);
     const uint64_t u = w >> 11;
-    const double x = __dmul_rn(__ull2double_rn(u), z.W[i]);
-    if (u < z.K[i]) return __dadd_rn(acc, x);
-    if (i == 0) { acc = __dadd_rn(acc, z.R); continue; }
+    const uint64_t xf0 = z.XF[i];
+    const uint64_t xf = (__umul64hi(u, xf0) << 11) | ((u * xf0) >> 53);
+    if (u < z.K[i]) return zfix_add(acc, xf);
+    if (i == 0) { acc = zfix_add(acc, c_zRF); continue; }
+    const double x = __dmul_rn(__ull2double_rn(u), c_zW[i]);
     const uint64_t w2 = s.word();
     const double t1 = __dmul_rn(__ull2double_rn(w2 >> 11), 0x1p-53);
-    const double t2 = __dsub_rn(z.F[i + 1], z.F[i]);
-    const double y = __dadd_rn(z.F[i], __dmul_rn(t1, t2));
-    if (y < exp_det(-x)) return __dadd_rn(acc, x);
+    const double t2 = __dsub_rn(c_zF[i + 1], c_zF[i]);
+    const double y = __dadd_rn(c_zF[i], __dmul_rn(t1, t2));
+    if (y < exp_det(-x)) return zfix_add(acc, xf);
   }
   *bad = PMWA_ETIMEOUT;
-  return 0.0;
+  return 0;
 }
 
-// Gap of a Bernoulli process of mean spacing `scale` on an integer grid:
-// 1 + floor(E scale), saturating at 2^62.
-__device__ __forceinline__ uint64_t grid_gap(double E, double scale) {
-  const double g = __dmul_rn(E, scale);
-  if (!(g < 0x1p62)) return kTwo62;
-  return 1 + __double2ull_rz(g);
+// Gap of a Bernoulli process of mean spacing S on an integer grid:
+// 1 + floor(E S) from the exact 128-bit product (E 2^58) m, shifted right
+// by sh (22 <= sh <= 82); saturates at 2^62.
+__device__ __forceinline__ uint64_t grid_gap(uint64_t Ef, GridScale S) {
+  const uint64_t hi = __umul64hi(Ef, S.m), lo = Ef * S.m;
+  uint64_t g;
+  if (S.sh >= 64) {
+    g = hi >> (S.sh - 64);
+  } else {
+    if (hi >> S.sh) return kTwo62;
+    g = (hi << (64 - S.sh)) | (lo >> S.sh);
+  }
+  if (g >= kTwo62) return kTwo62;
+  return 1 + g;
 }
 
 // Eq. 1 for hard-core bosons: worms on an interval of M worm grid points with
@@ -212,7 +279,7 @@ __device__ __forceinline__ uint64_t grid_gap(double E, double scale) {
 // odd, the extra worm uniform on the interval (a clash rejects).  Returns the
 // count (offsets sorted in offs[0..n)), or -1 with *bad set.
 template <int MAXN>
-__device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, double SW, uint64_t SWI,
+__device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, GridScale SW, uint64_t SWI,
                             uint64_t* offs, int* bad) {
   if (M == 0) { if (sigma) { *bad = PMWA_EINVARIANT; return -1; } return 0; }
   for (int tries = 0; tries < 128; ++tries) {
@@ -220,7 +287,7 @@ __device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, d
     bool first = true;
     uint64_t pos = 0;
     for (;;) {
-      const double E = zig_exp(z, s, bad);
+      const uint64_t E = zig_exp(z, s, bad);
       const uint64_t g = grid_gap(E, SW);
       const uint64_t nxt = first ? g - 1 : pos + g;
       first = false;

@@ -42,6 +42,7 @@ struct Derived {
   int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap, poolcap;
   double legs_per_site, mb;
   double d[4], D, tkink, SV, SW, XW;
+  GridScale SVs, SWs, XQ;
   uint64_t TV[4], SWI;
   uint64_t TH[256];
 };
@@ -69,6 +70,20 @@ int validate(const pmwa_params* p) {
   if (p->replica >= 65536u || p->init < 0 || p->init > 1) return PMWA_EINVAL;
   if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
   for (int k = 0; k < 5; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  // the gap arithmetic needs the mean grid spacings 2^59/(beta eta) and
+  // 2^59/(beta D) in [2^39, 2^99]
+  const double be = p->beta * p->eta;
+  if (!(be >= 0x1p-40 && be <= 0x1p20)) return PMWA_EINVAL;
+  const double c_off = (p->c_off < 0.0) ? 0.5 * p->t : p->c_off;
+  double E[4], Emax = -INFINITY, Emin = INFINITY;
+  for (int s = 0; s < 4; ++s) {
+    const int na = s & 1, nb = s >> 1;
+    E[s] = p->V * (double)(na * nb) - (p->mu / 4.0) * (double)(na + nb);
+    Emax = std::max(Emax, E[s]);
+    Emin = std::min(Emin, E[s]);
+  }
+  const double D = (Emax + c_off) - Emin;
+  if (D > 0.0 && !(p->beta * D >= 0x1p-40 && p->beta * D <= 0x1p20)) return PMWA_EINVAL;
   return PMWA_OK;
 }
 
@@ -105,6 +120,13 @@ void solve_family(const double w[4], double out[4][4]) {
   }
 }
 
+// S = f 2^e with f in [0.5, 1): m = f 2^64 (exact, 53 bits), sh = 122 - e.
+GridScale grid_scale(double S) {
+  int e = 0;
+  const double f = std::frexp(S, &e);
+  return GridScale{(uint64_t)std::ldexp(f, 64), 122 - e};
+}
+
 void derive(const pmwa_params* p, Derived* g) {
   g->dom_x = p->dom_x ? p->dom_x : p->Lx;
   g->dom_y = p->dom_y ? p->dom_y : p->Ly;
@@ -129,7 +151,14 @@ void derive(const pmwa_params* p, Derived* g) {
   g->SV = (g->D > 0.0) ? 0x1p59 / (p->beta * g->D) : INFINITY;
   g->SW = 0x1p59 / (p->beta * p->eta);
   g->SWI = (g->SW >= 0x1p62) ? kTwo62 : (uint64_t)g->SW;
+  g->SWs = grid_scale(g->SW);
+  g->SVs = (g->D > 0.0) ? grid_scale(g->SV) : GridScale{0, 64};
   g->XW = (p->beta * p->eta) * 0x1p-59;
+  {
+    int e = 0;
+    const double f = std::frexp((p->beta * p->eta) * 32.0, &e);
+    g->XQ = GridScale{(uint64_t)std::ldexp(f, 64), 64 - e};
+  }
   for (int S = 0; S < 16; ++S)
     for (int i = 0; i < 4; ++i) {
       uint64_t* th = g->TH + (S * 4 + i) * 4;
@@ -271,7 +300,9 @@ static int lay_strips(double R, Zig* z) {
     for (int i = 0; i < 256; ++i) {
       z->K[i] = (uint64_t)std::floor(X[i + 1] / X[i] * 0x1p53);
       z->W[i] = X[i] * 0x1p-53;
+      z->XF[i] = (uint64_t)(X[i] * 0x1p58);  // exact: 53-bit X[i] >= 2^-5
     }
+    z->RF = (uint64_t)(R * 0x1p58);
   }
   return 1;
 }
@@ -368,6 +399,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.cap = g.cap; d.capb = g.capb; d.wcap = g.wcap; d.poolcap = g.poolcap;
   d.key0 = uint32_t(p->seed); d.key1 = uint32_t(p->seed >> 32); d.replica = p->replica;
   d.beta = p->beta; d.eta = p->eta; d.SV = g.SV; d.SW = g.SW; d.XW = g.XW; d.SWI = g.SWI;
+  d.SVs = g.SVs; d.SWs = g.SWs; d.XQ = g.XQ;
   d.has_vertices = g.D > 0.0 ? 1 : 0;
   for (int s = 0; s < 4; ++s) { d.TV[s] = g.TV[s]; d.dvw[s] = g.d[s]; }
   d.tkink = g.tkink;

@@ -23,6 +23,15 @@ struct DevErr {
   int where;
 };
 
+// A mean grid spacing S of a Bernoulli process (Steps 3 and 4) in the form
+// the integer gap arithmetic uses: S = m 2^(sh - 122), m in [2^63, 2^64) the
+// binary64 mantissa of S at the top of a u64, sh = 121 - floor(log2 S), so
+// that E S = (E 2^58) m / 2^sh for a fixed-point deviate E 2^58.
+struct GridScale {
+  uint64_t m;
+  int sh;
+};
+
 // Everything a kernel needs, passed by value.
 struct Dev {
   // geometry
@@ -41,6 +50,8 @@ struct Dev {
   uint32_t key0, key1, replica, sweep;
   // model
   double beta, eta, SV, SW, XW;
+  GridScale SVs, SWs;  // SV and SW in the fixed-point form of the grid gaps
+  GridScale XQ;        // beta eta 2^5: x 2^64 = (I m) >> sh for an interval of I worm points
   uint64_t SWI;
   int has_vertices;
   uint64_t TV[4];
@@ -89,6 +100,8 @@ __host__ __device__ inline Dev at_iteration(const Dev& d0, const BatchBase& b, i
 struct Zig {
   double X[257], F[257], W[256];
   uint64_t K[256];
+  uint64_t XF[256];  // X[i] 2^58 (exact)
+  uint64_t RF;       // R 2^58 (exact)
   double R, v;
 };
 void build_zig(Zig* z);

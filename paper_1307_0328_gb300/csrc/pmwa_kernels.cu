@@ -110,7 +110,7 @@ __device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_
   n = w;
   uint64_t offs[kMaxWormsPerInterval];
   int bad = 0;
-  const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SW, d.SWI, offs, &bad);
+  const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SWs, d.SWI, offs, &bad);
   if (bad) return bad;
   const uint64_t m0 = wm_above(lo);
   for (int k = 0; k < nw; ++k) {
@@ -241,9 +241,9 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
   bool first = true;
   int bad = 0;
   for (;;) {
-    const double E = zig_exp(Z, sv, &bad);
+    const uint64_t E = zig_exp(Z, sv, &bad);
     if (bad) return bad;
-    const uint64_t g = grid_gap(E, d.SV);
+    const uint64_t g = grid_gap(E, d.SVs);
     const uint64_t nxt = first ? g - 1 : pos + g;
     first = false;
     if (nxt >= kTwo59) break;

@@ -28,7 +28,6 @@ namespace pmwa {
 
 namespace {
 
-constexpr int kTileThreads = 256;
 constexpr int kMaxCandPerBond = 128;
 constexpr int kMaxWormsPerInterval = 128;
 constexpr uint16_t kNone = 0xFFFF;
@@ -139,9 +138,9 @@ __device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, ui
   uint64_t pos = 0;
   bool first = true;
   for (;;) {
-    const double E = zig_exp(z, s, bad);
+    const uint64_t E = zig_exp(z, s, bad);
     if (*bad) break;
-    const uint64_t g = grid_gap(E, d.SV);
+    const uint64_t g = grid_gap(E, d.SVs);
     const uint64_t nxt = first ? g - 1 : pos + g;
     first = false;
     if (nxt >= kTwo59) break;
@@ -458,7 +457,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       if (nl == 0) {
         const int s0 = int(rs.word() >> 63);
         T.base[li] = uint8_t(s0);
-        const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, kTwo59, 0, d.SW, d.SWI, offs, &bad);
+        const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, kTwo59, 0, d.SWs, d.SWI, offs, &bad);
         if (!bad && n > 0) {
           const int o = atomicAdd(&misc->nworms, n);
           if (o + n > d.wcap) bad = PMWA_ECAPACITY;
@@ -473,7 +472,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
           const uint64_t M = wpts(kpk(lo), kpk(hi));
           const int p = kab(lo), sigma = p ^ kbl(hi);
-          const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, M, sigma, d.SW, d.SWI, offs, &bad);
+          const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, M, sigma, d.SWs, d.SWI, offs, &bad);
           T.wcnt[st + k] = uint8_t(n > 0 ? min(n, 255) : 0);
           if (n > 255) bad = PMWA_ECAPACITY;
           if (bad || n <= 0) continue;
@@ -621,15 +620,27 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         const uint64_t key = T.leg[st + k];
         if (T.tinfo[li * 6 + ktag(key)] & 1) { ++nv; if (kab(key) != kbl(key)) ++nk; }
       }
-      if (nl == 0) {
-        q += xg_sigma(0, double(kTwo59) * d.XW);
-      } else {
+      {
+        // improved <Q>: sum of x g_sigma(x) over the site's intervals, in
+        // fixed point (exact sum) where x < 1/2, else in binary64
+        uint64_t qlo = 0, qhi = 0;
         double qs = 0.0;
-        for (int k = 0; k < nl; ++k) {
-          const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
-          qs += xg_sigma(kab(lo) ^ kbl(hi), __ull2double_rn(wpts(kpk(lo), kpk(hi))) * d.XW);
+        for (int k = 0; k < (nl ? nl : 1); ++k) {
+          uint64_t I;
+          int sg;
+          if (nl == 0) {
+            I = kTwo59;
+            sg = 0;
+          } else {
+            const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
+            I = wpts(kpk(lo), kpk(hi));
+            sg = kab(lo) ^ kbl(hi);
+          }
+          uint64_t v;
+          if (xg_fix(sg, I, d.XQ, v)) add128(qlo, qhi, v, 0);
+          else qs += xg_sigma(sg, __ull2double_rn(I) * d.XW);
         }
-        q += qs;
+        q += qs + (__ull2double_rn(qhi) * 4.0 + __ull2double_rn(qlo) * 0x1p-62);
       }
     }
     if (stop >= 6) {

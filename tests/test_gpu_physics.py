@@ -1,0 +1,127 @@
+"""Statistical parity of the GPU chain against exact results.
+
+The GPU runs the same kernels as in the bit-exact tests, for long runs over
+many independent replicas (different seeds and replica ids) advanced together
+by one batched launch per kernel.  The error of an average comes from the
+scatter of the per-replica means.  Requirements:
+
+  * exact diagonalisation of H_eta (2x2, 3x3 and a 4x2 lattice cut into
+    domains, so that Step 2 of Eq. 4 runs): energy, density, <Q>/N (raw and
+    improved, Supplement S-I) and the kinetic term within 4 standard errors,
+    each known to a relative statistical error of at most 2e-3;
+  * t = V = 0: every site is an independent two-level problem whose thermal
+    averages have a closed form, exact at any size, checked at L = 256 in
+    16x16-site domains and at L = 2048 in 128x128 domains of 16x16 sites;
+  * V = mu = 0 is particle-hole symmetric: <n> = 1/2 on a 64x64 lattice in
+    16x16 domains.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import ed  # noqa: E402
+
+import paper_1307_0328_gb300 as P  # noqa: E402
+
+Z = 4.0
+REL = 2e-3
+
+
+def _batch_means(R, therm, sweeps, chunk=4000, seed0=100, **kw):
+    """Per-replica means of every observable over `sweeps` measured sweeps
+    after `therm` thermalisation sweeps: dict name -> array (R,)."""
+    reps = [dict(kw, seed=seed0 + r, replica=r, init=1, init_seed=7000 + r) for r in range(R)]
+    b = P.Batch(reps)
+    try:
+        left = therm
+        while left > 0:
+            s = min(chunk, left)
+            b.sweep(s)
+            for i in range(R):
+                b.rows(i)
+            left -= s
+        acc = [None] * R
+        left = sweeps
+        while left > 0:
+            s = min(chunk, left)
+            b.sweep(s)
+            for i in range(R):
+                ob = P.observables(b.rows(i), b.params[i])
+                sums = {k: float(v.sum()) for k, v in ob.items()}
+                if acc[i] is None:
+                    acc[i] = sums
+                else:
+                    for k in sums:
+                        acc[i][k] += sums[k]
+            left -= s
+    finally:
+        b.close()
+    return {k: np.array([a[k] / sweeps for a in acc]) for k in acc[0]}
+
+
+def _mean_err(v):
+    return float(v.mean()), float(v.std(ddof=1) / np.sqrt(len(v)))
+
+
+ED_CASES = [
+    # (Lx, Ly, model, geometry) -- the config-1 parameters first
+    (3, 3, dict(beta=2.0, eta=0.2), dict()),
+    (2, 2, dict(beta=2.0, eta=0.2), dict()),
+    (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=1.0), dict()),
+    (4, 2, dict(beta=2.0, eta=0.3, V=1.0, mu=0.5), dict(dom_x=2, dom_y=2, sub_block=2)),
+]
+
+
+@pytest.mark.parametrize("Lx,Ly,model,geo", ED_CASES)
+def test_gpu_chain_matches_ed_at_rel_2e3(Lx, Ly, model, geo):
+    m = dict(t=1.0, V=0.0, mu=0.0)
+    m.update(model)
+    ex = ed.thermal(Lx, Ly, m["beta"], m["t"], m["V"], m["mu"], m["eta"], slices_r=False)
+    ob = _batch_means(256, 2000, 48000, Lx=Lx, Ly=Ly, n_cycle=8, **m, **geo)
+    want = dict(E=ex["E"], n=ex["n"], Q_raw=ex["Q"], Q_impr=ex["Q"], kin=ex["kin"])
+    msgs = []
+    for k in ("E", "n", "Q_raw", "Q_impr", "kin"):
+        mu_, s = _mean_err(ob[k])
+        z = (mu_ - want[k]) / s
+        msgs.append("%s %.6f+-%.6f ed %.6f z=%.2f rel=%.1e" % (k, mu_, s, want[k], z, s / abs(want[k])))
+    for k in ("E", "n", "Q_raw", "Q_impr", "kin"):
+        mu_, s = _mean_err(ob[k])
+        assert abs(mu_ - want[k]) < Z * s, "; ".join(msgs)
+        assert s <= REL * abs(want[k]), "; ".join(msgs)
+
+
+@pytest.mark.parametrize("L,dom,therm,sweeps,bins", [(256, 16, 100, 400, 20), (2048, 16, 10, 20, 10)])
+def test_gpu_decoupled_sites_closed_form(L, dom, therm, sweeps, bins):
+    """t = V = 0 with mu = 1, eta = 0.4, beta = 2: <n>, <Q>/N (raw and
+    improved) and E/N = -mu <n> from the two-level closed form; the error
+    of the average comes from the scatter of bin means of consecutive
+    sweeps (sites are independent, so one sweep already averages N of
+    them)."""
+    beta, mu, eta = 2.0, 1.0, 0.4
+    kw = dict(Lx=L, Ly=L, beta=beta, t=0.0, V=0.0, mu=mu, eta=eta, c_off=0.5, dom_x=dom, dom_y=dom,
+              sub_block=2, exchange_every=2, n_cycle=4, seed=11, init=1, init_seed=3)
+    sim = P.Sim(**kw)
+    sim.sweep(therm)
+    sim.rows()
+    sim.sweep(sweeps)
+    ob = P.observables(sim.rows(), sim.params)
+    sim.close()
+    cf = ed.single_site(beta, mu, eta)
+    for k, want in [("n", cf["n"]), ("Q_raw", cf["Q"]), ("Q_impr", cf["Q"]), ("E", cf["E"])]:
+        v = ob[k].reshape(bins, -1).mean(axis=1)
+        m, s = float(v.mean()), float(v.std(ddof=1) / np.sqrt(bins))
+        assert abs(m - want) < Z * s + 1e-12, (k, m, s, want)
+        assert s <= REL * abs(want), (k, m, s, want)
+
+
+def test_gpu_particle_hole_half_filling():
+    """V = mu = 0, t = 1, beta = 4, eta = 0.1 on 64x64 in 16x16 domains:
+    <n> = 1/2."""
+    ob = _batch_means(16, 200, 1000, Lx=64, Ly=64, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2,
+                      exchange_every=2, n_cycle=24)
+    m, s = _mean_err(ob["n"])
+    assert abs(m - 0.5) < Z * s, (m, s)
+    assert s <= REL * 0.5

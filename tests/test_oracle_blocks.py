@@ -104,13 +104,16 @@ def _law(x, sigma, nmax):
     return p
 
 
-@pytest.mark.parametrize("x,sigma", [(0.05, 0), (0.05, 1), (0.7, 1), (1.0, 1),
-                                     (1.7, 1), (2.5, 0), (4.0, 1), (0.3, 0)])
-def test_worm_number_law(x, sigma):
+@pytest.mark.parametrize("x,sigma,M", [(0.05, 0, 2 ** 40), (0.05, 1, 2 ** 40), (0.7, 1, 2 ** 40),
+                                       (1.0, 1, 2 ** 40), (1.7, 1, 2 ** 40), (2.5, 0, 2 ** 40),
+                                       (4.0, 1, 2 ** 40), (0.3, 0, 2 ** 40),
+                                       (0.3, 0, 2 ** 59), (1.7, 1, 2 ** 59), (0.05, 1, 2 ** 59)])
+def test_worm_number_law(x, sigma, M):
     """Eq. 1 for hard-core bosons: P(n) = x^n / n! / f_sigma(x) for n of
     parity sigma, f_0 = cosh, f_1 = sinh.  Chi^2 on 20000 draws, each from
-    its own Philox unit; offsets are uniform on the interval (KS)."""
-    M = 2 ** 40
+    its own Philox unit; offsets are uniform on the interval (KS).  The two
+    interval lengths put the mean spacing SW near 2^40 and near 2^60, the two
+    ends of the fixed-point scale arithmetic of the gaps."""
     SW = M / x                      # so that x = M / SW
     draws = 20000
     counts = np.zeros(64, dtype=int)

@@ -101,9 +101,9 @@ struct Tile {
   uint8_t* wcnt;   // [legcap] worms in the interval just above each leg
   uint64_t* pool;  // [poolcap] (aliases the worm table)
   WormRec* W;      // [wcap]
-  uint16_t* idx;   // [wcap]
-  uint16_t* posu;  // [wcap] sub-block of each bucketed position
-  uint64_t* rw;    // [2 wcap] Philox words of each bucketed position
+  uint16_t* idx;   // [wcap] worms grouped by sub-block (a pass) or by site (output)
+  uint16_t* ord;   // [wcap] worm indices in label order (lab, site, key)
+  uint16_t* wsb;   // [wcap + 8] sub-block of the k-th worm in label order (a pass)
   int* bkt;        // [max(nsub, nds) + 1]
   int* fill;       // [max(nsub, nds)]
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
@@ -320,6 +320,75 @@ __device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t blo,
   lo = s;
 }
 
+// Label order of the nw worms of the domain, (lab, site, key) ascending,
+// into ord[]: a counting sort on the top bits of the (uniform 63-bit)
+// labels into nbk <= max(nsub, nds) buckets, then each worm's rank inside
+// its bucket.  Uses bkt/fill as bucket counters and idx as scratch.
+__device__ void label_order(const Tile& T, int nw, int* wsum) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int cap = max(T.nsub, T.nds);
+  int B = 0;
+  while ((2 << B) <= cap && (1 << B) < nw) ++B;
+  const int nbk = 1 << B;
+  for (int i = tid; i <= nbk; i += NT) T.bkt[i] = 0;
+  __syncthreads();
+  for (int w = tid; w < nw; w += NT) atomicAdd(&T.bkt[B ? int(T.W[w].lab >> (63 - B)) : 0], 1);
+  __syncthreads();
+  block_scan(T.bkt, nbk, wsum);
+  for (int i = tid; i < nbk; i += NT) T.fill[i] = T.bkt[i];
+  __syncthreads();
+  for (int w = tid; w < nw; w += NT)
+    T.idx[atomicAdd(&T.fill[B ? int(T.W[w].lab >> (63 - B)) : 0], 1)] = uint16_t(w);
+  __syncthreads();
+  for (int w = tid; w < nw; w += NT) {
+    const int b = B ? int(T.W[w].lab >> (63 - B)) : 0;
+    const int lo = T.bkt[b], hi = T.bkt[b + 1];
+    int r = 0;
+    for (int j = lo; j < hi; ++j) r += worm_less(T.W[T.idx[j]], T.W[w]);
+    T.ord[lo + r] = uint16_t(w);
+  }
+  __syncthreads();
+}
+
+// One warp (lane = threadIdx.x < 32): fill[u] = sum of bkt[0..u) for
+// u = 0..nsub, and bkt[] cleared for the next pass.
+__device__ void sub_starts(const Tile& T, int lane) {
+  const int n = T.nsub;
+  const int chunk = (n + 31) / 32;
+  const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += T.bkt[i];
+  int v = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += x;
+  }
+  int run = v - sum;
+  for (int i = lo; i < hi; ++i) {
+    const int x = T.bkt[i];
+    T.fill[i] = run;
+    run += x;
+    T.bkt[i] = 0;
+  }
+  if (lane == 31) T.fill[n] = v;
+}
+
+// The worms of sub-block u in label order: a scan of wsb[] eight entries
+// (16 bytes) at a time; wsb[nw .. nw+8) holds kNone.
+__device__ __forceinline__ void collect_sub(const Tile& T, int nw, int u, uint16_t* seg) {
+  int m = 0;
+  const uint4* v = reinterpret_cast<const uint4*>(T.wsb);
+  for (int k0 = 0; k0 < nw; k0 += 8) {
+    const uint4 c = v[k0 >> 3];
+    const uint32_t h[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (int(h[j] & 0xffffu) == u) seg[m++] = T.ord[k0 + 2 * j];
+      if (int(h[j] >> 16) == u) seg[m++] = T.ord[k0 + 2 * j + 1];
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -338,8 +407,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.pool = reinterpret_cast<uint64_t*>(sm + d.sm_pool);
   T.W = reinterpret_cast<WormRec*>(sm + d.sm_worm);
   T.idx = reinterpret_cast<uint16_t*>(sm + d.sm_idx);
-  T.posu = reinterpret_cast<uint16_t*>(sm + d.sm_posu);
-  T.rw = reinterpret_cast<uint64_t*>(sm + d.sm_rw);
+  T.ord = reinterpret_cast<uint16_t*>(sm + d.sm_ord);
+  T.wsb = reinterpret_cast<uint16_t*>(sm + d.sm_wsb);
   T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
   T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
@@ -495,49 +564,35 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     // ---- phase 4: Step 5
     if (stop >= 5) {
       const int nw = misc->nworms;
+      if (nw > 0) label_order(T, nw, wsum);
+      // The shifted sub-block schedule: in pass p every worm moves once,
+      // inside the sub-block of offset pattern p & 3 that holds its site, in
+      // label order; the r-th move of sub-block u draws Philox block r of
+      // stream (unit = domain * n_sub + u, scatter | pass).
+      for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
+      for (int k = nw + tid; k < nw + 8; k += NT) T.wsb[k] = kNone;
+      __syncthreads();
       for (int pass = 0; pass < (nw > 0 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
-        for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
-        __syncthreads();
         const int q = pass & 3;
-        for (int w = tid; w < nw; w += NT) atomicAdd(&T.bkt[T.sub[T.W[w].site * 4 + q]], 1);
-        __syncthreads();
-        block_scan(T.bkt, T.nsub, wsum);
-        for (int u = tid; u < T.nsub; u += NT) T.fill[u] = T.bkt[u];
-        __syncthreads();
-        for (int w = tid; w < nw; w += NT) {
-          const int u = T.sub[T.W[w].site * 4 + q];
-          const int at = atomicAdd(&T.fill[u], 1);
-          T.idx[at] = uint16_t(w);
-          T.posu[at] = uint16_t(u);
+        for (int k = tid; k < nw; k += NT) {
+          const int u = T.sub[T.W[T.ord[k]].site * 4 + q];
+          T.wsb[k] = uint16_t(u);
+          atomicAdd(&T.bkt[u], 1);
         }
         __syncthreads();
-        // label order inside every sub-block (ties: site, time)
-        for (int u = tid; u < T.nsub; u += NT) {
-          uint16_t* seg = T.idx + T.bkt[u];
-          const int n = T.bkt[u + 1] - T.bkt[u];
-          for (int p = 1; p < n; ++p) {
-            const uint16_t v = seg[p];
-            int r = p - 1;
-            while (r >= 0 && worm_less(T.W[v], T.W[seg[r]])) { seg[r + 1] = seg[r]; --r; }
-            seg[r + 1] = v;
-          }
-        }
-        // the r-th move of sub-block u draws Philox block r of stream
-        // (unit = domain * n_sub + u, scatter | pass): all of them up front
-        const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
-        for (int p = tid; p < nw; p += NT) {
-          const int u = T.posu[p];
-          const P4 b = philox(uint32_t(p - T.bkt[u]), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
-          T.rw[2 * p] = uint64_t(b.x) | (uint64_t(b.y) << 32);
-          T.rw[2 * p + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
-        }
+        if (tid < 32) sub_starts(T, tid);  // fill[u] = first slot of sub-block u; bkt[] = 0
         __syncthreads();
         phase_tick(d, 5, tclk);
+        const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
         for (int u = tid; u < T.nsub; u += NT) {
-          const int lo = T.bkt[u], n = T.bkt[u + 1] - lo;
-          const uint16_t* seg = T.idx + lo;
+          const int lo = T.fill[u], n = T.fill[u + 1] - lo;
+          if (n == 0) continue;
+          uint16_t* seg = T.idx + lo;
+          collect_sub(T, nw, u, seg);  // the sub-block's worms in label order
           for (int r = 0; r < n; ++r) {
-            const int rc = tile_move(T, seg, n, r, q, T.rw[2 * (lo + r)], T.rw[2 * (lo + r) + 1]);
+            const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+            const int rc = tile_move(T, seg, n, r, q, uint64_t(b.x) | (uint64_t(b.y) << 32),
+                                     uint64_t(b.z) | (uint64_t(b.w) << 32));
             if (rc) { tile_fail(misc, rc, 5); break; }
           }
         }
@@ -722,7 +777,7 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   const size_t fixed = o;
   // worm side of the union: table, index, two bucket arrays
   const size_t worm_bytes = [&](int wcap) {
-    return up16(size_t(wcap) * sizeof(WormRec)) + 2 * up16(size_t(wcap) * 2) + up16(size_t(wcap) * 16) +
+    return up16(size_t(wcap) * sizeof(WormRec)) + 2 * up16(size_t(wcap) * 2) + up16(size_t(wcap + 8) * 2) +
            2 * up16(size_t(nb) * sizeof(int));
   }(d->wcap);
   const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
@@ -737,8 +792,8 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   d->sm_worm = int(o);
   size_t w = o + up16(size_t(d->wcap) * sizeof(WormRec));
   d->sm_idx = int(w); w = up16(w + size_t(d->wcap) * 2);
-  d->sm_posu = int(w); w = up16(w + size_t(d->wcap) * 2);
-  d->sm_rw = int(w); w = up16(w + size_t(d->wcap) * 16);
+  d->sm_ord = int(w); w = up16(w + size_t(d->wcap) * 2);
+  d->sm_wsb = int(w); w = up16(w + size_t(d->wcap + 8) * 2);
   d->sm_bkt = int(w); w = up16(w + size_t(nb) * sizeof(int));
   d->sm_fill = int(w); w = up16(w + size_t(nb) * sizeof(int));
   o = std::max(w, o + pool_bytes);

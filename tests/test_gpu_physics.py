@@ -93,16 +93,19 @@ def test_gpu_chain_matches_ed_at_rel_2e3(Lx, Ly, model, geo):
         assert s <= REL * abs(want[k]), "; ".join(msgs)
 
 
-@pytest.mark.parametrize("L,dom,therm,sweeps,bins", [(256, 16, 100, 400, 20), (2048, 16, 10, 20, 10)])
+@pytest.mark.parametrize("L,dom,therm,sweeps,bins", [(256, 16, 2000, 4000, 20), (2048, 16, 800, 800, 8)])
 def test_gpu_decoupled_sites_closed_form(L, dom, therm, sweeps, bins):
     """t = V = 0 with mu = 1, eta = 0.4, beta = 2: <n>, <Q>/N (raw and
     improved) and E/N = -mu <n> from the two-level closed form; the error
     of the average comes from the scatter of bin means of consecutive
     sweeps (sites are independent, so one sweep already averages N of
-    them)."""
+    them).  At t = 0 a site's occupation changes only when worms cross
+    its diagonal vertices, and the autocorrelation time is about 100
+    sweeps: the runs thermalise for several hundred sweeps and the bins
+    hold 100 sweeps or more."""
     beta, mu, eta = 2.0, 1.0, 0.4
     kw = dict(Lx=L, Ly=L, beta=beta, t=0.0, V=0.0, mu=mu, eta=eta, c_off=0.5, dom_x=dom, dom_y=dom,
-              sub_block=2, exchange_every=2, n_cycle=4, seed=11, init=1, init_seed=3)
+              sub_block=2, exchange_every=2, n_cycle=16, seed=11, init=1, init_seed=3)
     sim = P.Sim(**kw)
     sim.sweep(therm)
     sim.rows()

@@ -44,7 +44,7 @@ struct Dev {
   int poolcap;  // Step-3 candidates per domain in shared memory
   // shared-memory carve-up of the tile kernel (byte offsets)
   int sm_th, sm_zig, sm_off, sm_base, sm_bcnt, sm_boff, sm_misc, sm_nbr, sm_sub, sm_tinfo, sm_leg, sm_wcnt, sm_pool,
-      sm_worm, sm_idx, sm_ord, sm_wsb, sm_bkt, sm_fill, sm_total;
+      sm_worm, sm_idx, sm_ord, sm_wsb, sm_wrk, sm_rw, sm_bkt, sm_fill, sm_total;
   unsigned long long* phase_cycles;  // 8 counters when profiling, else null
   // random numbers
   uint32_t key0, key1, replica, sweep;

@@ -103,7 +103,9 @@ struct Tile {
   WormRec* W;      // [wcap]
   uint16_t* idx;   // [wcap] worms grouped by sub-block (a pass) or by site (output)
   uint16_t* ord;   // [wcap] worm indices in label order (lab, site, key)
-  uint16_t* wsb;   // [wcap + 8] sub-block of the k-th worm in label order (a pass)
+  uint16_t* wsb;   // [wcap] sub-block of the k-th worm in label order (a pass)
+  uint16_t* wrk;   // [wcap] rank of the k-th worm inside its sub-block (a pass)
+  uint64_t* rw;    // [2 wcap] Philox words of each grouped position (a pass)
   int* bkt;        // [max(nsub, nds) + 1]
   int* fill;       // [max(nsub, nds)]
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
@@ -350,9 +352,27 @@ __device__ void label_order(const Tile& T, int nw, int* wsum) {
   __syncthreads();
 }
 
-// One warp (lane = threadIdx.x < 32): fill[u] = sum of bkt[0..u) for
-// u = 0..nsub, and bkt[] cleared for the next pass.
-__device__ void sub_starts(const Tile& T, int lane) {
+// One warp (lane = threadIdx.x < 32) groups the nw worms of pass pattern q
+// by sub-block, keeping label order inside each group: for the worms in
+// label order, 32 at a time, the sub-block u of each (wsb), its rank among
+// the worms of u met so far (wrk; equal sub-blocks in a chunk found with
+// __match_any_sync, running counts in bkt[]), then fill[u] = first slot of
+// sub-block u (exclusive scan of the counts) and bkt[] cleared.
+__device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  for (int k0 = 0; k0 < nw; k0 += 32) {
+    const int k = k0 + lane;
+    const int u = (k < nw) ? int(T.sub[T.W[T.ord[k]].site * 4 + q]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, u);
+    const int base = (u >= 0) ? T.bkt[u] : 0;
+    __syncwarp();
+    if (u >= 0) {
+      T.wsb[k] = uint16_t(u);
+      T.wrk[k] = uint16_t(base + __popc(peers & lt));
+      if ((peers & lt) == 0) T.bkt[u] = base + __popc(peers);
+    }
+    __syncwarp();
+  }
   const int n = T.nsub;
   const int chunk = (n + 31) / 32;
   const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
@@ -371,22 +391,6 @@ __device__ void sub_starts(const Tile& T, int lane) {
     T.bkt[i] = 0;
   }
   if (lane == 31) T.fill[n] = v;
-}
-
-// The worms of sub-block u in label order: a scan of wsb[] eight entries
-// (16 bytes) at a time; wsb[nw .. nw+8) holds kNone.
-__device__ __forceinline__ void collect_sub(const Tile& T, int nw, int u, uint16_t* seg) {
-  int m = 0;
-  const uint4* v = reinterpret_cast<const uint4*>(T.wsb);
-  for (int k0 = 0; k0 < nw; k0 += 8) {
-    const uint4 c = v[k0 >> 3];
-    const uint32_t h[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (int(h[j] & 0xffffu) == u) seg[m++] = T.ord[k0 + 2 * j];
-      if (int(h[j] >> 16) == u) seg[m++] = T.ord[k0 + 2 * j + 1];
-    }
-  }
 }
 
 }  // namespace
@@ -409,6 +413,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.idx = reinterpret_cast<uint16_t*>(sm + d.sm_idx);
   T.ord = reinterpret_cast<uint16_t*>(sm + d.sm_ord);
   T.wsb = reinterpret_cast<uint16_t*>(sm + d.sm_wsb);
+  T.wrk = reinterpret_cast<uint16_t*>(sm + d.sm_wrk);
+  T.rw = reinterpret_cast<uint64_t*>(sm + d.sm_rw);
   T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
   T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
@@ -570,29 +576,26 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       // label order; the r-th move of sub-block u draws Philox block r of
       // stream (unit = domain * n_sub + u, scatter | pass).
       for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
-      for (int k = nw + tid; k < nw + 8; k += NT) T.wsb[k] = kNone;
       __syncthreads();
       for (int pass = 0; pass < (nw > 0 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         const int q = pass & 3;
+        if (tid < 32) rank_pass(T, nw, q, tid);
+        __syncthreads();
+        const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
         for (int k = tid; k < nw; k += NT) {
-          const int u = T.sub[T.W[T.ord[k]].site * 4 + q];
-          T.wsb[k] = uint16_t(u);
-          atomicAdd(&T.bkt[u], 1);
+          const int u = T.wsb[k], r = T.wrk[k], at = T.fill[u] + r;
+          T.idx[at] = T.ord[k];
+          const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+          T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
+          T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
         }
         __syncthreads();
-        if (tid < 32) sub_starts(T, tid);  // fill[u] = first slot of sub-block u; bkt[] = 0
-        __syncthreads();
         phase_tick(d, 5, tclk);
-        const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
         for (int u = tid; u < T.nsub; u += NT) {
           const int lo = T.fill[u], n = T.fill[u + 1] - lo;
-          if (n == 0) continue;
-          uint16_t* seg = T.idx + lo;
-          collect_sub(T, nw, u, seg);  // the sub-block's worms in label order
+          const uint16_t* seg = T.idx + lo;
           for (int r = 0; r < n; ++r) {
-            const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
-            const int rc = tile_move(T, seg, n, r, q, uint64_t(b.x) | (uint64_t(b.y) << 32),
-                                     uint64_t(b.z) | (uint64_t(b.w) << 32));
+            const int rc = tile_move(T, seg, n, r, q, T.rw[2 * (lo + r)], T.rw[2 * (lo + r) + 1]);
             if (rc) { tile_fail(misc, rc, 5); break; }
           }
         }
@@ -777,7 +780,7 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   const size_t fixed = o;
   // worm side of the union: table, index, two bucket arrays
   const size_t worm_bytes = [&](int wcap) {
-    return up16(size_t(wcap) * sizeof(WormRec)) + 2 * up16(size_t(wcap) * 2) + up16(size_t(wcap + 8) * 2) +
+    return up16(size_t(wcap) * sizeof(WormRec)) + 4 * up16(size_t(wcap) * 2) + up16(size_t(wcap) * 16) +
            2 * up16(size_t(nb) * sizeof(int));
   }(d->wcap);
   const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
@@ -793,7 +796,9 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   size_t w = o + up16(size_t(d->wcap) * sizeof(WormRec));
   d->sm_idx = int(w); w = up16(w + size_t(d->wcap) * 2);
   d->sm_ord = int(w); w = up16(w + size_t(d->wcap) * 2);
-  d->sm_wsb = int(w); w = up16(w + size_t(d->wcap + 8) * 2);
+  d->sm_wsb = int(w); w = up16(w + size_t(d->wcap) * 2);
+  d->sm_wrk = int(w); w = up16(w + size_t(d->wcap) * 2);
+  d->sm_rw = int(w); w = up16(w + size_t(d->wcap) * 16);
   d->sm_bkt = int(w); w = up16(w + size_t(nb) * sizeof(int));
   d->sm_fill = int(w); w = up16(w + size_t(nb) * sizeof(int));
   o = std::max(w, o + pool_bytes);

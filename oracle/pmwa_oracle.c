@@ -119,15 +119,18 @@ double or_exp_det(double x) {
   return (p * ipow2(k + 600)) * ipow2(-600);
 }
 
-/* e^x - 1: Taylor series of degree 24 for |x| <= 1 (Horner, no constant
-   term), exp_det(x) - 1 otherwise.                                         */
+/* e^x - 1 for |x| <= 1: the Taylor series (Horner, no constant term) cut
+   at degree 7, 9, 13 or 19 as |x| <= 2^-6, 2^-4, 2^-2 or 1, which keeps the
+   truncation below 2^-57 relative; exp_det(x) - 1 for |x| > 1.             */
 double or_expm1_det(double x) {
   if (!(x <= 1.0 && x >= -1.0)) return or_exp_det(x) - 1.0;
-  double c[25];
+  double ax = fabs(x);
+  int d = (ax <= 0x1p-6) ? 7 : (ax <= 0x1p-4) ? 9 : (ax <= 0x1p-2) ? 13 : 19;
+  double c[20];
   double fact = 1.0;
-  for (int n = 1; n <= 24; n++) { fact = fact * (double)n; c[n] = 1.0 / fact; }
-  double p = c[24];
-  for (int n = 23; n >= 1; n--) p = p * x + c[n];
+  for (int n = 1; n <= 19; n++) { fact = fact * (double)n; c[n] = 1.0 / fact; }
+  double p = c[d];
+  for (int n = d - 1; n >= 1; n--) p = p * x + c[n];
   return p * x;
 }
 

@@ -112,12 +112,15 @@ __device__ inline double exp_det(double x) {
   return __dmul_rn(__dmul_rn(p, pow2i(k + 600)), pow2i(-600));
 }
 
-// e^x - 1: degree-24 Taylor polynomial (no constant term) on [-1, 1].
+// e^x - 1 on [-1, 1]: the Taylor polynomial (no constant term) of degree
+// 7, 9, 13 or 19 as |x| <= 2^-6, 2^-4, 2^-2 or 1 (truncation below 2^-57
+// relative), Horner's rule with explicit rounding; exp_det(x) - 1 beyond.
 __device__ inline double expm1_det(double x) {
   if (!(x <= 1.0 && x >= -1.0)) return __dsub_rn(exp_det(x), 1.0);
-  double p = c_inv_fact[24];
-#pragma unroll
-  for (int n = 23; n >= 1; --n) p = __dadd_rn(__dmul_rn(p, x), c_inv_fact[n]);
+  const double ax = fabs(x);
+  const int d = (ax <= 0x1p-6) ? 7 : (ax <= 0x1p-4) ? 9 : (ax <= 0x1p-2) ? 13 : 19;
+  double p = c_inv_fact[d];
+  for (int n = d - 1; n >= 1; --n) p = __dadd_rn(__dmul_rn(p, x), c_inv_fact[n]);
   return __dmul_rn(p, x);
 }
 

@@ -84,12 +84,55 @@ __device__ bool site_legs(const uint64_t* K, int n, uint64_t pv, Legs* L) {
   return true;
 }
 
-__device__ __forceinline__ void aslot_erase(uint64_t* K, int n, int at) {
-  for (int k = at; k + 1 < n; ++k) K[k] = K[k + 1];
-}
+// Warp-cooperative list edits on a staged site list (all 32 lanes call them
+// with the same arguments and see the same result).
+//
+// insert `key` at index `at`, shifting K[at..n) up by one, 32 keys at a time
+// from the top (each chunk is read before any lane writes it)
 __device__ __forceinline__ void aslot_insert(uint64_t* K, int n, int at, uint64_t key) {
-  for (int k = n; k > at; --k) K[k] = K[k - 1];
-  K[at] = key;
+  const int lane = threadIdx.x & 31;
+  for (int top = n; top > at; top -= 32) {
+    const int k = top - 1 - lane;
+    const bool act = k >= at;
+    uint64_t v = 0;
+    if (act) v = K[k];
+    __syncwarp();
+    if (act) K[k + 1] = v;
+    __syncwarp();
+  }
+  if (lane == 0) K[at] = key;
+  __syncwarp();
+}
+
+// keep the keys for which drop(key) is false, in order; returns their count
+template <class Drop>
+__device__ __forceinline__ int warp_compact(uint64_t* K, int n, Drop drop) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int w = 0;
+  for (int b = 0; b < n; b += 32) {
+    const int k = b + lane;
+    uint64_t key = 0;
+    bool keep = false;
+    if (k < n) { key = K[k]; keep = !drop(key); }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    if (keep) K[w + __popc(m & lt)] = key;
+    w += __popc(m);
+    __syncwarp();
+  }
+  return w;
+}
+
+// first index >= from whose key has tag `tag` (n if none)
+__device__ __forceinline__ int warp_find_tag(const uint64_t* K, int n, int from, int tag) {
+  const int lane = threadIdx.x & 31;
+  for (int b = from; b < n; b += 32) {
+    const int k = b + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, k < n && ktag(K[k]) == tag);
+    if (m) return b + __ffs(int(m)) - 1;
+  }
+  return n;
 }
 
 // erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
@@ -98,16 +141,11 @@ __device__ __forceinline__ void aslot_insert(uint64_t* K, int n, int at, uint64_
 __device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_t* K, int& n,
                               uint64_t lo, uint64_t hi, int p, int q) {
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
-  int w = 0;
-  for (int k = 0; k < n; ++k) {  // compact away the worms of the interval
-    const uint64_t key = K[k];
-    if (kworm(key)) {
-      const uint64_t off = (kpk(key) + kTwo62 - lo) & (kTwo62 - 1);
-      if (off > 0 && off < span) continue;
-    }
-    K[w++] = key;
-  }
-  n = w;
+  n = warp_compact(K, n, [&](uint64_t key) {  // the worms of the interval
+    if (!kworm(key)) return false;
+    const uint64_t off = (kpk(key) + kTwo62 - lo) & (kTwo62 - 1);
+    return off > 0 && off < span;
+  });
   uint64_t offs[kMaxWormsPerInterval];
   int bad = 0;
   const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SWs, d.SWI, offs, &bad);
@@ -150,8 +188,7 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
   uint64_t last = 0;
   bool any = false;
   for (;;) {
-    int k = any ? slot_lower(KA, nA, last + 1) : 0;
-    while (k < nA && ktag(KA[k]) != tag) ++k;
+    const int k = warp_find_tag(KA, nA, any ? slot_lower(KA, nA, last + 1) : 0, tag);
     if (k >= nA) break;
     const uint64_t pv = kpk(KA[k]);
     last = pv;
@@ -185,13 +222,17 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
       }
       wS = w;
     }
+    // running sums in the order S = 0..15 over the states of non-zero
+    // weight only (adding +0.0 changes no sum, so this is the sequential
+    // sum over all 16); a zero-weight state keeps cumS = 0 and is never hit
+    const unsigned pos = __ballot_sync(0xffffffffu, lane < 16 && wS > 0.0);
+    if (!pos) return PMWA_EINVARIANT;
     double tot = 0.0, cumS = 0.0;
-    for (int S = 0; S < 16; ++S) {
+    for (unsigned m = pos; m; m &= m - 1) {
+      const int S = __ffs(int(m)) - 1;
       tot = __dadd_rn(tot, __shfl_sync(0xffffffffu, wS, S));
       if (lane == S) cumS = tot;
     }
-    const unsigned pos = __ballot_sync(0xffffffffu, lane < 16 && wS > 0.0);
-    if (!pos) return PMWA_EINVARIANT;
     const int lastS = 31 - __clz(int(pos));
     const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
     const unsigned hit = __ballot_sync(0xffffffffu, lane < 16 && u < cumS);
@@ -217,20 +258,11 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
   if (nB) baseB = kab(KB[nB - 1]);
   // Step 3 on this bond: erase its diagonal vertices, lay new ones
   {
-    int wa = 0;
-    for (int k = 0; k < nA; ++k) {
-      const uint64_t key = KA[k];
-      if (ktag(key) == uint64_t(tag) && kab(key) == kbl(key)) continue;
-      KA[wa++] = key;
-    }
-    const int removed = nA - wa;
+    auto diag = [&](uint64_t key) { return ktag(key) == tag && kab(key) == kbl(key); };
+    const int wa = warp_compact(KA, nA, diag);
+    const int wb = warp_compact(KB, nB, diag);
+    const int removed = nA - wa, gone = nB - wb;
     nA = wa;
-    int wb = 0, gone = 0;
-    for (int k = 0; k < nB; ++k) {
-      const uint64_t key = KB[k];
-      if (ktag(key) == uint64_t(tag) && kab(key) == kbl(key)) { ++gone; continue; }
-      KB[wb++] = key;
-    }
     nB = wb;
     if (gone != removed) return PMWA_EINVARIANT;
   }

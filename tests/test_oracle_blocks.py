@@ -63,7 +63,12 @@ def test_exp_det_close_to_libm():
             assert abs(got - want) <= 4 * 5e-324 + 2e-16 * want
             continue
         assert abs(got - want) <= 2 * math.ulp(want), x
-    for x in np.linspace(-3, 3, 6001):
+    # every degree band of the series (|x| <= 2^-6, 2^-4, 2^-2, 1) and its
+    # edges, both signs, plus the exp_det branch beyond 1
+    mags = np.concatenate([np.geomspace(1e-12, 1.0, 6001), np.linspace(0.0, 3.0, 6001),
+                           np.array([2.0 ** -6, 2.0 ** -4, 2.0 ** -2, 1.0])])
+    mags = np.concatenate([mags, np.nextafter(mags, 0.0), np.nextafter(mags, 4.0)])
+    for x in np.concatenate([mags, -mags]):
         got = lib.or_expm1_det(float(x))
         want = math.expm1(float(x))
         assert abs(got - want) <= 4 * math.ulp(want) + 1e-300, x

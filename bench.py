@@ -47,6 +47,43 @@ DESCR = {
 }
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TILE_PROFILE = os.path.join(ROOT, "profiles", "k_tile_config2.md")
+TILE_SOURCES = ["pmwa_tile.cu", "pmwa_device.cuh", "pmwa_internal.h"]
+
+
+def tile_source_hash():
+    """sha256 over the sources of the sweep kernel (k_tile)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TILE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1307_0328_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def tile_traffic(wl, events):
+    """DRAM bytes (read + write) per k_tile launch: the bytes per event of
+    the committed ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
+    of one launch / that launch's events) times this run's mean events per
+    launch, when the capture was taken on this workload from the current
+    kernel sources; else None."""
+    try:
+        with open(TILE_PROFILE) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("traffic_record:"):
+            for kv in line.split(":", 1)[1].split():
+                k, _, v = kv.partition("=")
+                vals[k] = v
+    if vals.get("workload") != wl or vals.get("sources_sha256") != tile_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_event"]) * events
+    except (KeyError, ValueError):
+        return None
 
 
 def peaks():
@@ -233,7 +270,7 @@ def serving_run(n_jobs, scale, budget_gb=64.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
@@ -374,7 +411,8 @@ def main():
                         mean_vertices=float(rows["n_v"].mean()), mean_worms=nw,
                         plain_per_instance=True),
             roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=peak, unit="GB/s",
-                          frac=achieved / peak, traffic=None,
+                          frac=achieved / peak, traffic=tile_traffic(wl, ev) if top == "tile" else None,
+                          alg_bytes_per_launch=alg.get(top, 0.0),
                           peak_source=which + " MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"),
             kernels=kernels,
             tile_phase_cycles=phases,
@@ -383,7 +421,7 @@ def main():
             clocks=clk, wall_s=wall,
         )
         if not args.no_batch:
-            line["batched"] = batched_vs_plain(P, args.steps, args.warmup)
+            line["batched"] = batched_vs_plain(P, min(args.steps, 20), args.warmup)
         if args.serve_jobs > 0:
             line["serving"] = serving_run(args.serve_jobs, args.serve_scale)
         if not args.no_cpu:

@@ -95,6 +95,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def legs_hint(n_v, kw, slack=1.05):
+    """Vertex legs per site from a pilot, 2 n_v / N times a slack for a
+    chain still drifting, rounded up (the sizing hint of the shared-memory
+    leg table; the library adds 8 standard deviations)."""
+    return int(math.ceil(slack * 2.0 * float(n_v) / (kw["Lx"] * kw["Ly"])))
+
+
 def ncycle_rule(n_v, n_w):
     """Every vertex leg visited once per sweep on average: each move lands a
     worm on one leg, a sweep has 2 n_v legs and n_w worms move per pass
@@ -178,11 +185,11 @@ def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
 
 def oracle_pilot_n_cycle(wl, pilot):
     """The same N_cycle rule as the GPU arm, from a pilot run of the oracle:
-    N_cycle = ceil(2 <n_v> / <n_w>) over the second half of `pilot` sweeps
-    at 16 passes."""
+    N_cycle = ceil(2 <n_v> / <n_w>) over the second half of the pilot
+    sweeps (at most 60) at 16 passes."""
     from oracle import oracle as O
     o = O.Oracle(n_cycle=16, **WORKLOADS[wl])
-    o.sweep(max(2, pilot))
+    o.sweep(max(2, min(pilot, 60)))  # a bounded CPU sample
     r = o.rows()
     half = r[len(r) // 2:]
     return ncycle_rule(float(half["n_v"].mean()), float(half["n_w"].mean()))
@@ -274,7 +281,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
-    ap.add_argument("--pilot", type=int, default=30, help="thermalisation sweeps of the N_cycle pilot")
+    ap.add_argument("--pilot", type=int, default=200, help="thermalisation sweeps of the N_cycle pilot")
     ap.add_argument("--n-cycle", type=int, default=0, help="fix N_cycle instead of the pilot rule")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -319,6 +326,7 @@ def main():
         r = pilot.rows()
         half = r[len(r) // 2:]
         nc = ncycle_rule(half["n_v"].mean(), half["n_w"].mean())
+        kw["legs_hint"] = legs_hint(r[3 * len(r) // 4:]["n_v"].max(), kw)
         snap = pilot.export()
         s_idx = pilot.sweep_index
         pilot.close()
@@ -329,11 +337,23 @@ def main():
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = sim.stream
 
-    # warm-up
-    sim.sweep(args.warmup)
+    # warm-up; a leg table sized from the pilot that turns out too small
+    # (PMWA_ECAPACITY) is replaced by the a-priori bound, from the same state
+    snap0, idx0 = sim.export(), sim.sweep_index
+    try:
+        sim.sweep(args.warmup)
+    except P.PmwaError as e:
+        if e.status != P.PMWA_ECAPACITY:
+            raise
+        sim.close()
+        kw["legs_hint"] = 0
+        sim = P.Sim(n_cycle=nc, **kw)
+        sim.import_(snap0)
+        sim.sweep_index = idx0
+        sim.sweep(args.warmup)
     sim.rows()
+    stream = sim.stream
     # timed region: per-sweep device spans (library events on its stream)
     P.pmwa_profile(sim.h, True)
     P.pmwa_profile_read(sim.h)
@@ -407,6 +427,7 @@ def main():
             ms_per_step=1000.0 * t_job / args.steps, higher_is_better=True, scaling="weak",
             vs_baseline=None, dtype="u64", data="synthetic",
             config=dict(workload=DESCR[wl], n_cycle=nc, sub_block=kw["sub_block"], replicas_per_gpu=1,
+                        legs_hint=kw.get("legs_hint", 0), pilot_sweeps=args.pilot,
                         l2="flushed before every timed sweep (256 MB write)",
                         mean_vertices=float(rows["n_v"].mean()), mean_worms=nw,
                         plain_per_instance=True),

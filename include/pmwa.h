@@ -71,7 +71,13 @@ typedef struct {
   uint32_t replica;         /* 0..65535, mixed into every Philox counter          */
   int32_t  cap_site;        /* events per site slot; 0 = sized from beta, t, V, mu */
   int32_t  rows_cap;        /* measurement rows held on the device; 0 = 4096      */
-  int32_t  reserved[5];     /* must be 0                                          */
+  int32_t  legs_hint;       /* mean vertex legs per site, e.g. 2 n_v / N from a
+                               pilot run: sizes the shared-memory leg table of a
+                               domain tighter than the bound 4 beta (D + t), which
+                               leaves room to stage the domain's configuration in
+                               shared memory; 0 = the bound.  Too small a hint
+                               makes a sweep return PMWA_ECAPACITY.            */
+  int32_t  reserved[4];     /* must be 0                                          */
 } pmwa_params;
 
 /* One row per sweep (Step 6 measurement after Step 5). */
@@ -207,6 +213,13 @@ int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* dev_arena, 
 int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4,
                 uint64_t* th256, double* sv, double* sw,
                 double* zig_x, double* zig_f, double* zig_w, uint64_t* zig_k);
+
+/* The shared-memory plan of a domain for these parameters: *smem bytes per
+   CTA, *legcap vertex legs in its leg table, *oldcap events of the current
+   configuration staged in shared memory for Steps 3 (0: read from HBM).
+   Host only; returns PMWA_EINVAL for invalid parameters or a domain that
+   does not fit.  Any pointer may be NULL. */
+int pmwa_tile_plan(const pmwa_params* p, int32_t* smem, int32_t* legcap, int32_t* oldcap);
 
 /* Shared memory (bytes) the sweep kernel needs per domain for these
    parameters, 0 if a domain does not fit on one SM (a domain-shape tuner

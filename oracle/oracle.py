@@ -97,6 +97,8 @@ def lib():
 def make_params(**kw):
     d = dict(DEFAULTS)
     d.update(kw)
+    for k in ("cap_site", "rows_cap", "legs_hint"):  # device capacities: no meaning here
+        d.pop(k, None)
     if not d["dom_x"]:
         d["dom_x"] = d["Lx"]
     if not d["dom_y"]:

@@ -31,7 +31,7 @@ class Params(C.Structure):
                 ("sub_block", C.c_int32), ("init", C.c_int32),
                 ("init_seed", C.c_uint64), ("c_off", C.c_double),
                 ("replica", C.c_uint32), ("cap_site", C.c_int32),
-                ("rows_cap", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("rows_cap", C.c_int32), ("legs_hint", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
@@ -39,7 +39,7 @@ ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", 
 
 DEFAULTS = dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1, dom_x=0, dom_y=0,
                 exchange_every=2, n_cycle=8, sub_block=0, init=1, init_seed=1, c_off=-1.0,
-                replica=0, cap_site=0, rows_cap=0)
+                replica=0, cap_site=0, rows_cap=0, legs_hint=0)
 
 _lib = None
 
@@ -74,6 +74,7 @@ def load(build=True):
         "pmwa_strerror": (C.c_char_p, [C.c_int]),
         "pmwa_profile": (C.c_int, [vp, C.c_int32]),
         "pmwa_set_n_cycle": (C.c_int, [vp, C.c_int32]),
+        "pmwa_tile_plan": (C.c_int, [P(Params), vp, vp, vp]),
         "pmwa_tile_smem": (C.c_int32, [P(Params)]),
         "pmwa_batch_footprint": (sz, [vp, C.c_int32]),
         "pmwa_batch_create": (C.c_int, [vp, C.c_int32, vp, sz, vp, P(vp)]),
@@ -205,6 +206,13 @@ def pmwa_set_sweep(h, s):
 
 def pmwa_tile_smem(**kw):
     return int(load().pmwa_tile_smem(C.byref(make_params(**kw))))
+
+
+def pmwa_tile_plan(**kw):
+    """Shared-memory plan of a domain: dict(smem, legcap, oldcap)."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check("pmwa_tile_plan", load().pmwa_tile_plan(C.byref(make_params(**kw)), C.byref(a), C.byref(b), C.byref(c)))
+    return dict(smem=a.value, legcap=b.value, oldcap=c.value)
 
 
 def pmwa_set_n_cycle(h, n):

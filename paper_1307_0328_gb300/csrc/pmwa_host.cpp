@@ -40,7 +40,7 @@ namespace {
 
 struct Derived {
   int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap, poolcap;
-  double legs_per_site, mb;
+  double legs_want, mb;  // legs wanted in a domain table; mean Step-3 candidates per bond
   double d[4], D, tkink, SV, SW, XW;
   GridScale SVs, SWs, XQ;
   uint64_t TV[4], SWI;
@@ -69,7 +69,8 @@ int validate(const pmwa_params* p) {
   if (B && B < dy && dy % B) return PMWA_EINVAL;
   if (p->replica >= 65536u || p->init < 0 || p->init > 1) return PMWA_EINVAL;
   if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
-  for (int k = 0; k < 5; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  if (p->legs_hint < 0 || p->legs_hint > (1 << 20)) return PMWA_EINVAL;
+  for (int k = 0; k < 4; ++k) if (p->reserved[k]) return PMWA_EINVAL;
   // the gap arithmetic needs the mean grid spacings 2^59/(beta eta) and
   // 2^59/(beta D) in [2^39, 2^99]
   const double be = p->beta * p->eta;
@@ -187,7 +188,14 @@ void derive(const pmwa_params* p, Derived* g) {
   // shared-memory tile of one domain: legs (<= 4 bonds x beta (D + t) per
   // site), Step-3 candidates (mean beta D per bond), worms (<= beta eta per site)
   const int nds = g->dom_x * g->dom_y;
-  g->legs_per_site = 4.0 * p->beta * (g->D + p->t);
+  // legs wanted in a domain's table: the bound 4 beta (D + t) per site with
+  // 10 % slack, or a measured mean per site with 8 standard deviations
+  if (p->legs_hint > 0) {
+    const double m = double(p->legs_hint) * nds;
+    g->legs_want = m + 8.0 * std::sqrt(m) + 128.0;
+  } else {
+    g->legs_want = 1.1 * 4.0 * p->beta * (g->D + p->t) * nds + 256.0;
+  }
   g->poolcap = int(std::min(60000.0, 1.5 * mb * 2.0 * nds + 256.0));
   g->wcap = int(std::min(16000.0, 2.0 * p->beta * p->eta * nds + 256.0));
 }
@@ -416,7 +424,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   h->err = d.err;
   h->phase = reinterpret_cast<unsigned long long*>(base + L.phase);
   d.phase_cycles = nullptr;
-  if (!plan_tile_smem(&d, g.legs_per_site, g.mb)) {  // a domain too large for shared memory
+  if (!plan_tile_smem(&d, g.legs_want, g.mb)) {  // a domain too large for shared memory
     delete h;
     return PMWA_EINVAL;
   }
@@ -467,16 +475,24 @@ int pmwa_destroy(pmwa_handle* h) {
   return PMWA_OK;
 }
 
-int32_t pmwa_tile_smem(const pmwa_params* p) {
-  if (validate(p)) return 0;
+int pmwa_tile_plan(const pmwa_params* p, int32_t* smem, int32_t* legcap, int32_t* oldcap) {
+  if (validate(p)) return PMWA_EINVAL;
   Derived g;
   derive(p, &g);
   Dev d;
   std::memset(&d, 0, sizeof d);
   d.Lx = p->Lx; d.Ly = p->Ly; d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy;
   d.sub_block = p->sub_block; d.wcap = g.wcap; d.poolcap = g.poolcap;
-  if (!plan_tile_smem(&d, g.legs_per_site, g.mb)) return 0;
-  return d.sm_total;
+  if (!plan_tile_smem(&d, g.legs_want, g.mb)) return PMWA_EINVAL;
+  if (smem) *smem = d.sm_total;
+  if (legcap) *legcap = d.legcap;
+  if (oldcap) *oldcap = d.oldcap;
+  return PMWA_OK;
+}
+
+int32_t pmwa_tile_smem(const pmwa_params* p) {
+  int32_t smem = 0;
+  return pmwa_tile_plan(p, &smem, nullptr, nullptr) ? 0 : smem;
 }
 
 int pmwa_set_n_cycle(pmwa_handle* h, int32_t n_cycle) {
@@ -727,6 +743,9 @@ struct pmwa_batch {
   int2* bwork[2] = {nullptr, nullptr};
   int n_tile = 0, n_bwork[2] = {0, 0}, cap_max = 0;
   int cls_off[3] = {0, 0, 0}, cls_n[3] = {0, 0, 0}, cls_smem[3] = {0, 0, 0};
+  int bcls_off[2][3] = {{0, 0, 0}, {0, 0, 0}}, bcls_n[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};  // one capture branch per CTA-size class
+  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph = nullptr;
   int graph_sweeps = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -799,6 +818,55 @@ void build_tile_work(pmwa_batch* b, std::vector<int2>* work) {
   }
 }
 
+// Boundary work of both directions: blocks of bonds per instance, grouped
+// by the instance's CTA-size class (its domains all have one size), so that
+// each class can run as its own chain of launches.
+int build_boundary_work(pmwa_batch* b) {
+  std::vector<int2> bw;
+  const int bpb = boundary_bonds_per_block(b->cap_max);
+  for (int dir = 0; dir < 2; ++dir) {
+    bw.clear();
+    for (int c = 0; c < 3; ++c) {
+      b->bcls_off[dir][c] = int(bw.size());
+      for (int i = 0; i < b->n; ++i) {
+        const Dev& d = b->h[size_t(i)]->d;
+        if (tile_class(d.dom_x * d.dom_y) != c) continue;
+        const int nb = dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
+        for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
+      }
+      b->bcls_n[dir][c] = int(bw.size()) - b->bcls_off[dir][c];
+    }
+    b->n_bwork[dir] = int(bw.size());
+    if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
+      return PMWA_ECUDA;
+  }
+  return PMWA_OK;
+}
+
+int batch_streams(pmwa_batch* b) {
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) || cudaEventCreate(&b->ev0) ||
+      cudaEventCreate(&b->ev1) || cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming))
+    return PMWA_ECUDA;
+  for (int c = 0; c < 3; ++c)
+    if (cudaStreamCreateWithFlags(&b->cs[c], cudaStreamNonBlocking) ||
+        cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming))
+      return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
+void batch_free_streams(pmwa_batch* b) {
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int c = 0; c < 3; ++c) {
+    if (b->cs[c]) cudaStreamDestroy(b->cs[c]);
+    if (b->join[c]) cudaEventDestroy(b->join[c]);
+  }
+  b->cap = nullptr; b->ev0 = b->ev1 = b->fork = nullptr;
+  for (int c = 0; c < 3; ++c) { b->cs[c] = nullptr; b->join[c] = nullptr; }
+}
+
 int batch_upload(pmwa_batch* b) {
   std::vector<Dev> devs(size_t(b->n));
   for (int i = 0; i < b->n; ++i) devs[size_t(i)] = b->h[size_t(i)]->d;
@@ -820,6 +888,18 @@ void batch_drop_graph(pmwa_batch* b) {
 }
 
 // one batched sweep at iteration `it` (boundary x, boundary y, tile)
+// One sweep of the instances of class c: boundary x, boundary y, tile.
+int batch_launch_class(pmwa_batch* b, int it, int c, cudaStream_t st) {
+  for (int dir = 0; dir < 2; ++dir)
+    if (b->bcls_n[dir][c] && launch_boundary_batch(b->devs, b->base, b->bwork[dir] + b->bcls_off[dir][c],
+                                                   b->bcls_n[dir][c], it, dir, b->cap_max, st))
+      return PMWA_ECUDA;
+  if (b->cls_n[c] && launch_tile_batch(c, b->devs, b->base, b->tile_work + b->cls_off[c], b->cls_n[c],
+                                       b->cls_smem[c], it, 6, st))
+    return PMWA_ECUDA;
+  return PMWA_OK;
+}
+
 int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
   for (int dir = 0; dir < 2; ++dir)
     if (b->n_bwork[dir] &&
@@ -873,30 +953,13 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     b->cap_max = std::max(b->cap_max, hi->d.cap);
   }
   if (rc == PMWA_OK && cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
-  if (rc == PMWA_OK) {
-    std::vector<int2> bw;
-    for (int dir = 0; dir < 2 && rc == PMWA_OK; ++dir) {
-      bw.clear();
-      const int bpb = boundary_bonds_per_block(b->cap_max);
-      for (int i = 0; i < n; ++i) {
-        Derived g;
-        derive(p + i, &g);
-        const int nb = boundary_bonds(p + i, g, dir);
-        for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
-      }
-      b->n_bwork[dir] = int(bw.size());
-      if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
-        rc = PMWA_ECUDA;
-    }
-  }
+  if (rc == PMWA_OK) rc = build_boundary_work(b);
   if (rc == PMWA_OK) rc = batch_upload(b);
   if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
-  if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
-                        cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
-    rc = PMWA_ECUDA;
+  if (rc == PMWA_OK) rc = batch_streams(b);
   if (rc) {
     for (pmwa_handle* hi : b->h) if (hi) pmwa_destroy(hi);
-    if (b->cap) cudaStreamDestroy(b->cap);
+    batch_free_streams(b);
     delete b;
     return rc;
   }
@@ -953,31 +1016,22 @@ int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* arena, size
     b->cap_max = std::max(b->cap_max, hs[i]->d.cap);
   }
   if (cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
-  std::vector<int2> bw;
-  for (int dir = 0; dir < 2 && rc == PMWA_OK; ++dir) {
+  for (int dir = 0; dir < 2; ++dir) {
     b->bwork[dir] = reinterpret_cast<int2*>(base + o);
-    bw.clear();
-    const int bpb = boundary_bonds_per_block(b->cap_max);
     int nb_total = 0;
     for (int i = 0; i < n; ++i) {
       const Dev& d = hs[i]->d;
-      const int nb = dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
-      nb_total += nb;
-      for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
+      nb_total += dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
     }
     o = align_up(o + size_t(std::max(1, nb_total)) * sizeof(int2));
-    b->n_bwork[dir] = int(bw.size());
-    if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
-      rc = PMWA_ECUDA;
   }
+  if (rc == PMWA_OK) rc = build_boundary_work(b);
   if (rc == PMWA_OK) rc = batch_upload(b);
   if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
-  if (rc == PMWA_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) ||
-                        cudaEventCreate(&b->ev0) || cudaEventCreate(&b->ev1)))
-    rc = PMWA_ECUDA;
+  if (rc == PMWA_OK) rc = batch_streams(b);
   if (rc) {
     for (int i = 0; i < n; ++i) hs[i]->err = hs[i]->d.err = b->own_err[size_t(i)];
-    if (b->cap) cudaStreamDestroy(b->cap);
+    batch_free_streams(b);
     delete b;
     return rc;
   }
@@ -1016,10 +1070,20 @@ int pmwa_batch_graph(pmwa_batch* b, int32_t sweeps) {
     if (rc) return rc;
     b->dirty = false;
   }
+  // one branch per CTA-size class: the classes hold different instances, so
+  // each runs its S sweeps as its own chain of launches and their tails
+  // overlap; the branches join before the advance kernel
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) return PMWA_ECUDA;
   int rc = PMWA_OK;
-  for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_sweep(b, it, b->cap);
+  if (cudaEventRecord(b->fork, b->cap)) rc = PMWA_ECUDA;
+  for (int c = 0; c < 3 && rc == PMWA_OK; ++c) {
+    if (!b->cls_n[c] && !b->bcls_n[0][c] && !b->bcls_n[1][c]) continue;
+    if (cudaStreamWaitEvent(b->cs[c], b->fork, 0)) { rc = PMWA_ECUDA; break; }
+    for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_class(b, it, c, b->cs[c]);
+    if (rc == PMWA_OK && (cudaEventRecord(b->join[c], b->cs[c]) || cudaStreamWaitEvent(b->cap, b->join[c], 0)))
+      rc = PMWA_ECUDA;
+  }
   if (rc == PMWA_OK && launch_advance(b->base, b->n, sweeps, b->cap)) rc = PMWA_ECUDA;
   if (cudaStreamEndCapture(b->cap, &g) || rc) {
     if (g) cudaGraphDestroy(g);
@@ -1095,9 +1159,7 @@ int pmwa_batch_destroy(pmwa_batch* b) {
   } else {
     for (pmwa_handle* hi : b->h) pmwa_destroy(hi);
   }
-  if (b->cap) cudaStreamDestroy(b->cap);
-  if (b->ev0) cudaEventDestroy(b->ev0);
-  if (b->ev1) cudaEventDestroy(b->ev1);
+  batch_free_streams(b);
   delete b;
   return PMWA_OK;
 }

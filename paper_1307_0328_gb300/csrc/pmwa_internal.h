@@ -45,6 +45,8 @@ struct Dev {
   // shared-memory carve-up of the tile kernel (byte offsets)
   int sm_th, sm_zig, sm_off, sm_base, sm_bcnt, sm_boff, sm_misc, sm_nbr, sm_sub, sm_tinfo, sm_leg, sm_wcnt, sm_pool,
       sm_worm, sm_idx, sm_ord, sm_wsb, sm_wrk, sm_rw, sm_bkt, sm_fill, sm_total;
+  int sm_soff, sm_old;  // staged current configuration of the domain (phases 1-2)
+  int oldcap;           // events it can hold; 0 = read the configuration from HBM
   unsigned long long* phase_cycles;  // 8 counters when profiling, else null
   // random numbers
   uint32_t key0, key1, replica, sweep;
@@ -126,7 +128,7 @@ int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sum
 int rho_slices_static(const Dev& d, int K, double* host_out, void* stream);
 // shared-memory plan of the tile kernel for this instance (fills the sm_*
 // offsets); returns false if a domain cannot fit in shared memory.
-bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond);
+bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond);
 
 // Step-5 sub-block count along one axis (host copy of the device rule).
 inline int sb_slots_host(int D, int B, int nd) {

@@ -111,9 +111,16 @@ struct Tile {
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
   uint8_t* tinfo;  // [6 nds] per leg tag: 1 = lower site of the bond, 2 = bond leaves the domain
   uint16_t* sub;   // [4 nds] sub-block of each site for offset pattern pass & 3
+  int* soff;       // [nds + 1] start of each site's events in old[] (when staged)
+  uint64_t* old;   // [oldcap] the domain's current configuration (when staged)
+  bool staged;
   int x0, y0, nds, nsub;
 
   __device__ int gsite(int li) const { return (x0 + li % d->dom_x) + d->Lx * (y0 + li / d->dom_x); }
+  // current events of local site li (global site s): the staged copy or HBM
+  __device__ const uint64_t* okeys(int li, int s) const {
+    return staged ? old + soff[li] : d->keyA + size_t(s) * d->cap;
+  }
   __device__ int lsite(int s) const { return (s % d->Lx - x0) + d->dom_x * (s / d->Lx - y0); }
   __device__ int sub_of(int li, int pass) const {
     const int B = d->sub_block;
@@ -127,11 +134,10 @@ struct Tile {
 
 // ---------------------------------------------------------------------------
 // phase 1: Step 3 candidates of bond (a, dir) from the current configuration
-__device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, uint64_t* buf, int cap, int* bad) {
+__device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, const uint64_t* KA, const uint64_t* KB,
+                               uint64_t* buf, int cap, int* bad) {
   const int b = site_step(d, a, dir, +1);
   const uint64_t tag = uint64_t(bond_tag(d, a, dir));
-  const uint64_t* KA = d.keyA + size_t(a) * d.cap;
-  const uint64_t* KB = d.keyA + size_t(b) * d.cap;
   const uint32_t ca = d.cntA[a], cb = d.cntA[b];
   const int nA = cnt_n(ca), nB = cnt_n(cb);
   Stream s;
@@ -393,6 +399,44 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
   if (lane == 31) T.fill[n] = v;
 }
 
+// All N_cycle passes of a domain holding nw <= 32 worms, run by one warp
+// (lane = threadIdx.x < 32) with no block barrier.  Lane k holds the k-th
+// worm in label order; __match_any_sync over the sub-blocks gives each worm
+// its rank r inside its sub-block, and round r moves the r-th worm of every
+// sub-block at once (sub-blocks share no sites), so every sub-block's worms
+// move in label order with the r-th move drawing Philox block r, as in the
+// block-wide passes.  Returns a status (the same for all lanes).
+__device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
+  const Dev& d = *T.d;
+  const unsigned lt = (1u << lane) - 1u;
+  const bool act = lane < nw;
+  const int w = act ? T.ord[lane] : 0;
+  for (int pass = 0; pass < d.n_cycle; ++pass) {
+    const int q = pass & 3;
+    const int u = act ? int(T.sub[T.W[w].site * 4 + q]) : 0x7fffffff;
+    const unsigned peers = __match_any_sync(0xffffffffu, u);
+    const int r = __popc(peers & lt), n = __popc(peers);
+    int less = 0;  // worms of sub-blocks numbered below u: the start of u's group
+    for (int j = 0; j < 32; ++j) less += (__shfl_sync(0xffffffffu, u, j) < u) ? 1 : 0;
+    if (act) T.idx[less + r] = uint16_t(w);
+    const int maxr = __reduce_max_sync(0xffffffffu, act ? r : 0);
+    P4 b{0u, 0u, 0u, 0u};
+    if (act) b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2_word(kScatter, uint32_t(pass), d.replica),
+                        d.sweep, d.key0, d.key1);
+    __syncwarp();
+    int rc = PMWA_OK;
+    for (int rr = 0; rr <= maxr; ++rr) {
+      if (act && r == rr)
+        rc = tile_move(T, T.idx + less, n, r, q, uint64_t(b.x) | (uint64_t(b.y) << 32),
+                       uint64_t(b.z) | (uint64_t(b.w) << 32));
+      __syncwarp();
+    }
+    const unsigned bad = __ballot_sync(0xffffffffu, rc != PMWA_OK);
+    if (bad) return __shfl_sync(0xffffffffu, rc, __ffs(int(bad)) - 1);
+  }
+  return PMWA_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -420,6 +464,9 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
   T.tinfo = reinterpret_cast<uint8_t*>(sm + d.sm_tinfo);
   T.sub = reinterpret_cast<uint16_t*>(sm + d.sm_sub);
+  T.soff = reinterpret_cast<int*>(sm + d.sm_soff);
+  T.old = reinterpret_cast<uint64_t*>(sm + d.sm_old);
+  T.staged = false;
   T.x0 = (dom % d.ndx) * d.dom_x;
   T.y0 = (dom / d.ndx) * d.dom_y;
   T.nds = d.dom_x * d.dom_y;
@@ -449,14 +496,34 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   }
   __syncthreads();
 
+  // stage the domain's current configuration in shared memory (one warp per
+  // site, coalesced), so that the scans of phases 1-2 do not wait on HBM/L2
+  if (d.oldcap > 0) {
+    for (int li = tid; li < nds; li += NT) T.soff[li] = cnt_n(d.cntA[T.gsite(li)]);
+    __syncthreads();
+    if (block_scan(T.soff, nds, wsum) <= d.oldcap) {
+      const int lane = tid & 31;
+      for (int li = tid >> 5; li < nds; li += NT >> 5) {
+        const uint64_t* KO = d.keyA + size_t(T.gsite(li)) * d.cap;
+        const int st = T.soff[li], n = T.soff[li + 1] - st;
+        for (int k = lane; k < n; k += 32) T.old[st + k] = KO[k];
+      }
+      T.staged = true;
+    }
+    __syncthreads();
+  }
+
   // ---- phase 1: Step 3 candidates per bond
   for (int lb = tid; lb < 2 * nds; lb += NT) {
     const int li = lb >> 1, dir = lb & 1;
     const int a = T.gsite(li);
     uint64_t buf[kMaxCandPerBond];
     int n = 0, bad = 0;
-    if (d.has_vertices && !boundary_bond(d, a, dir))
-      n = bond_candidates(d, Z, a, dir, buf, min(d.capb, kMaxCandPerBond), &bad);
+    if (d.has_vertices && !boundary_bond(d, a, dir)) {
+      const int b = site_step(d, a, dir, +1);
+      n = bond_candidates(d, Z, a, dir, T.okeys(li, a), T.okeys(T.lsite(b), b), buf, min(d.capb, kMaxCandPerBond),
+                          &bad);
+    }
     if (bad) { tile_fail(misc, bad, 31); n = 0; }
     int o = 0;
     if (n) {
@@ -474,7 +541,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   // ---- phase 2: kept legs + new legs per site, merged in time order
   for (int li = tid; li < nds; li += NT) {
     const int s = T.gsite(li);
-    const uint64_t* KO = d.keyA + size_t(s) * d.cap;
+    const uint64_t* KO = T.okeys(li, s);
     const int nO = cnt_n(d.cntA[s]);
     int c = 0;
     const uint8_t* ti = T.tinfo + li * 6;
@@ -490,7 +557,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   if (misc->err) goto fail;
   for (int li = tid; li < nds; li += NT) {
     const int s = T.gsite(li);
-    const uint64_t* KO = d.keyA + size_t(s) * d.cap;
+    const uint64_t* KO = T.okeys(li, s);
     const int nO = cnt_n(d.cntA[s]);
     int lb[4], ci[4] = {0, 0, 0, 0}, cn[4];
     site_bonds(T, li, lb);
@@ -577,7 +644,15 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       // stream (unit = domain * n_sub + u, scatter | pass).
       for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
       __syncthreads();
-      for (int pass = 0; pass < (nw > 0 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
+      if (nw > 0 && nw <= 32) {  // few worms: one warp, no block barrier per pass
+        if (tid < 32) {
+          const int rc = small_passes(T, dom, nw, tid);
+          if (rc && tid == 0) tile_fail(misc, rc, 5);
+        }
+        __syncthreads();
+        if (misc->err) goto fail;
+      }
+      for (int pass = 0; pass < (nw > 32 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         const int q = pass & 3;
         if (tid < 32) rank_pass(T, nw, q, tid);
         __syncthreads();
@@ -761,7 +836,13 @@ __global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
 }
 
 // ---------------------------------------------------------------------------
-bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
+// Shared-memory plan of one domain.  Fixed tables, then the leg table
+// (legcap legs and a worm count each), then a union that holds the Step-3
+// candidate pool and, beside it, the staged current configuration (phases
+// 1-2), later the worm table and the Step-5 arrays.  The configuration is
+// staged only when that costs no CTA per SM (CTAs per SM: the 228 KB of
+// shared memory of an SM over the per-CTA size plus its 1 KB reserve).
+bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const int nds = d->dom_x * d->dom_y;
   const int nsub = sb_slots_host(d->dom_x, d->sub_block, d->ndx) * sb_slots_host(d->dom_y, d->sub_block, d->ndy);
   const int nb = std::max(nsub, nds) + 1;
@@ -778,20 +859,35 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   d->sm_sub = int(o); o = up16(o + size_t(4 * nds) * sizeof(uint16_t));
   d->sm_tinfo = int(o); o = up16(o + size_t(6 * nds));
   const size_t fixed = o;
-  // worm side of the union: table, index, two bucket arrays
-  const size_t worm_bytes = [&](int wcap) {
-    return up16(size_t(wcap) * sizeof(WormRec)) + 4 * up16(size_t(wcap) * 2) + up16(size_t(wcap) * 16) +
-           2 * up16(size_t(nb) * sizeof(int));
-  }(d->wcap);
+  // worm side of the union: table, index, label order, sub-block ids and
+  // ranks, Philox words, two bucket arrays
+  const size_t worm_bytes = up16(size_t(d->wcap) * sizeof(WormRec)) + 4 * up16(size_t(d->wcap) * 2) +
+                            up16(size_t(d->wcap) * 16) + 2 * up16(size_t(nb) * sizeof(int));
   const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
-  const size_t uni = std::max(worm_bytes, pool_bytes);
-  const long long room = (long long)kSmemLimit - 1024 - (long long)fixed - (long long)uni;
+  const long long want = std::min<long long>((long long)legs_want, 65000);
+  const long long limit = (long long)kSmemLimit - 1024;
+  // CTAs per SM: shared memory, registers (about 80 a thread: 3, 6 or 12
+  // CTAs of 256, 128 or 64 threads) and the 32-CTA limit
+  const long long by_regs = nds <= 32 ? 12 : (nds <= 96 ? 6 : 3);
+  auto per_sm = [&](long long bytes) { return std::min(std::min((228LL * 1024) / (bytes + 1024), by_regs), 32LL); };
+  // without staging
+  const long long uni0 = (long long)std::max(worm_bytes, pool_bytes);
+  const long long room = limit - (long long)fixed - uni0;
   if (room < 8 * 64) return false;
-  const long long want = (long long)(1.1 * legs_per_site * nds) + 256;
-  d->legcap = int(std::min<long long>(std::min<long long>(want, room / 9 - 16), 65000));
+  const long long cap0 = std::min<long long>(want, room / 9 - 16);
+  const long long tot0 = (long long)fixed + (long long)up16(size_t(cap0) * 8) + (long long)up16(size_t(cap0)) + uni0;
+  // with staging: room for as many events as legs
+  const long long stage = (long long)up16(size_t(nds + 1) * sizeof(int)) + (long long)up16(size_t(want) * 8);
+  const long long uni1 = std::max((long long)worm_bytes, (long long)pool_bytes + stage);
+  const long long tot1 = (long long)fixed + (long long)up16(size_t(want) * 8) + (long long)up16(size_t(want)) + uni1;
+  const bool staged = cap0 == want && tot1 <= limit && per_sm(tot1) >= per_sm(tot0);
+  d->legcap = int(cap0);
+  d->oldcap = staged ? int(want) : 0;
   d->sm_leg = int(o); o = up16(o + size_t(d->legcap) * sizeof(uint64_t));
   d->sm_wcnt = int(o); o = up16(o + size_t(d->legcap));
   d->sm_pool = int(o);
+  d->sm_soff = int(o + pool_bytes);
+  d->sm_old = int(o + pool_bytes + up16(size_t(nds + 1) * sizeof(int)));
   d->sm_worm = int(o);
   size_t w = o + up16(size_t(d->wcap) * sizeof(WormRec));
   d->sm_idx = int(w); w = up16(w + size_t(d->wcap) * 2);
@@ -801,7 +897,7 @@ bool plan_tile_smem(Dev* d, double legs_per_site, double cands_per_bond) {
   d->sm_rw = int(w); w = up16(w + size_t(d->wcap) * 16);
   d->sm_bkt = int(w); w = up16(w + size_t(nb) * sizeof(int));
   d->sm_fill = int(w); w = up16(w + size_t(nb) * sizeof(int));
-  o = std::max(w, o + pool_bytes);
+  o = std::max(w, o + pool_bytes + (staged ? size_t(stage) : 0));
   d->sm_total = int(o);
   (void)cands_per_bond;
   return d->sm_total <= kSmemLimit - 1024;

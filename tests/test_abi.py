@@ -52,3 +52,18 @@ def test_host_tables_equal_oracle_tables(kw):
     z = O.zig_tables()
     for k in "XFWK":
         assert np.array_equal(a[k], z[k]), k
+
+
+def test_tile_plan_stages_the_configuration_when_it_costs_no_occupancy():
+    """With a measured leg count the 256x256, beta t = 4 domains (16x16
+    sites) hold the staged configuration and still fit two CTAs per SM;
+    with the a-priori bound 4 beta (D + t) the leg table alone is too large
+    for that, and the configuration is read from HBM."""
+    kw = dict(Lx=256, Ly=256, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=31)
+    hinted = P.pmwa_tile_plan(**kw, legs_hint=15)
+    assert hinted["oldcap"] >= hinted["legcap"] > 15 * 256
+    assert (228 * 1024) // (hinted["smem"] + 1024) >= 2
+    bound = P.pmwa_tile_plan(**kw)
+    assert bound["oldcap"] == 0 and bound["legcap"] > hinted["legcap"]
+    with pytest.raises(P.PmwaError):
+        P.pmwa_tile_plan(**kw, legs_hint=-1)

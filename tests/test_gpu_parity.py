@@ -36,7 +36,17 @@ GEOMS = [
     # large V, negative mu, bounce-rich directed loops
     dict(Lx=12, Ly=4, beta=3.0, eta=0.25, V=3.0, mu=-1.5, t=0.7, dom_x=6, dom_y=2,
          sub_block=2, n_cycle=4, seed=13),
+    # many worms and a tight leg-count hint: the domain's configuration
+    # (legs + worms) overflows the shared-memory staging area after the first
+    # sweep, so Steps 3 read it from HBM instead
+    dict(Lx=8, Ly=8, beta=2.0, t=0.5, eta=4.0, n_cycle=4, seed=23, init=1, init_seed=3, legs_hint=5),
+    # more than 32 worms per domain: the block-wide Step-5 passes (the cases
+    # above hold fewer and take the one-warp passes)
+    dict(Lx=16, Ly=16, beta=4.0, eta=0.3, sub_block=2, n_cycle=6, seed=17, init=1, init_seed=5),
+    dict(Lx=32, Ly=32, beta=4.0, eta=0.25, dom_x=16, dom_y=16, sub_block=2, n_cycle=8,
+         exchange_every=2, seed=19, init=1, init_seed=9),
 ]
+MANY_WORMS = GEOMS[-2:]
 
 
 def _pair(kw):
@@ -150,3 +160,27 @@ def test_rows_buffer_full_is_reported():
     assert e.value.status == P.PMWA_EROWS
     assert len(g.rows()) == 4
     g.sweep(1)
+
+
+@pytest.mark.parametrize("kw", MANY_WORMS)
+def test_many_worm_cases_exceed_one_warp(kw):
+    """The last two geometries really hold more than 32 worms per domain
+    (so the block-wide passes are the ones compared above)."""
+    g = P.Sim(**kw)
+    g.sweep(4)
+    r = g.rows()
+    nd = (kw["Lx"] // (kw.get("dom_x") or kw["Lx"])) * (kw["Ly"] // (kw.get("dom_y") or kw["Ly"]))
+    assert r["n_w"][1:].min() / nd > 32, r["n_w"]
+
+
+def test_too_small_leg_hint_is_a_capacity_error():
+    """A leg-count hint far below the real count makes the sweep return
+    PMWA_ECAPACITY (checked in the kernel, no device fault); the device
+    stays usable."""
+    kw = dict(Lx=16, Ly=16, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=4, seed=3, legs_hint=1)
+    g = P.Sim(**kw)
+    with pytest.raises(P.PmwaError) as e:
+        g.sweep(6)
+    assert e.value.status == P.PMWA_ECAPACITY
+    ok = P.Sim(**dict(kw, legs_hint=0))
+    ok.sweep(2)

@@ -65,7 +65,8 @@ typedef struct {
   int32_t  n_cycle;         /* Step-5 passes per sweep, 0..4095                   */
   int32_t  sub_block;       /* Step-5 shifted sub-block edge B (even); 0 = domain */
   int32_t  init;            /* 0: empty lattice; 1: floor(N/2) particles placed by
-                               a Fisher-Yates permutation of stream init_seed     */
+                               a Fisher-Yates permutation of stream init_seed;
+                               2: checkerboard, sites with x + y even occupied    */
   uint64_t init_seed;
   double   c_off;           /* diagonal vertex weight offset; < 0 means t/2       */
   uint32_t replica;         /* 0..65535, mixed into every Philox counter          */

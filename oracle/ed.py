@@ -113,3 +113,41 @@ def single_site(beta, mu, eta):
     n = 0.5 + (mu / (4.0 * D)) * th
     Q = (eta / D) * th
     return dict(n=n, Q=Q, E=-mu * n)
+
+
+def thermal_lowest(Lx, Ly, beta, t, V, mu, eta, k=60):
+    """Thermal averages (E/N of H, <n>, <Q>/N, <b+b + h.c.> per bond) from
+    the k lowest eigenstates of H_eta (sparse Lanczos, scipy's eigsh), for
+    lattices too large for dense diagonalisation at low temperature.  The
+    Boltzmann weight of the highest state kept is returned as p_last; the
+    truncation is valid when it is negligible (e.g. < 1e-30)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    N = Lx * Ly
+    dim, states, occ = _ops(N)
+    diag = np.zeros(dim)
+    rows, cols, vals = [], [], []
+    for a, c in bonds(Lx, Ly):
+        diag += V * occ[a] * occ[c] - (mu / 4.0) * (occ[a] + occ[c])
+        m = (occ[a] == 1) & (occ[c] == 0)
+        src = states[m]
+        dst = src ^ (1 << a) ^ (1 << c)
+        rows += [dst, src]
+        cols += [src, dst]
+        vals += [np.full(len(src), -t)] * 2
+    Hk = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(dim, dim))
+    H = Hk + sp.diags(diag)
+    Q = sp.csr_matrix((np.ones(N * dim), (np.concatenate([states ^ (1 << i) for i in range(N)]),
+                                           np.tile(states, N))), shape=(dim, dim))
+    nop = sp.diags(np.sum(occ, axis=0))
+    w, U = sla.eigsh(H - eta * Q, k=k, which="SA", tol=1e-12)
+    order = np.argsort(w)
+    w, U = w[order], U[:, order]
+    p = np.exp(-beta * (w - w[0]))
+    Z = p.sum()
+
+    def avg(A):
+        return float(p @ np.einsum("ik,ik->k", U, A @ U) / Z)
+
+    return dict(E=avg(H) / N, n=avg(nop) / N, Q=avg(Q) / N,
+                kin=avg(-Hk) / (t * 2 * N) if t > 0 else 0.0, p_last=float(p[-1] / Z))

@@ -1007,7 +1007,7 @@ static int validate(const or_params* p) {
   if (B < 0 || (B && (B & 1))) return OR_EINVAL;
   if (B && B < p->dom_x && p->dom_x % B) return OR_EINVAL;
   if (B && B < p->dom_y && p->dom_y % B) return OR_EINVAL;
-  if (p->replica >= 65536) return OR_EINVAL;
+  if (p->replica >= 65536 || p->init < 0 || p->init > 2) return OR_EINVAL;
   /* the grid scales 2^59/(beta eta) and 2^59/(beta D) must lie in [2^39, 2^99] */
   if (!(p->beta * p->eta >= 0x1p-40 && p->beta * p->eta <= 0x1p20)) return OR_EINVAL;
   {
@@ -1041,6 +1041,9 @@ int or_create(const or_params* p, or_handle** out) {
     }
     for (int k = 0; k < h->N / 2; k++) h->site[perm[k]].base = 1;
     free(perm);
+  } else if (p->init == 2) {
+    /* the checkerboard: site (x, y) occupied iff x + y is even */
+    for (int s = 0; s < h->N; s++) h->site[s].base = ((sx(h, s) + sy(h, s)) & 1) == 0;
   }
   *out = h;
   return OR_OK;

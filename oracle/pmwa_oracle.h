@@ -39,7 +39,8 @@ typedef struct {
   int32_t  exchange_every;  /* K: Step 2 when sweep % K == 0                  */
   int32_t  n_cycle;         /* Step-5 passes per sweep                        */
   int32_t  sub_block;       /* shifted sub-block edge B (even), 0 = domain    */
-  int32_t  init;            /* 0: empty lattice, 1: random half filling       */
+  int32_t  init;            /* 0: empty lattice, 1: random half filling,
+                               2: checkerboard (x + y even occupied)           */
   uint64_t init_seed;
   double   c_off;           /* vertex-density offset; < 0 means t/2           */
   uint32_t replica;         /* replica id mixed into every Philox counter     */

@@ -67,7 +67,7 @@ int validate(const pmwa_params* p) {
   if (B < 0 || (B & 1)) return PMWA_EINVAL;
   if (B && B < dx && dx % B) return PMWA_EINVAL;
   if (B && B < dy && dy % B) return PMWA_EINVAL;
-  if (p->replica >= 65536u || p->init < 0 || p->init > 1) return PMWA_EINVAL;
+  if (p->replica >= 65536u || p->init < 0 || p->init > 2) return PMWA_EINVAL;
   if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
   if (p->legs_hint < 0 || p->legs_hint > (1 << 20)) return PMWA_EINVAL;
   for (int k = 0; k < 4; ++k) if (p->reserved[k]) return PMWA_EINVAL;
@@ -451,6 +451,8 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
       std::swap(perm[size_t(k)], perm[size_t(j)]);
     }
     for (int k = 0; k < g.N / 2; ++k) cnt[size_t(perm[size_t(k)])] = 1u << 31;
+  } else if (p->init == 2) {  // checkerboard: (x + y) even occupied
+    for (int s = 0; s < g.N; ++s) cnt[size_t(s)] = (((s % p->Lx) + (s / p->Lx)) & 1) ? 0u : (1u << 31);
   }
   DevErr z{0, 0};
   if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||

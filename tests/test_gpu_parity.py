@@ -30,6 +30,9 @@ GEOMS = [
     # 16x16 in 8x8 domains (config-2 shape, smaller), K = 2
     dict(Lx=16, Ly=16, beta=4.0, eta=0.1, dom_x=8, dom_y=8, sub_block=4, n_cycle=8,
          exchange_every=2, seed=7, init=1, init_seed=7),
+    # checkerboard start, large V and mu (the checkerboard-solid regime), domains
+    dict(Lx=8, Ly=8, beta=2.0, eta=0.2, V=3.0, mu=4.2, dom_x=4, dom_y=4, sub_block=2, n_cycle=4,
+         seed=29, init=2),
     # odd sizes, non-square domains, t = 0 and a long circle
     dict(Lx=6, Ly=9, beta=4.0, eta=0.15, t=0.0, c_off=0.3, mu=0.8, dom_x=3, dom_y=3,
          n_cycle=3, seed=11),

@@ -234,3 +234,16 @@ def test_half_filled_initial_state():
     hdr = buf[1:]
     assert np.all((hdr & np.uint64(0x7FFFFFFF)) == 0)
     assert int((hdr >> np.uint64(63)).sum()) == 24
+
+
+def test_checkerboard_initial_state():
+    """init = 2: the checkerboard, site (x, y) occupied iff x + y is even,
+    with no events, a valid configuration."""
+    Lx, Ly = 6, 4
+    o = O.Oracle(Lx=Lx, Ly=Ly, init=2, beta=2.0, t=0.0, V=3.0, mu=4.2, eta=0.05, c_off=0.5, n_cycle=2)
+    hdr = o.export()[1:]
+    assert np.all((hdr & np.uint64(0x7FFFFFFF)) == 0)
+    occ = (hdr >> np.uint64(63)).astype(int).reshape(Ly, Lx)
+    want = ((np.arange(Lx)[None, :] + np.arange(Ly)[:, None]) % 2 == 0).astype(int)
+    assert np.array_equal(occ, want)
+    assert o.check() == 0

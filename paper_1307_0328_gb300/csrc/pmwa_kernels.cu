@@ -71,7 +71,7 @@ struct Legs {
 
 // the two legs of the vertex at pv on a site: to the next vertex leg below
 // and above, worms ignored; one interval round the circle if v is alone.
-__device__ bool site_legs(const uint64_t* K, int n, uint64_t pv, Legs* L) {
+__device__ __noinline__ bool site_legs(const uint64_t* K, int n, uint64_t pv, Legs* L) {
   const int iv = slot_find(K, n, pv);
   if (iv < 0) return false;
   int jn = iv, jp = iv;
@@ -138,7 +138,7 @@ __device__ __forceinline__ int warp_find_tag(const uint64_t* K, int n, int from,
 // erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
 // and draw new ones with end states p (above lo) and q (below hi); K holds
 // n events (capacity cap).
-__device__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_t* K, int& n,
+__device__ __noinline__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_t* K, int& n,
                               uint64_t lo, uint64_t hi, int p, int q) {
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
   n = warp_compact(K, n, [&](uint64_t key) {  // the worms of the interval

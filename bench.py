@@ -10,7 +10,7 @@ ceil(2 <n_v> / <n_w>) from a pilot run).  Inputs are synthetic: the lattice
 parameters are the whole input.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config2|config4|config1]
+                  [--workload 256x256_bt4|2048x2048_bt16|8x8_bt2]
 
 Prints one JSON line.  `value` = vertices summed over the timed sweeps / the
 device time of those sweeps (CUDA events recorded by the library on its
@@ -33,21 +33,21 @@ METRIC = "vertex updates/s per GB300 (hard-core BH), batched vs plain; % of HBM 
 UNIT = "vertex updates/s"
 
 WORKLOADS = {
-    "config2": dict(Lx=256, Ly=256, beta=4.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
+    "256x256_bt4": dict(Lx=256, Ly=256, beta=4.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
                     exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
-    "config4": dict(Lx=2048, Ly=2048, beta=16.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
+    "2048x2048_bt16": dict(Lx=2048, Ly=2048, beta=16.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
                     exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
-    "config1": dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, dom_x=8, dom_y=8,
+    "8x8_bt2": dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, dom_x=8, dom_y=8,
                     exchange_every=2, sub_block=0, init=1, init_seed=1, seed=1),
 }
 DESCR = {
-    "config2": "256x256 periodic hcBH, t=1 V=0 mu=0 beta*t=4 eta=0.1, 16x16-site domains, K=2",
-    "config4": "2048x2048 periodic hcBH, t=1 V=0 mu=0 beta*t=16 eta=0.1, 128x128 domains of 16x16 sites, K=2",
-    "config1": "8x8 periodic hcBH, t=1 V=0 mu=0 beta*t=2 eta=0.2, one domain",
+    "256x256_bt4": "256x256 periodic hcBH, t=1 V=0 mu=0 beta*t=4 eta=0.1, 16x16-site domains, K=2",
+    "2048x2048_bt16": "2048x2048 periodic hcBH, t=1 V=0 mu=0 beta*t=16 eta=0.1, 128x128 domains of 16x16 sites, K=2",
+    "8x8_bt2": "8x8 periodic hcBH, t=1 V=0 mu=0 beta*t=2 eta=0.2, one domain",
 }
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TILE_PROFILE = os.path.join(ROOT, "profiles", "k_tile_config2.md")
+TILE_PROFILE = os.path.join(ROOT, "profiles", "k_tile_256x256_bt4.md")
 TILE_SOURCES = ["pmwa_tile.cu", "pmwa_device.cuh", "pmwa_internal.h"]
 
 
@@ -280,7 +280,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="256x256_bt4", choices=sorted(WORKLOADS))
     ap.add_argument("--pilot", type=int, default=200, help="thermalisation sweeps of the N_cycle pilot")
     ap.add_argument("--n-cycle", type=int, default=0, help="fix N_cycle instead of the pilot rule")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

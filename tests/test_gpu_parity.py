@@ -20,14 +20,14 @@ import paper_1307_0328_gb300 as P  # noqa: E402
 REL = 1e-12
 
 GEOMS = [
-    # config-1 parameters on the 8x8 lattice, one domain
+    # the 8x8, beta t = 2, eta = 0.2 workload, one domain
     dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=6, seed=1, init=1, init_seed=1),
     # 2x2 lattice (every pair carries two bonds), empty start
     dict(Lx=2, Ly=2, beta=1.5, eta=0.5, n_cycle=4, seed=3, init=0),
     # domains + sub-blocks, non-zero V and mu
     dict(Lx=8, Ly=8, beta=2.0, eta=0.3, V=1.0, mu=0.7, dom_x=4, dom_y=4, sub_block=2,
          n_cycle=5, exchange_every=1, seed=5),
-    # 16x16 in 8x8 domains (config-2 shape, smaller), K = 2
+    # 16x16 in 8x8 domains (the 256x256 workload in small), K = 2
     dict(Lx=16, Ly=16, beta=4.0, eta=0.1, dom_x=8, dom_y=8, sub_block=4, n_cycle=8,
          exchange_every=2, seed=7, init=1, init_seed=7),
     # checkerboard start, large V and mu (the checkerboard-solid regime), domains
@@ -134,7 +134,7 @@ def test_green_functions_match_oracle_densities():
     assert pl == pytest.approx(p4 / eta ** 4, rel=1e-12)
 
 
-def test_many_sweeps_config1_shape():
+def test_many_sweeps_8x8_one_domain():
     """Config-1 shape over 200 sweeps: configuration identical at the end."""
     kw = dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=8, seed=1, init=1, init_seed=1)
     g, o = _pair(kw)

@@ -67,7 +67,7 @@ def _mean_err(v):
 
 
 ED_CASES = [
-    # (Lx, Ly, model, geometry) -- the config-1 parameters first
+    # (Lx, Ly, model, geometry) -- beta t = 2, eta = 0.2 first
     (3, 3, dict(beta=2.0, eta=0.2), dict()),
     (2, 2, dict(beta=2.0, eta=0.2), dict()),
     (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=1.0), dict()),

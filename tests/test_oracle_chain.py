@@ -53,8 +53,8 @@ def _agree(ob, ex, keys=("E", "n", "Q_raw", "Q_impr", "kin")):
 
 CASES = [
     # (Lx, Ly, model, geometry, sweeps) -- model dicts use t, V, mu, beta, eta
-    (2, 2, dict(beta=2.0, eta=0.2), dict(), 200_000),                       # config-1 parameters
-    (3, 3, dict(beta=2.0, eta=0.2), dict(), 120_000),                       # config-1 parameters
+    (2, 2, dict(beta=2.0, eta=0.2), dict(), 200_000),                       # beta t = 2, eta = 0.2
+    (3, 3, dict(beta=2.0, eta=0.2), dict(), 120_000),                       # beta t = 2, eta = 0.2
     (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=1.0), dict(), 120_000),
     (3, 3, dict(beta=2.0, eta=0.2, V=1.0, mu=-1.0), dict(), 120_000),
     (3, 3, dict(beta=0.25, eta=1.0), dict(), 240_000),                      # beta t = 1/4

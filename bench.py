@@ -109,6 +109,22 @@ def ncycle_rule(n_v, n_w):
     return max(1, min(512, int(math.ceil(2.0 * n_v / max(n_w, 1.0)))))
 
 
+# --------------------------------------------------------------------------- ranks
+def over_ranks(t_local, units_local, world, device):
+    """Whole-job time and units over the ranks of a replicas-only run (one
+    independent replica per GPU, weak scaling): the slowest rank's time and
+    the units summed over all ranks.  With one rank, the local values."""
+    if world <= 1:
+        return float(t_local), float(units_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local, units_local], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -377,14 +393,7 @@ def main():
     nv = float(rows["n_v"].sum())
     nw = float(rows["n_w"].mean())
     t_local = span_ms / 1000.0
-    if world > 1:
-        t = torch.tensor([t_local, nv], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        t_job, nv_job = float(tmax[0]), float(t[1])
-    else:
-        t_job, nv_job = t_local, nv
+    t_job, nv_job = over_ranks(t_local, nv, world, dev)
     value = nv_job / t_job
 
     # e2e through the public API: sweep + read the step's measurement row
@@ -397,14 +406,8 @@ def main():
         nv_e2e += float(r["n_v"].sum())
     e_t = time.perf_counter() - e0
     e2e_local = nv_e2e / e_t
-    if world > 1:
-        t = torch.tensor([e_t, nv_e2e], device=dev, dtype=torch.float64)
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_val = float(t[1]) / float(tm[0])
-    else:
-        e2e_val = e2e_local
+    e_job, nv_e2e_job = over_ranks(e_t, nv_e2e, world, dev)
+    e2e_val = nv_e2e_job / e_job
 
     if rank == 0:
         kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}

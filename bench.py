@@ -202,10 +202,10 @@ def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
 def oracle_pilot_n_cycle(wl, pilot):
     """The same N_cycle rule as the GPU arm, from a pilot run of the oracle:
     N_cycle = ceil(2 <n_v> / <n_w>) over the second half of the pilot
-    sweeps (at most 60) at 16 passes."""
+    sweeps (at most 200, as many as the GPU arm's default) at 16 passes."""
     from oracle import oracle as O
     o = O.Oracle(n_cycle=16, **WORKLOADS[wl])
-    o.sweep(max(2, min(pilot, 60)))  # a bounded CPU sample
+    o.sweep(max(2, min(pilot, 200)))  # a bounded CPU sample (about 80 s at 256x256)
     r = o.rows()
     half = r[len(r) // 2:]
     return ncycle_rule(float(half["n_v"].mean()), float(half["n_w"].mean()))

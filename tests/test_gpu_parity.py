@@ -187,3 +187,24 @@ def test_too_small_leg_hint_is_a_capacity_error():
     assert e.value.status == P.PMWA_ECAPACITY
     ok = P.Sim(**dict(kw, legs_hint=0))
     ok.sweep(2)
+
+
+@pytest.mark.parametrize("legs_hint", [0, 18])
+def test_full_size_256x256_bit_exact(legs_hint):
+    """The 256x256, beta t = 4, eta = 0.1 workload at full size in the launch
+    configuration the benchmark times (16x16-site domains, 2x2 sub-blocks,
+    boundary step every 2 sweeps, N_cycle 31; with the a-priori leg table
+    and with a leg-count hint): 12 sweeps from the seeded half-filled start
+    on both sides, configuration and counters equal bit for bit after every
+    third sweep."""
+    kw = dict(Lx=256, Ly=256, beta=4.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2,
+              exchange_every=2, n_cycle=31, init=1, init_seed=7, seed=7, legs_hint=legs_hint)
+    g, o = _pair(kw)
+    for _ in range(4):
+        g.sweep(3)
+        o.sweep(3)
+        _same(g.export(), o.export(), "configuration")
+        a, b = g.rows(), o.rows()
+        for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+            assert np.array_equal(a[f], b[f]), f
+        assert np.allclose(a["q_impr"], b["q_impr"], rtol=REL, atol=0)

@@ -696,7 +696,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       for (int w = tid; w < nw; w += NT) T.idx[atomicAdd(&T.fill[T.W[w].site], 1)] = uint16_t(w);
       __syncthreads();
     }
-    uint64_t nv = 0, nk = 0, nwc = 0, olo = 0, ohi = 0;
+    uint64_t nv = 0, nk = 0, nwc = 0, olo = 0, ohi = 0, qlo = 0, qhi = 0;
     double q = 0.0;
     for (int li = tid; li < nds; li += NT) {
       const int s = T.gsite(li);
@@ -740,41 +740,51 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       else base = (stop >= 4) ? T.base[li] : cnt_base(d.cntA[s]);
       d.cntB[s] = uint32_t(no) | (uint32_t(base) << 31);
       if (stop < 6) continue;
-      // Step 6 counters of this site
-      if (no == 0 && base) olo += kTwo62;
+      // Step 6, per site: occupied time (at most 2^62 a site, summed in 128
+      // bits), worms; a site without legs is one interval of sigma = 0
+      uint64_t occ = (no == 0 && base) ? kTwo62 : 0;
       for (int k = 0; k < no; ++k) {
         const uint64_t key = OUT[k];
         const uint64_t nx = kpk(OUT[k + 1 == no ? 0 : k + 1]);
         const uint64_t len = (no == 1) ? kTwo62 : ((nx - kpk(key)) & kMask62);
-        if (kab(key)) olo += len;
+        if (kab(key)) occ += len;
       }
+      add128(olo, ohi, occ, 0);
       nwc += uint64_t(no - nl);
-      for (int k = 0; k < nl; ++k) {
-        const uint64_t key = T.leg[st + k];
-        if (T.tinfo[li * 6 + ktag(key)] & 1) { ++nv; if (kab(key) != kbl(key)) ++nk; }
+      if (nl == 0) {
+        uint64_t v;
+        if (xg_fix(0, kTwo59, d.XQ, v)) add128(qlo, qhi, v, 0);
+        else q += xg_sigma(0, double(kTwo59) * d.XW);
       }
-      {
-        // improved <Q>: sum of x g_sigma(x) over the site's intervals, in
-        // fixed point (exact sum) where x < 1/2, else in binary64
-        uint64_t qlo = 0, qhi = 0;
-        double qs = 0.0;
-        for (int k = 0; k < (nl ? nl : 1); ++k) {
-          uint64_t I;
-          int sg;
-          if (nl == 0) {
-            I = kTwo59;
-            sg = 0;
-          } else {
-            const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
-            I = wpts(kpk(lo), kpk(hi));
-            sg = kab(lo) ^ kbl(hi);
-          }
+    }
+    if (stop >= 6) {
+      // Step 6, per interval (legs split evenly over the threads): vertex
+      // and kink counts, and the improved <Q> sum of x g_sigma(x), in fixed
+      // point (exact sum) where x < 1/2, else in binary64
+      const int total = T.off[nds];
+      const int chunk = (total + NT - 1) / NT;
+      int j = tid * chunk;
+      const int jend = min(total, j + chunk);
+      if (j < jend) {
+        int a = 0, b = nds;  // the site of leg j: off[a] <= j < off[a + 1]
+        while (a + 1 < b) {
+          const int m = (a + b) >> 1;
+          if (T.off[m] <= j) a = m; else b = m;
+        }
+        int li = a;
+        for (; j < jend; ++j) {
+          while (T.off[li + 1] <= j) ++li;
+          const uint64_t lo = T.leg[j];
+          const uint64_t hi = T.leg[(j + 1 == T.off[li + 1]) ? T.off[li] : j + 1];
+          if (T.tinfo[li * 6 + ktag(lo)] & 1) { ++nv; if (kab(lo) != kbl(lo)) ++nk; }
+          const uint64_t I = wpts(kpk(lo), kpk(hi));
+          const int sg = kab(lo) ^ kbl(hi);
           uint64_t v;
           if (xg_fix(sg, I, d.XQ, v)) add128(qlo, qhi, v, 0);
-          else qs += xg_sigma(sg, __ull2double_rn(I) * d.XW);
+          else q += xg_sigma(sg, __ull2double_rn(I) * d.XW);
         }
-        q += qs + (__ull2double_rn(qhi) * 4.0 + __ull2double_rn(qlo) * 0x1p-62);
       }
+      q += __ull2double_rn(qhi) * 4.0 + __ull2double_rn(qlo) * 0x1p-62;
     }
     if (stop >= 6) {
       for (int o = 16; o > 0; o >>= 1) {

@@ -43,6 +43,10 @@ GEOMS = [
     # (legs + worms) overflows the shared-memory staging area after the first
     # sweep, so Steps 3 read it from HBM instead
     dict(Lx=8, Ly=8, beta=2.0, t=0.5, eta=4.0, n_cycle=4, seed=23, init=1, init_seed=3, legs_hint=5),
+    # one 32x32 domain (four sites a thread) at high density: many sites are
+    # occupied all the time, so a thread's occupied time exceeds 2^64 grid
+    # units and needs its 128-bit sum
+    dict(Lx=32, Ly=32, beta=0.25, eta=0.1, mu=8.0, n_cycle=3, seed=41, init=1, init_seed=2),
     # more than 32 worms per domain: the block-wide Step-5 passes (the cases
     # above hold fewer and take the one-warp passes)
     dict(Lx=16, Ly=16, beta=4.0, eta=0.3, sub_block=2, n_cycle=6, seed=17, init=1, init_seed=5),

@@ -46,6 +46,8 @@ struct Dev {
   int sm_th, sm_zig, sm_off, sm_base, sm_bcnt, sm_boff, sm_misc, sm_nbr, sm_sub, sm_tinfo, sm_leg, sm_wcnt, sm_pool,
       sm_worm, sm_idx, sm_ord, sm_wsb, sm_wrk, sm_rw, sm_bkt, sm_fill, sm_total;
   int sm_soff, sm_old;  // staged current configuration of the domain (phases 1-2)
+  int sm_part;          // [legcap] u16: index of each vertex leg's partner leg (Step 5)
+  int use_part;         // 1: the partner table is planned; 0: Step 5 searches for partners
   int oldcap;           // events it can hold; 0 = read the configuration from HBM
   unsigned long long* phase_cycles;  // 8 counters when profiling, else null
   // random numbers

@@ -99,6 +99,7 @@ struct Tile {
   Misc* misc;
   uint64_t* leg;   // [legcap]
   uint8_t* wcnt;   // [legcap] worms in the interval just above each leg
+  uint16_t* part;  // [legcap] index of the partner leg of each leg's vertex (kNone: none in the domain)
   uint64_t* pool;  // [poolcap] (aliases the worm table)
   WormRec* W;      // [wcap]
   uint16_t* idx;   // [wcap] worms grouped by sub-block (a pass) or by site (output)
@@ -240,7 +241,7 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   const int pl = nb >> 1;
   const bool li_a = nb & 1;                            // li is the bond's lower site
   if (T.sub[li * 4 + q] != T.sub[pl * 4 + q]) { w.key = key ^ 2u; return PMWA_OK; }
-  const int ip = leg_index(T, pl, pv);
+  const int ip = T.d->use_part ? (T.part[iv] == kNone ? -1 : int(T.part[iv])) : leg_index(T, pl, pv);
   if (ip < 0) return PMWA_EINVARIANT;
   const int al = li_a ? li : pl, bl = li_a ? pl : li;
   const int ia = li_a ? iv : ip, ib = li_a ? ip : iv;
@@ -452,6 +453,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.misc = reinterpret_cast<Misc*>(sm + d.sm_misc);
   T.leg = reinterpret_cast<uint64_t*>(sm + d.sm_leg);
   T.wcnt = reinterpret_cast<uint8_t*>(sm + d.sm_wcnt);
+  T.part = reinterpret_cast<uint16_t*>(sm + d.sm_part);
   T.pool = reinterpret_cast<uint64_t*>(sm + d.sm_pool);
   T.W = reinterpret_cast<WormRec*>(sm + d.sm_worm);
   T.idx = reinterpret_cast<uint16_t*>(sm + d.sm_idx);
@@ -585,6 +587,37 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     }
   }
   __syncthreads();
+  if (stop >= 5 && d.use_part) {
+    // the partner leg of every vertex leg whose bond lies in the domain: the
+    // leg with the same time on the bond's other site (legs keep their
+    // places through Step 5; only their states change)
+    // (legs split evenly over the threads; each vertex once, from its lower site)
+    const int total = T.off[nds];
+    for (int j = tid; j < total; j += NT) T.part[j] = kNone;
+    __syncthreads();
+    const int chunk = (total + NT - 1) / NT;
+    int j = tid * chunk;
+    const int jend = min(total, j + chunk);
+    if (j < jend) {
+      int a = 0, b = nds;  // the site of leg j: off[a] <= j < off[a + 1]
+      while (a + 1 < b) {
+        const int m = (a + b) >> 1;
+        if (T.off[m] <= j) a = m; else b = m;
+      }
+      int li = a;
+      for (; j < jend; ++j) {
+        while (T.off[li + 1] <= j) ++li;
+        const uint64_t key = T.leg[j];
+        const int nb = T.nbr[li * 6 + ktag(key)];
+        if (nb < 0 || (nb & 1) == 0) continue;
+        const int ip = leg_index(T, nb >> 1, kpk(key));
+        if (ip < 0) { tile_fail(misc, PMWA_EINVARIANT, 34); continue; }
+        T.part[j] = uint16_t(ip);
+        T.part[ip] = uint16_t(j);
+      }
+    }
+    __syncthreads();
+  }
   phase_tick(d, 1, tclk);
 
   if (stop >= 4) {
@@ -884,17 +917,29 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const long long uni0 = (long long)std::max(worm_bytes, pool_bytes);
   const long long room = limit - (long long)fixed - uni0;
   if (room < 8 * 64) return false;
-  const long long cap0 = std::min<long long>(want, room / 9 - 16);
-  const long long tot0 = (long long)fixed + (long long)up16(size_t(cap0) * 8) + (long long)up16(size_t(cap0)) + uni0;
+  // legs, their worm counts and (optionally) their partner indices
+  auto legs_bytes = [&](long long c, bool part) {
+    return (long long)up16(size_t(c) * 8) + (long long)up16(size_t(c)) + (part ? (long long)up16(size_t(c) * 2) : 0);
+  };
+  const long long capn = std::min<long long>(want, room / 9 - 16);
+  const long long totn = (long long)fixed + legs_bytes(capn, false) + uni0;
+  const long long capp = std::min<long long>(want, room / 11 - 16);
+  const long long totp = (long long)fixed + legs_bytes(capp, true) + uni0;
+  // the partner table only when it shrinks neither the leg table nor occupancy
+  const bool part = capp == capn && per_sm(totp) >= per_sm(totn);
+  const long long cap0 = part ? capp : capn;
+  const long long tot0 = part ? totp : totn;
   // with staging: room for as many events as legs
   const long long stage = (long long)up16(size_t(nds + 1) * sizeof(int)) + (long long)up16(size_t(want) * 8);
   const long long uni1 = std::max((long long)worm_bytes, (long long)pool_bytes + stage);
-  const long long tot1 = (long long)fixed + (long long)up16(size_t(want) * 8) + (long long)up16(size_t(want)) + uni1;
+  const long long tot1 = (long long)fixed + legs_bytes(want, part) + uni1;
   const bool staged = cap0 == want && tot1 <= limit && per_sm(tot1) >= per_sm(tot0);
   d->legcap = int(cap0);
   d->oldcap = staged ? int(want) : 0;
   d->sm_leg = int(o); o = up16(o + size_t(d->legcap) * sizeof(uint64_t));
   d->sm_wcnt = int(o); o = up16(o + size_t(d->legcap));
+  d->use_part = part ? 1 : 0;
+  d->sm_part = int(o); if (part) o = up16(o + size_t(d->legcap) * 2);
   d->sm_pool = int(o);
   d->sm_soff = int(o + pool_bytes);
   d->sm_old = int(o + pool_bytes + up16(size_t(nds + 1) * sizeof(int)));

@@ -54,16 +54,17 @@ def test_host_tables_equal_oracle_tables(kw):
         assert np.array_equal(a[k], z[k]), k
 
 
-def test_tile_plan_stages_the_configuration_when_it_costs_no_occupancy():
-    """With a measured leg count the 256x256, beta t = 4 domains (16x16
-    sites) hold the staged configuration and still fit two CTAs per SM;
-    with the a-priori bound 4 beta (D + t) the leg table alone is too large
-    for that, and the configuration is read from HBM."""
+def test_tile_plan_sizes_from_the_hint_and_keeps_occupancy():
+    """A measured leg count (legs_hint) sizes the leg table of the 256x256,
+    beta t = 4 domains (16x16 sites) below the a-priori bound 4 beta (D + t)
+    and keeps two CTAs per SM; small domains with room to spare also stage
+    their configuration in shared memory; a negative hint is rejected."""
     kw = dict(Lx=256, Ly=256, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=31)
     hinted = P.pmwa_tile_plan(**kw, legs_hint=15)
-    assert hinted["oldcap"] >= hinted["legcap"] > 15 * 256
-    assert (228 * 1024) // (hinted["smem"] + 1024) >= 2
     bound = P.pmwa_tile_plan(**kw)
-    assert bound["oldcap"] == 0 and bound["legcap"] > hinted["legcap"]
+    assert 15 * 256 < hinted["legcap"] < bound["legcap"]
+    assert (228 * 1024) // (hinted["smem"] + 1024) >= 2
+    small = P.pmwa_tile_plan(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=6, legs_hint=12)
+    assert small["oldcap"] >= small["legcap"] > 12 * 64
     with pytest.raises(P.PmwaError):
         P.pmwa_tile_plan(**kw, legs_hint=-1)

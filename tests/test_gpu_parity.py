@@ -43,6 +43,9 @@ GEOMS = [
     # (legs + worms) overflows the shared-memory staging area after the first
     # sweep, so Steps 3 read it from HBM instead
     dict(Lx=8, Ly=8, beta=2.0, t=0.5, eta=4.0, n_cycle=4, seed=23, init=1, init_seed=3, legs_hint=5),
+    # beta t = 16 on one 16x16 domain: the leg table fills shared memory, so
+    # the plan leaves out the partner table and Step 5 searches for partners
+    dict(Lx=16, Ly=16, beta=16.0, eta=0.1, sub_block=2, n_cycle=8, seed=47, init=1, init_seed=4),
     # one 32x32 domain (four sites a thread) at high density: many sites are
     # occupied all the time, so a thread's occupied time exceeds 2^64 grid
     # units and needs its 128-bit sum

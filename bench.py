@@ -227,26 +227,53 @@ def run_reference(args, wl, n_cycle):
 
 
 # --------------------------------------------------------------------------- batched leg
-def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=12):
-    """The 512-replica workload (L in {16..64}, beta t in {1..16}, mu in
-    [-2, 2], V in {0, 1}, eta in {0.05, 0.1, 0.2}; autotuned domains) swept
-    (a) batched: one launch per kernel per sweep, replayed from a CUDA graph,
-    and (b) plain: the same instances one after another, each with its own
-    launches.  Vertex updates/s from device time (CUDA events)."""
-    from paper_1307_0328_gb300 import autotune as A
-    reps = A.replica_set(n_reps)
+def _rebuild(P, reps, snaps):
     batch = P.Batch(reps)
+    for i, (snap, sw) in enumerate(snaps):
+        P.pmwa_import(batch.handles[i], snap)
+        P.pmwa_set_sweep(batch.handles[i], sw)
+    return batch
+
+
+def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
+    """The 512-replica workload (L in {16..64}, beta t in {1..16}, mu in
+    [-2, 2], V in {0, 1}, eta in {0.05, 0.1, 0.2}) swept (a) batched: one
+    launch per kernel per sweep, replayed from a CUDA graph, and (b) plain:
+    the same instances one after another, each with its own launches.
+    Vertex updates/s from device time (CUDA events).  A pilot sets each
+    instance's N_cycle and leg-count hint, and the tuner picks its domains
+    again with the hint; if a hint turns out too small (PMWA_ECAPACITY) the
+    batch falls back to the a-priori plans, from the same configurations."""
+    from paper_1307_0328_gb300 import autotune as A
+    reps0 = A.replica_set(n_reps)
+    batch = P.Batch(reps0)
     batch.sweep(pilot)
-    ncs = []
+    ncs, reps, snaps = [], [], []
     for i in range(batch.n):
         r = batch.rows(i)
         half = r[len(r) // 2:]
         nc = A.n_cycle_rule(half["n_v"].mean(), half["n_w"].mean())
         ncs.append(nc)
-        batch.set_n_cycle(i, nc)
+        p = dict(reps0[i], n_cycle=nc, legs_hint=legs_hint(r[3 * len(r) // 4:]["n_v"].max(), reps0[i], slack=1.3))
+        p.update(A.tune(p))
+        reps.append(p)
+        snaps.append((batch.export(i), P.pmwa_get_sweep(batch.handles[i])))
+    batch.close()
     G = graph_sweeps or steps
-    batch.graph(G)
-    batch.sweep(G * max(1, -(-warmup // G)))
+    hinted = True
+    batch = _rebuild(P, reps, snaps)
+    try:
+        batch.graph(G)
+        batch.sweep(G * max(1, -(-warmup // G)))
+    except P.PmwaError as e:
+        if e.status != P.PMWA_ECAPACITY:
+            raise
+        batch.close()
+        hinted = False
+        reps = [dict(reps0[i], n_cycle=ncs[i]) for i in range(len(reps0))]
+        batch = _rebuild(P, reps, snaps)
+        batch.graph(G)
+        batch.sweep(G * max(1, -(-warmup // G)))
     for i in range(batch.n):
         batch.rows(i)
     batch.sweep(steps)
@@ -268,7 +295,8 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=12):
                value=nv_b / (ms_b / 1000.0), unit=UNIT, ms_per_step=ms_b / steps, graph_sweeps=G,
                plain_value=nv_p / (ms_p / 1000.0), plain_ms_per_step=ms_p / steps,
                speedup=(nv_b / ms_b) / (nv_p / ms_p), vertices_per_sweep=nv_b / steps,
-               n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=batch.arena.numel() / 1e9)
+               n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=batch.arena.numel() / 1e9,
+               leg_hints=hinted, mean_domain_sites=sum(p["dom_x"] * p["dom_y"] for p in reps) / len(reps))
     batch.close()
     return out
 

@@ -3,8 +3,9 @@
 The tuner picks, per instance, the domain edge and the Step-5 sub-block edge:
 the largest square domain that divides L and whose shared-memory plan
 (pmwa_tile_smem) fits two CTAs per SM, at least 4 sites wide when the lattice
-allows it, with 2x2 shifted sub-blocks.  Results are cached per
-(L, beta, t, V, mu, eta, c_off) class.  N_cycle follows the rule "every
+allows it, with 2x2 shifted sub-blocks; a measured leg count (legs_hint)
+shrinks the plan and can admit larger domains.  Results are cached per
+(L, beta, t, V, mu, eta, c_off, legs_hint) class.  N_cycle follows the rule "every
 vertex leg reached once per sweep on average", N_cycle = ceil(2 <n_v> / <n_w>),
 from a short pilot of the instance itself, capped at 512.
 """
@@ -26,7 +27,7 @@ def tune(p):
     """dom_x, dom_y, sub_block for one parameter dict (square lattices)."""
     key = tuple(round(float(p.get(k, d)), 9) for k, d in
                 [("Lx", 8), ("Ly", 8), ("beta", 2.0), ("t", 1.0), ("V", 0.0), ("mu", 0.0), ("eta", 0.2),
-                 ("c_off", -1.0)])
+                 ("c_off", -1.0), ("legs_hint", 0)])
     if key in _cache:
         return dict(_cache[key])
     Lx, Ly = int(p["Lx"]), int(p["Ly"])

@@ -53,6 +53,14 @@ extern "C" {
 #define PMWA_EINVARIANT  5  /* the configuration breaks an invariant              */
 #define PMWA_EROWS       6  /* measurement row buffer full: call pmwa_measure     */
 
+/* When a kernel reports PMWA_ECAPACITY, PMWA_ETIMEOUT or PMWA_EINVARIANT, it
+   has stopped part-way and the handle's configuration is undefined: the
+   kernels queued after it on that instance leave at once, and pmwa_sweep,
+   pmwa_tile, pmwa_boundary, pmwa_rho_slices*, pmwa_green, pmwa_export* and
+   pmwa_batch_sweep (for an active instance) return PMWA_EINVARIANT until
+   pmwa_import restores a configuration.  Every per-site event count stays
+   within the site's slot at all times, so no call reads out of bounds. */
+
 /* Simulation parameters (problem statement: introduction, Eq. 5; domains:
    Supplement S-II; Step-5 passes: Step 6 of the pseudo code). */
 typedef struct {

@@ -322,6 +322,13 @@ __device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, G
   return -1;
 }
 
+// An instance whose error word is set has an undefined configuration:
+// every kernel that reads it leaves at once.  All threads of the CTA call
+// this together (it is a barrier), so they all take the same branch.
+__device__ __forceinline__ bool instance_failed(const DevErr* err) {
+  return __syncthreads_or(threadIdx.x == 0 && *reinterpret_cast<const volatile int*>(&err->code) != 0) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Event keys.
 __device__ __forceinline__ uint64_t kpk(uint64_t k) { return k >> 2; }

@@ -31,6 +31,7 @@ struct pmwa_handle {
   DevErr* err;
   unsigned long long* phase;  // device phase-cycle counters
   int device;                 // CUDA device current at pmwa_create
+  bool broken = false;        // a kernel reported an error: configuration undefined until pmwa_import
   bool profiling = false;
   std::vector<Timed> timed;            // events of launches not yet read
   std::vector<cudaEvent_t> event_pool;  // spare events
@@ -229,6 +230,9 @@ int drain_error(pmwa_handle* h) {
   DevErr e;
   if (cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) return PMWA_ECUDA;
   if (e.code) {
+    // a kernel stopped part-way: the configuration is undefined (the
+    // kernels queued after it left at once) until pmwa_import restores one
+    h->broken = true;
     DevErr z{0, 0};
     cudaMemcpy(h->err, &z, sizeof z, cudaMemcpyHostToDevice);
     return e.code;
@@ -458,6 +462,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||
       cudaMemcpy(const_cast<uint64_t*>(d.TH), g.TH, sizeof g.TH, cudaMemcpyHostToDevice) ||
       cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ||
+      cudaMemset(d.cntB, 0, cnt.size() * sizeof(uint32_t)) ||  // every count stays <= cap at all times
       cudaMemset(h->phase, 0, 8 * sizeof(uint64_t)) ||
       cudaMemset(d.rows, 0, size_t(h->rows_cap) * sizeof(pmwa_row))) {
     delete h;
@@ -541,6 +546,7 @@ int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n) 
 
 int pmwa_sweep(pmwa_handle* h, int64_t n) {
   if (!h || n < 0) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   if (h->rows_pending + n > h->rows_cap) return PMWA_EROWS;
   const bool multi = h->d.ndom > 1;
   for (int64_t k = 0; k < n; ++k) {
@@ -570,6 +576,7 @@ int pmwa_sweep(pmwa_handle* h, int64_t n) {
 
 int pmwa_boundary(pmwa_handle* h) {
   if (!h) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   h->d.sweep = uint32_t(h->sweep);
   if (launch_boundary(h->d, 0, h->stream) || launch_boundary(h->d, 1, h->stream)) return PMWA_ECUDA;
   return drain_error(h);
@@ -577,6 +584,7 @@ int pmwa_boundary(pmwa_handle* h) {
 
 int pmwa_tile(pmwa_handle* h, int32_t stop) {
   if (!h || stop < 3 || stop > 6) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   if (stop == 6 && h->rows_pending + 1 > h->rows_cap) return PMWA_EROWS;
   const int rc = run_tile(h, stop, true);
   if (rc) return rc;
@@ -603,6 +611,7 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
 
 int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
   if (!h || K < 1 || !host_out) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   if (size_t(K) > size_t(h->d.cap)) return PMWA_EINVAL;  // scratch: the idle next-configuration slots
   double* dev = reinterpret_cast<double*>(h->d.keyB);
   if (launch_rho(h->d, K, dev, h->stream)) return PMWA_ECUDA;
@@ -614,6 +623,7 @@ int pmwa_rho_slices(pmwa_handle* h, int32_t K, double* host_out) {
 
 int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, double* plaq) {
   if (!h || K < 1 || rmax < 0 || !gx || !gy || !plaq) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   if (rmax > std::min(h->p.Lx, h->p.Ly) / 2) return PMWA_EINVAL;
   const size_t N = size_t(h->d.N);
   // scratch: the idle next-configuration slots hold rho, then the sums
@@ -638,6 +648,7 @@ int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, 
 
 int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out) {
   if (!h) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PMWA_ECUDA;
   if (dev != h->device) return PMWA_EINVAL;  // the handle's device must be current
@@ -659,6 +670,7 @@ int pmwa_set_sweep(pmwa_handle* h, uint64_t s) {
 
 int pmwa_export_bytes(pmwa_handle* h, size_t* bytes) {
   if (!h || !bytes) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
   if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
   std::vector<uint32_t> cnt(size_t(h->d.N));
   if (cudaMemcpy(cnt.data(), h->d.cntA, cnt.size() * 4, cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
@@ -724,6 +736,7 @@ int pmwa_import(pmwa_handle* h, const void* buf, size_t bytes) {
       cudaMemcpy(h->d.cntA, cnt.data(), N * 4, cudaMemcpyHostToDevice) ||
       cudaMemcpy(h->d.keyA, keys.data(), N * cap * 8, cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
+  h->broken = false;
   return PMWA_OK;
 }
 
@@ -1102,6 +1115,8 @@ int pmwa_batch_sweep(pmwa_batch* b, int64_t n) {
   if (!b || n < 0) return PMWA_EINVAL;
   if (n == 0) return PMWA_OK;
   for (int i = 0; i < b->n; ++i)
+    if (b->active[size_t(i)] && b->h[size_t(i)]->broken) return PMWA_EINVARIANT;
+  for (int i = 0; i < b->n; ++i)
     if (b->active[size_t(i)] && b->h[size_t(i)]->rows_pending + n > b->h[size_t(i)]->rows_cap) return PMWA_EROWS;
   for (int i = 0; i < b->n; ++i) {
     const pmwa_handle* hi = b->h[size_t(i)];
@@ -1138,12 +1153,14 @@ int pmwa_batch_sweep(pmwa_batch* b, int64_t n) {
   cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1);
   std::vector<DevErr> e(size_t(b->n));
   if (cudaMemcpy(e.data(), b->errs, e.size() * sizeof(DevErr), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
-  for (const DevErr& x : e)
-    if (x.code) {
-      cudaMemset(b->errs, 0, e.size() * sizeof(DevErr));
-      return x.code;
+  int rc = PMWA_OK;
+  for (size_t i = 0; i < e.size(); ++i)
+    if (e[i].code) {
+      b->h[i]->broken = true;  // undefined until pmwa_import on its handle
+      if (rc == PMWA_OK) rc = e[i].code;
     }
-  return PMWA_OK;
+  if (rc) cudaMemset(b->errs, 0, e.size() * sizeof(DevErr));
+  return rc;
 }
 
 int pmwa_batch_last_ms(pmwa_batch* b, double* ms) {

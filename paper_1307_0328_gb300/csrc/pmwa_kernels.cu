@@ -336,6 +336,7 @@ constexpr int kBoundaryWarps = 4;  // bonds (warps) per block
 
 __global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary(const __grid_constant__ Dev d, int dir) {
   extern __shared__ __align__(16) unsigned char bsm[];
+  if (instance_failed(d.err)) return;
   const ZigTab Z = zig_stage(bsm);
   __syncthreads();
   const int wid = threadIdx.x >> 5;
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary_batch(const De
   if (threadIdx.x == 0) sd = at_iteration(devs[w.x], bb, it);
   const ZigTab Z = zig_stage(bsm);
   __syncthreads();
+  if (instance_failed(sd.err)) return;
   if (sd.ndom < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
   const int wid = threadIdx.x >> 5;
   uint64_t* stage = reinterpret_cast<uint64_t*>(bsm + kZigBytes) + size_t(2 * wid) * cap;

@@ -858,6 +858,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ Dev d, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wsum[32];
+  if (instance_failed(d.err)) return;
   tile_body(d, int(blockIdx.x), stop, sm, wsum);
 }
 
@@ -875,6 +876,7 @@ __global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
   if (!base[w.x].active) return;
   if (threadIdx.x == 0) sd = at_iteration(devs[w.x], base[w.x], it);
   __syncthreads();
+  if (instance_failed(sd.err)) return;
   tile_body(sd, w.y, stop, sm, wsum);
 }
 

@@ -185,15 +185,24 @@ def test_many_worm_cases_exceed_one_warp(kw):
 
 def test_too_small_leg_hint_is_a_capacity_error():
     """A leg-count hint far below the real count makes the sweep return
-    PMWA_ECAPACITY (checked in the kernel, no device fault); the device
-    stays usable."""
+    PMWA_ECAPACITY (checked in the kernel, no device fault); the sweeps
+    queued behind the failed one leave at once, the handle refuses further
+    sweeps until a configuration is imported, and the device stays
+    usable."""
     kw = dict(Lx=16, Ly=16, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=4, seed=3, legs_hint=1)
     g = P.Sim(**kw)
     with pytest.raises(P.PmwaError) as e:
         g.sweep(6)
     assert e.value.status == P.PMWA_ECAPACITY
+    # the configuration is now undefined: the handle refuses to go on ...
+    with pytest.raises(P.PmwaError) as e:
+        g.sweep(1)
+    assert e.value.status == P.PMWA_EINVARIANT
+    # ... until a configuration is imported
     ok = P.Sim(**dict(kw, legs_hint=0))
     ok.sweep(2)
+    g.import_(ok.export())
+    assert np.array_equal(g.export(), ok.export())
 
 
 @pytest.mark.parametrize("legs_hint", [0, 18])

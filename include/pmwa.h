@@ -56,7 +56,7 @@ extern "C" {
 /* When a kernel reports PMWA_ECAPACITY, PMWA_ETIMEOUT or PMWA_EINVARIANT, it
    has stopped part-way and the handle's configuration is undefined: the
    kernels queued after it on that instance leave at once, and pmwa_sweep,
-   pmwa_tile, pmwa_boundary, pmwa_rho_slices*, pmwa_green, pmwa_export* and
+   pmwa_tile, pmwa_boundary, pmwa_rho_slices*, pmwa_green, pmwa_export*, pmwa_check and
    pmwa_batch_sweep (for an active instance) return PMWA_EINVARIANT until
    pmwa_import restores a configuration.  Every per-site event count stays
    within the site's slot at all times, so no call reads out of bounds. */
@@ -166,6 +166,36 @@ int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out);
 int pmwa_export_bytes(pmwa_handle* h, size_t* bytes);
 int pmwa_export(pmwa_handle* h, void* host_buf, size_t bytes);
 int pmwa_import(pmwa_handle* h, const void* host_buf, size_t bytes);
+
+/* Invariants of the current configuration, checked on the device (one warp
+   per site; the worldline representation of the paper's introduction and
+   Steps 3-5 keep them all):
+     PMWA_CHECK_CAPACITY      a site's count exceeds its slot;
+     PMWA_CHECK_TAG           a key is neither a bond leg (tags 0..5) nor a worm (7);
+     PMWA_CHECK_ORDER         a site's times do not strictly increase;
+     PMWA_CHECK_CONTINUITY    the state above an event differs from the state
+                              below the next one (cyclic in time);
+     PMWA_CHECK_BASE          the base state differs from the state above the last event;
+     PMWA_CHECK_BOND          a leg's tag names no bond of its site;
+     PMWA_CHECK_PARTNER       the bond's other site has no leg at the same time;
+     PMWA_CHECK_CONSERVATION  a vertex does not conserve particles (s0 + s1 != s2 + s3).
+   Returns PMWA_OK with *site = -1, *what = 0 when all hold; PMWA_EINVARIANT
+   with the lowest failing site and the lowest failing code at that site; on
+   a handle whose configuration is undefined (see above) PMWA_EINVARIANT with
+   *site = -1.  pmwa_import checks the first five and the capacity on the
+   host; this call checks all eight on the device, for example after every
+   step of a debugging run.  Reads stay inside the slots whatever the
+   configuration.  Synchronous; uses the idle next-configuration slots as
+   scratch.  Cost: one pass over the configuration. */
+#define PMWA_CHECK_CAPACITY     1
+#define PMWA_CHECK_TAG          2
+#define PMWA_CHECK_ORDER        3
+#define PMWA_CHECK_CONTINUITY   4
+#define PMWA_CHECK_BASE         5
+#define PMWA_CHECK_BOND         6
+#define PMWA_CHECK_PARTNER      7
+#define PMWA_CHECK_CONSERVATION 8
+int pmwa_check(pmwa_handle* h, int64_t* site, int32_t* what);
 
 /* Sweep index (the Philox counter word of every draw of a sweep). */
 int pmwa_get_sweep(pmwa_handle* h, uint64_t* sweep);

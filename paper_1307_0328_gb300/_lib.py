@@ -67,6 +67,7 @@ def load(build=True):
         "pmwa_export_bytes": (C.c_int, [vp, P(sz)]),
         "pmwa_export": (C.c_int, [vp, vp, sz]),
         "pmwa_import": (C.c_int, [vp, vp, sz]),
+        "pmwa_check": (C.c_int, [vp, P(C.c_int64), P(C.c_int32)]),
         "pmwa_get_sweep": (C.c_int, [vp, P(C.c_uint64)]),
         "pmwa_set_sweep": (C.c_int, [vp, C.c_uint64]),
         "pmwa_destroy": (C.c_int, [vp]),
@@ -194,6 +195,22 @@ def pmwa_import(h, buf):
     _check("pmwa_import", load().pmwa_import(h, buf.ctypes.data, buf.nbytes))
 
 
+CHECK_NAMES = {1: "capacity", 2: "tag", 3: "order", 4: "continuity", 5: "base", 6: "bond", 7: "partner",
+               8: "conservation"}
+
+
+def pmwa_check(h):
+    """None when every invariant of the current configuration holds, else
+    (site, code) of the lowest failing site (code as PMWA_CHECK_*, names in
+    CHECK_NAMES; site -1 on a handle whose configuration is undefined)."""
+    site, what = C.c_int64(), C.c_int32()
+    rc = load().pmwa_check(h, C.byref(site), C.byref(what))
+    if rc == 5:
+        return (site.value, what.value)
+    _check("pmwa_check", rc)
+    return None
+
+
 def pmwa_get_sweep(h):
     s = C.c_uint64()
     _check("pmwa_get_sweep", load().pmwa_get_sweep(h, C.byref(s)))
@@ -308,6 +325,9 @@ class Sim:
     def rho_slices(self, K):
         return pmwa_rho_slices(self.h, self.N, K)
 
+    def check(self):
+        return pmwa_check(self.h)
+
     @property
     def sweep_index(self):
         return pmwa_get_sweep(self.h)
@@ -368,6 +388,9 @@ class Batch:
 
     def export(self, i):
         return pmwa_export(self.handles[i])
+
+    def check(self, i):
+        return pmwa_check(self.handles[i])
 
     def close(self):
         if getattr(self, "b", None):

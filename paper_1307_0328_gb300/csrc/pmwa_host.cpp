@@ -740,6 +740,23 @@ int pmwa_import(pmwa_handle* h, const void* buf, size_t bytes) {
   return PMWA_OK;
 }
 
+int pmwa_check(pmwa_handle* h, int64_t* site, int32_t* what) {
+  if (!h || !site || !what) return PMWA_EINVAL;
+  *site = -1;
+  *what = 0;
+  if (h->broken) return PMWA_EINVARIANT;
+  // scratch: the first idle next-configuration slot
+  unsigned long long* dev = reinterpret_cast<unsigned long long*>(h->d.keyB);
+  if (launch_check(h->d, dev, h->stream)) return PMWA_ECUDA;
+  unsigned long long r = 0;
+  if (cudaStreamSynchronize(h->stream) || cudaMemcpy(&r, dev, sizeof r, cudaMemcpyDeviceToHost))
+    return PMWA_ECUDA;
+  if (r == ~0ull) return PMWA_OK;
+  *site = int64_t(r >> 4);
+  *what = int32_t(r & 15u);
+  return PMWA_EINVARIANT;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

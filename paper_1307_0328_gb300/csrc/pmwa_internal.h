@@ -125,6 +125,12 @@ int prepare_boundary(int cap);
 int prepare_tile_batch(int cls, int smem);
 int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
+// Invariant check of the current configuration (codes as PMWA_CHECK_*):
+// *out = ~0 when all hold, else min over failing sites of site << 4 | code.
+int launch_check(const Dev& d, unsigned long long* out, void* stream);
+constexpr int kCheckNone = 0x7fffffff;
+constexpr int kCheckCapacity = 1, kCheckTag = 2, kCheckOrder = 3, kCheckContinuity = 4, kCheckBase = 5,
+              kCheckBond = 6, kCheckPartner = 7, kCheckConservation = 8;
 int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sums, void* stream);
 // rho slices through the library's own static device scratch (no allocation)
 int rho_slices_static(const Dev& d, int K, double* host_out, void* stream);

@@ -1,9 +1,10 @@
 // pmwa_kernels.cu -- sm_103a kernels of one PMWA Monte Carlo step.
 //
 //   k_boundary   Step 2 (Eq. 4) + Step 3 on the bonds between domains;
-//                one thread per boundary bond, x bonds then y bonds, in
+//                one warp per boundary bond, x bonds then y bonds, in
 //                place on the current configuration.
 //   k_rho        Supplement S-I worm density at equal-time slices.
+//   k_check      invariants of the current configuration, one warp per site.
 // Steps 3-6 of every other bond and site run in k_tile (pmwa_tile.cu).
 //
 // Configuration layout in HBM: site i owns the slot key[i*cap .. i*cap+cap)
@@ -499,6 +500,80 @@ int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sum
 
 int launch_rho(const Dev& d, int K, double* out, void* stream) {
   k_rho<<<blocks_for(d.N, 128), 128, 0, cudaStream_t(stream)>>>(d, K, out);
+  return int(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Invariants of a worldline configuration with worms (Steps 3-5 keep them):
+// per site, the count fits the slot; every key is a bond leg (tags 0..5) or
+// a worm (7); times strictly increase; the state is continuous around the
+// circle (the state above an event is the state below the next one) and the
+// base state is the state above the last event; a leg's tag names a bond of
+// its site; the bond's other site holds the partner leg at the same time;
+// the vertex conserves particles, s0 + s1 = s2 + s3.  One warp per site,
+// lanes over its events; a partner is found by bisection in at most cap
+// keys, so every read stays inside the slots whatever the configuration.
+// out = min over failing sites of site << 4 | code (lowest code at a site).
+__device__ __forceinline__ int find_pk(const uint64_t* K, int n, uint64_t pk) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (kpk(K[mid]) < pk) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && kpk(K[lo]) == pk) ? lo : -1;
+}
+
+__global__ void k_check(const __grid_constant__ Dev d, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const long long s = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (s >= d.N) return;
+  const uint32_t c = d.cntA[s];
+  const int n = cnt_n(c);
+  int bad = kCheckNone;
+  if (n > d.cap) {
+    bad = kCheckCapacity;
+  } else {
+    const uint64_t* K = d.keyA + size_t(s) * d.cap;
+    for (int k = lane; k < n; k += 32) {
+      const uint64_t key = K[k];
+      const uint64_t nx = K[(k + 1 == n) ? 0 : k + 1];
+      const int t = ktag(key);
+      int b = kCheckNone;
+      if (t == 6) b = kCheckTag;
+      else if (k + 1 < n && kpk(nx) <= kpk(key)) b = kCheckOrder;
+      else if (kab(key) != kbl(nx)) b = kCheckContinuity;
+      else if (k + 1 == n && cnt_base(c) != kab(key)) b = kCheckBase;
+      else if (t != 7) {
+        int dir;
+        const int a = leg_lower(d, int(s), t, &dir);
+        const int o = (a == int(s)) ? site_step(d, a, dir, +1) : a;
+        if (bond_tag(d, a, dir) != t) {
+          b = kCheckBond;
+        } else {
+          const int no = min(cnt_n(d.cntA[o]), d.cap);
+          const uint64_t* KO = d.keyA + size_t(o) * d.cap;
+          const int ko = find_pk(KO, no, kpk(key));
+          if (ko < 0) {
+            b = kCheckPartner;
+          } else {
+            const uint64_t va = (a == int(s)) ? key : KO[ko], vb = (a == int(s)) ? KO[ko] : key;
+            if (kbl(va) + kbl(vb) != kab(va) + kab(vb)) b = kCheckConservation;
+          }
+        }
+      }
+      bad = min(bad, b);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+  if (lane == 0 && bad != kCheckNone)
+    atomicMin(out, (static_cast<unsigned long long>(s) << 4) | static_cast<unsigned long long>(bad));
+}
+
+int launch_check(const Dev& d, unsigned long long* out, void* stream) {
+  if (cudaMemsetAsync(out, 0xff, sizeof(unsigned long long), cudaStream_t(stream)) != cudaSuccess)
+    return int(cudaGetLastError());
+  const long long threads = static_cast<long long>(d.N) * 32;
+  k_check<<<blocks_for(threads, 256), 256, 0, cudaStream_t(stream)>>>(d, out);
   return int(cudaGetLastError());
 }
 

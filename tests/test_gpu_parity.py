@@ -198,11 +198,13 @@ def test_too_small_leg_hint_is_a_capacity_error():
     with pytest.raises(P.PmwaError) as e:
         g.sweep(1)
     assert e.value.status == P.PMWA_EINVARIANT
+    assert g.check() == (-1, 0)
     # ... until a configuration is imported
     ok = P.Sim(**dict(kw, legs_hint=0))
     ok.sweep(2)
     g.import_(ok.export())
     assert np.array_equal(g.export(), ok.export())
+    assert g.check() is None
 
 
 @pytest.mark.parametrize("legs_hint", [0, 18])

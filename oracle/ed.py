@@ -102,6 +102,43 @@ def thermal(Lx, Ly, beta, t, V, mu, eta, slices_r=True):
     return out
 
 
+def green_tau(Lx, Ly, beta, t, V, mu, eta, K, rmax):
+    """Exact single-particle Green function of H_eta at unequal times,
+        G_d(r, dk) = (1/N) sum_i Tr[e^{-(beta - tau) H_eta} b_j e^{-tau H_eta} b+_i] / Z,
+    j = i + r e_d (d = x, y), tau = dk beta / K, for r = 0..rmax and
+    dk = 0..K-1, as an array (2, rmax + 1, K); the entry r = dk = 0 (the two
+    operators at one point) is left 0.  In the eigenbasis of H_eta
+    (energies w, shifted by their minimum) the trace is
+    sum_{m,n} e^{-(beta - tau) w_m - tau w_n} <m|b_j|n> <m|b_i|n>."""
+    N = Lx * Ly
+    H, Q = hamiltonians(Lx, Ly, t, V, mu, eta)
+    w, U = np.linalg.eigh(H - eta * Q)
+    w = w - w.min()
+    Z = np.exp(-beta * w).sum()
+    dim, states, occ = _ops(N)
+    B = []
+    for i in range(N):
+        b = np.zeros((dim, dim))
+        src = states[((states >> i) & 1) == 1]
+        b[src ^ (1 << i), src] = 1.0
+        B.append(U.T @ b @ U)
+    G = np.zeros((2, rmax + 1, K))
+    for dk in range(K):
+        tau = dk * beta / K
+        W = np.exp(-(beta - tau) * w[:, None] - tau * w[None, :]) / Z
+        for r in range(rmax + 1):
+            if r == 0 and dk == 0:
+                continue
+            for d in range(2):
+                acc = 0.0
+                for i in range(N):
+                    x, y = i % Lx, i // Lx
+                    j = (x + r) % Lx + Lx * y if d == 0 else x + Lx * ((y + r) % Ly)
+                    acc += float((W * B[j] * B[i]).sum())
+                G[d, r, dk] = acc / N
+    return G
+
+
 def single_site(beta, mu, eta):
     """Closed form at t = 0, V = 0, where the sites decouple.  Each site is
     h = -mu n - eta (b + b+) = -mu/2 + (mu/2) sz - eta sx (sz = 1 - 2n), a spin

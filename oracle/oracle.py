@@ -79,6 +79,8 @@ def lib():
         L.or_sweep_index.restype = C.c_uint64
         L.or_set_sweep_index.argtypes = [C.c_void_p, C.c_uint64]
         L.or_rho_slices.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.or_rho_alpha.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+        L.or_rho_pair.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
         L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_exp_det.argtypes = [C.c_double]
         L.or_exp_det.restype = C.c_double
@@ -172,6 +174,42 @@ class Oracle:
         out = np.zeros((N, K), dtype=np.float64)
         self._ok(lib().or_rho_slices(self.h, K, out.ctypes.data), "or_rho_slices")
         return out
+
+    def rho_alpha(self, K):
+        """(rho (N, K, 2) with [..., 0] for b and [..., 1] for b+, iv (N, K))."""
+        N = self.params.Lx * self.params.Ly
+        out = np.zeros((N, K, 2), dtype=np.float64)
+        iv = np.zeros((N, K), dtype=np.int32)
+        self._ok(lib().or_rho_alpha(self.h, K, out.ctypes.data, iv.ctypes.data), "or_rho_alpha")
+        return out, iv
+
+    def rho_pair(self, K):
+        """(N, K, K, 2, 2): Q_a1 at slice k1 and Q_a2 at slice k2 on one site."""
+        N = self.params.Lx * self.params.Ly
+        out = np.zeros((N, K, K, 2, 2), dtype=np.float64)
+        self._ok(lib().or_rho_pair(self.h, K, out.ctypes.data), "or_rho_pair")
+        return out
+
+    def green_tau(self, K, rmax):
+        """Supplement S-I: G_d(r, dk) = <b_{i + r e_d}(tau_k + dk beta/K) b+_i(tau_k)>
+        estimated as the average over sites i and slices k of the two-point
+        density / eta^2, for d = x, y, r = 0..rmax, dk = 0..K-1 (0 at r = dk = 0,
+        where the two operators meet).  Returns an array (2, rmax + 1, K)."""
+        p = self.params
+        Lx, Ly, N, eta = p.Lx, p.Ly, p.Lx * p.Ly, p.eta
+        rho, _ = self.rho_alpha(K)
+        pair = self.rho_pair(K)
+        idx = np.arange(N)
+        x, y = idx % Lx, idx // Lx
+        G = np.zeros((2, rmax + 1, K))
+        for dk in range(K):
+            k2 = (np.arange(K) + dk) % K
+            same = pair[:, np.arange(K), k2, 1, 0]            # b+ at k, b at k + dk
+            G[:, 0, dk] = same.sum() / (N * K) / eta ** 2
+            for r in range(1, rmax + 1):
+                for d, j in ((0, (x + r) % Lx + Lx * y), (1, x + Lx * ((y + r) % Ly))):
+                    G[d, r, dk] = (rho[j][:, k2, 0] * rho[:, :, 1]).sum() / (N * K) / eta ** 2
+        return G
 
 
 def philox(ctr, key):

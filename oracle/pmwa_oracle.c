@@ -1137,6 +1137,123 @@ int or_check(or_handle* h) {
 
 static double gfun(int sigma, double x) { return sigma ? coth_det(x) : tanh_det(x); }
 
+/* ---- Supplement S-I resolved by the component of Q --------------------
+   rho_a(X) = eta <q| e^{I2 eta Q} Q_a e^{I1 eta Q} |p> / <q| e^{I eta Q} |p>
+   for X inside the interval I between two vertex legs of a site: p is the
+   state above the lower leg, q the state below the upper one, I1 the part of
+   I below X and I2 the part above.  For one site Q = b + b+ flips the state,
+   so <a| e^{x Q} |b> = f_{ab}(x) = cosh x (a = b) or sinh x (a != b).
+   Writing f_{ab}(x) = e^x F(a ^ b, x) / 2 with F(0, x) = 2 + expm1(-2x) and
+   F(1, x) = -expm1(-2x), the factors e^x cancel because I1 + I2 = I (the
+   lengths are counts of worm grid points, x = count * beta eta / 2^59):
+     rho_a = eta F(q ^ out_a, I2) F(in_a ^ p, I1) / (2 F(q ^ p, I)),
+   with Q_b taking 1 to 0 (in 1, out 0) and Q_b+ taking 0 to 1 (in 0, out 1).
+   I1 counts the worm points strictly between the lower leg and X (0 when X
+   sits on the leg), I2 = I - I1.
+   A site without vertex legs is a circle with no reference point: the
+   conditional density is the trace form eta Tr[Q_a e^{x Q}] / Tr[e^{x Q}]
+   = eta F(1, x) / (2 F(0, x)) with x = beta eta (the whole circle).
+   Two points on one interval (L below U going up from the lower leg, parts
+   Ia, Ib, Ic from the bottom; the paper defers this case) follow from the
+   same expansion with both operators inserted:
+     eta^2 <q| e^{Ic Q} Q_U e^{Ib Q} Q_L e^{Ia Q} |p> / <q| e^{I Q} |p>
+       = eta^2 F(q ^ out_U, Ic) F(in_U ^ out_L, Ib) F(in_L ^ p, Ia) / (4 F(q ^ p, I)),
+   and on a site without legs (b+ ... going up from the point k1 to k2 over
+   Ib points, the rest of the circle Ic = 2^59 - Ib):
+     eta^2 Tr[Q_2 e^{Ib Q} Q_1 e^{Ic Q}] / Tr[e^{2^59 Q}]
+       = eta^2 F(in_2 ^ out_1, Ib) F(in_1 ^ out_2, Ic) / (4 F(0, 2^59)).  */
+static double Fsig(int sigma, uint64_t M, double XW) {
+  double e = or_expm1_det(-2.0 * ((double)M * XW));
+  return sigma ? -e : 2.0 + e;
+}
+static int q_in(int a) { return 1 - a; }   /* state below Q_a */
+static int q_out(int a) { return a; }      /* state above Q_a */
+
+typedef struct {
+  int iv;          /* event index of the lower leg, -1: no legs */
+  int p, q;        /* state above the lower leg, below the upper one */
+  uint64_t M, M1;  /* worm points of the interval and below the slice */
+  uint64_t off;    /* pk distance from the lower leg up to the slice */
+  uint64_t pt;     /* the slice's pk */
+} slice_t;
+
+static uint64_t slice_pk(int32_t K, int k) { return (uint64_t)(((u128)k << 62) / (u128)K); }
+
+static void slice_of(const site_t* S, uint64_t pt, slice_t* o) {
+  o->pt = pt;
+  int last = -1, lo = -1;
+  for (int i = 0; i < S->n; i++)
+    if (!kworm(S->key[i])) { last = i; if (kpk(S->key[i]) <= pt) lo = i; }
+  if (last < 0) { o->iv = -1; o->p = o->q = 0; o->M = TWO59; o->M1 = 0; o->off = 0; return; }
+  if (lo < 0) lo = last;                       /* the slice lies below the first leg */
+  int hi = lo;                                 /* the next leg going up, cyclic */
+  for (int i = 1; i <= S->n; i++) { hi = (lo + i) % S->n; if (!kworm(S->key[hi])) break; }
+  uint64_t plo = kpk(S->key[lo]), phi = kpk(S->key[hi]);
+  o->iv = lo;
+  o->p = kab(S->key[lo]);
+  o->q = kbl(S->key[hi]);
+  o->M = wpts(plo, phi);
+  o->M1 = (pt == plo) ? 0 : wpts(plo, pt);
+  o->off = (pt - plo) & (TWO62 - 1);
+}
+
+static double rho_one(const slice_t* z, int a, double eta, double XW) {
+  if (z->iv < 0) return eta * (Fsig(1, TWO59, XW) / (2.0 * Fsig(0, TWO59, XW)));
+  double num = Fsig(z->q ^ q_out(a), z->M - z->M1, XW) * Fsig(q_in(a) ^ z->p, z->M1, XW);
+  return eta * (num / (2.0 * Fsig(z->q ^ z->p, z->M, XW)));
+}
+
+/* Q_a1 at slice z1 and Q_a2 at slice z2, both on one interval of a site */
+static double rho_two_same(const slice_t* z1, int a1, const slice_t* z2, int a2, double eta, double XW) {
+  if (z1->iv < 0) {
+    uint64_t Ib = wpts(z1->pt, z2->pt), Ic = TWO59 - Ib;
+    double num = Fsig(q_in(a2) ^ q_out(a1), Ib, XW) * Fsig(q_in(a1) ^ q_out(a2), Ic, XW);
+    return (eta * eta) * (num / (4.0 * Fsig(0, TWO59, XW)));
+  }
+  const slice_t *L = z1, *U = z2;
+  int aL = a1, aU = a2;
+  if (z2->off < z1->off) { L = z2; U = z1; aL = a2; aU = a1; }
+  uint64_t Ia = L->M1, Ib = U->M1 - L->M1, Ic = L->M - U->M1;
+  double num = (Fsig(L->q ^ q_out(aU), Ic, XW) * Fsig(q_in(aU) ^ q_out(aL), Ib, XW)) *
+               Fsig(q_in(aL) ^ L->p, Ia, XW);
+  return (eta * eta) * (num / (4.0 * Fsig(L->q ^ L->p, L->M, XW)));
+}
+
+int or_rho_alpha(or_handle* h, int32_t K, double* out, int32_t* iv) {
+  if (K < 1) return OR_EINVAL;
+  double XW = xw_of(h), eta = h->p.eta;
+  for (int s = 0; s < h->N; s++)
+    for (int k = 0; k < K; k++) {
+      slice_t z;
+      slice_of(&h->site[s], slice_pk(K, k), &z);
+      size_t o = (size_t)s * (size_t)K + (size_t)k;
+      for (int a = 0; a < 2; a++) out[o * 2 + (size_t)a] = rho_one(&z, a, eta, XW);
+      if (iv) iv[o] = z.iv;
+    }
+  return OR_OK;
+}
+
+int or_rho_pair(or_handle* h, int32_t K, double* out) {
+  if (K < 1) return OR_EINVAL;
+  double XW = xw_of(h), eta = h->p.eta;
+  slice_t* z = (slice_t*)malloc(sizeof(slice_t) * (size_t)K);
+  for (int s = 0; s < h->N; s++) {
+    for (int k = 0; k < K; k++) slice_of(&h->site[s], slice_pk(K, k), &z[k]);
+    for (int k1 = 0; k1 < K; k1++)
+      for (int k2 = 0; k2 < K; k2++)
+        for (int a1 = 0; a1 < 2; a1++)
+          for (int a2 = 0; a2 < 2; a2++) {
+            double r;
+            if (k1 == k2) r = 0.0;
+            else if (z[k1].iv != z[k2].iv) r = rho_one(&z[k1], a1, eta, XW) * rho_one(&z[k2], a2, eta, XW);
+            else r = rho_two_same(&z[k1], a1, &z[k2], a2, eta, XW);
+            out[(((size_t)s * (size_t)K + (size_t)k1) * (size_t)K + (size_t)k2) * 4 + (size_t)(a1 * 2 + a2)] = r;
+          }
+  }
+  free(z);
+  return OR_OK;
+}
+
 int or_rho_slices(or_handle* h, int32_t K, double* out) {
   if (K < 1) return OR_EINVAL;
   double XW = xw_of(h), eta = h->p.eta;

@@ -84,6 +84,15 @@ int   or_set_sweep_index(or_handle* h, uint64_t s);
 /* rho_i(tau_k) = eta g_sigma(I eta) of the interval that holds slice
    tau_k = k beta / K on site i (Supplement S-I); out[i*K + k]. */
 int   or_rho_slices(or_handle* h, int32_t K, double* out);
+/* Supplement S-I, resolved by the component of Q (a = 0: Q_b = b, a = 1:
+   Q_b+ = b+) at the K slices tau_k = k beta / K:
+   out[(s K + k) 2 + a] = rho_a; iv[s K + k] = event index of the lower
+   vertex leg of the slice's interval, -1 on a site without legs (two slices
+   of one site share an interval iff their iv are equal).                  */
+int   or_rho_alpha(or_handle* h, int32_t K, double* out, int32_t* iv);
+/* two-point densities of one site: out[((s K + k1) K + k2) 4 + a1 2 + a2]
+   for Q_a1 at slice k1 and Q_a2 at slice k2 (0 when k1 == k2).           */
+int   or_rho_pair(or_handle* h, int32_t K, double* out);
 
 /* building blocks, exported for the pins */
 void  or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

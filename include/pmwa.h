@@ -160,6 +160,46 @@ int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, 
    race; each call overwrites every value it returns. */
 int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out);
 
+/* Supplement S-I resolved by the component of Q = b + b+ (a = 0: Q_b = b,
+   which takes a site from 1 to 0; a = 1: Q_b+ = b+): at the K slices
+   tau_k = k beta / K of every site,
+     rho_a(X) = eta <q| e^{I2 eta Q} Q_a e^{I1 eta Q} |p> / <q| e^{I eta Q} |p>,
+   where the slice X splits the interval I between the vertex legs around it
+   (p the state above the lower leg, q the state below the upper one) into
+   I1 below X and I2 above; rho_b + rho_b+ is the value of pmwa_rho_slices.
+   A site without vertex legs gets the trace form eta tanh(beta eta) / 2 for
+   both components.  host_rho[(s K + k) 2 + a] (N K 2 doubles, caller-owned);
+   host_iv[s K + k] (N K int32, caller-owned, may be NULL) = index of the
+   interval's lower leg in the site's time-ordered events, -1 on a site
+   without legs: two slices of one site lie on the same interval iff their
+   iv are equal, and then their joint density is not the product of the two
+   (pmwa_green_tau handles that case).  Products of densities at points on
+   different intervals estimate eta^n <prod Q_a(X)> (Supplement S-I).
+   Scratch: the idle next-configuration slots (8 cap bytes per site), filled
+   by chunks of sites.  Synchronous. */
+int pmwa_rho_alpha(pmwa_handle* h, int32_t K, double* host_rho, int32_t* host_iv);
+
+/* Unequal-time single-particle Green function of H_eta from the densities
+   above (Supplement S-I):
+     host_g[(d (rmax + 1) + r) K + dk] = G_d(r, dk)
+       = < b_{i + r e_d}(tau_k + dk beta / K) b+_i(tau_k) >,
+   averaged over sites i and slices k, d = 0 (x) or 1 (y), r = 0..rmax,
+   dk = 0..K-1 (tau cyclic in beta).  Points on different intervals take the
+   product of their densities / eta^2; two points on one interval of a site
+   (r = 0; the case the paper leaves to later work) take both operators inside
+   the interval's matrix element,
+     eta^2 <q| e^{Ic Q} Q_U e^{Ib Q} Q_L e^{Ia Q} |p> / <q| e^{I Q} |p> / eta^2
+   (L the lower point going up from the lower leg, Ia, Ib, Ic the parts of I
+   from the bottom), and on a site without legs the cyclic trace form.  G at
+   r = dk = 0 (both operators at one point) is not estimated and is 0; the
+   r = 0 row is the same for d = 0 and 1.  1 <= K <= 64,
+   0 <= rmax <= min(Lx, Ly) / 2; host_g holds 2 (rmax + 1) K doubles
+   (caller-owned).  Scratch: the idle next-configuration slots hold every
+   site's densities when rmax >= 1, so PMWA_EINVAL unless 16 K bytes per
+   site plus the sums fit in 8 cap bytes per site (K <= cap / 2 about; cap
+   from pmwa_slot_capacity).  Synchronous. */
+int pmwa_green_tau(pmwa_handle* h, int32_t K, int32_t rmax, double* host_g);
+
 /* Canonical configuration (format in the header comment) to / from host
    memory.  pmwa_export_bytes gives the size; pmwa_import checks the
    invariants and the per-site capacity. */
@@ -259,6 +299,11 @@ int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4,
    Host only; returns PMWA_EINVAL for invalid parameters or a domain that
    does not fit.  Any pointer may be NULL. */
 int pmwa_tile_plan(const pmwa_params* p, int32_t* smem, int32_t* legcap, int32_t* oldcap);
+
+/* Events each site's slot holds (the configuration's per-site capacity,
+   fixed at create from the parameters).  PMWA_EINVAL for invalid
+   parameters. */
+int pmwa_slot_capacity(const pmwa_params* p, int32_t* cap);
 
 /* Shared memory (bytes) the sweep kernel needs per domain for these
    parameters, 0 if a domain does not fit on one SM (a domain-shape tuner

@@ -68,6 +68,9 @@ def load(build=True):
         "pmwa_export": (C.c_int, [vp, vp, sz]),
         "pmwa_import": (C.c_int, [vp, vp, sz]),
         "pmwa_check": (C.c_int, [vp, P(C.c_int64), P(C.c_int32)]),
+        "pmwa_rho_alpha": (C.c_int, [vp, C.c_int32, vp, vp]),
+        "pmwa_slot_capacity": (C.c_int, [P(Params), P(C.c_int32)]),
+        "pmwa_green_tau": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
         "pmwa_get_sweep": (C.c_int, [vp, P(C.c_uint64)]),
         "pmwa_set_sweep": (C.c_int, [vp, C.c_uint64]),
         "pmwa_destroy": (C.c_int, [vp]),
@@ -170,6 +173,21 @@ def pmwa_green(h, K, rmax):
     return gx, gy, pl.value
 
 
+def pmwa_rho_alpha(h, N, K):
+    """(rho (N, K, 2): [..., 0] for b, [..., 1] for b+; iv (N, K) int32)."""
+    rho = np.zeros((N, K, 2), dtype=np.float64)
+    iv = np.zeros((N, K), dtype=np.int32)
+    _check("pmwa_rho_alpha", load().pmwa_rho_alpha(h, K, rho.ctypes.data, iv.ctypes.data))
+    return rho, iv
+
+
+def pmwa_green_tau(h, K, rmax):
+    """G_d(r, dk) as an array (2, rmax + 1, K)."""
+    g = np.zeros((2, rmax + 1, K), dtype=np.float64)
+    _check("pmwa_green_tau", load().pmwa_green_tau(h, K, rmax, g.ctypes.data))
+    return g
+
+
 def pmwa_rho_slices_static(h, N, K):
     """rho slices with the library's own fixed device scratch (no allocation)."""
     out = np.zeros((N, K), dtype=np.float64)
@@ -223,6 +241,12 @@ def pmwa_set_sweep(h, s):
 
 def pmwa_tile_smem(**kw):
     return int(load().pmwa_tile_smem(C.byref(make_params(**kw))))
+
+
+def pmwa_slot_capacity(**kw):
+    c = C.c_int32()
+    _check("pmwa_slot_capacity", load().pmwa_slot_capacity(C.byref(make_params(**kw)), C.byref(c)))
+    return c.value
 
 
 def pmwa_tile_plan(**kw):
@@ -327,6 +351,12 @@ class Sim:
 
     def check(self):
         return pmwa_check(self.h)
+
+    def rho_alpha(self, K):
+        return pmwa_rho_alpha(self.h, self.N, K)
+
+    def green_tau(self, K, rmax):
+        return pmwa_green_tau(self.h, K, rmax)
 
     @property
     def sweep_index(self):

@@ -1,6 +1,6 @@
 """Build libpmwa.so in-tree with nvcc for sm_103a (GB300).
 
-Two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_1307_0328_gb300/_build/libpmwa.so.  No FMA contraction anywhere
 (--fmad=false for device code, -ffp-contract=off for host code): the
 deterministic mode reproduces IEEE binary64 results operation by operation.
@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpmwa.so")
-SOURCES = ["pmwa_kernels.cu", "pmwa_tile.cu", "pmwa_host.cpp"]
+SOURCES = ["pmwa_kernels.cu", "pmwa_tile.cu", "pmwa_green.cu", "pmwa_host.cpp"]
 DEPS = SOURCES + ["pmwa_device.cuh", "pmwa_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17",

@@ -377,6 +377,14 @@ int pmwa_tables(const pmwa_params* p, double* d4, double* D, uint64_t* tv4, uint
   return PMWA_OK;
 }
 
+int pmwa_slot_capacity(const pmwa_params* p, int32_t* cap) {
+  if (!p || !cap || validate(p)) return PMWA_EINVAL;
+  Derived g;
+  derive(p, &g);
+  *cap = int32_t(g.cap);
+  return PMWA_OK;
+}
+
 int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, pmwa_handle** out) {
   if (!out) return PMWA_EINVAL;
   *out = nullptr;
@@ -390,7 +398,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   {
     Zig z;
     build_zig(&z);
-    if (upload_zig(z) || upload_zig_tile(z)) return PMWA_ECUDA;
+    if (upload_zig(z) || upload_zig_tile(z) || upload_zig_green(z)) return PMWA_ECUDA;
     zig_ready = true;
   }
   pmwa_handle* h = new (std::nothrow) pmwa_handle();
@@ -737,6 +745,54 @@ int pmwa_import(pmwa_handle* h, const void* buf, size_t bytes) {
       cudaMemcpy(h->d.keyA, keys.data(), N * cap * 8, cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
   h->broken = false;
+  return PMWA_OK;
+}
+
+int pmwa_rho_alpha(pmwa_handle* h, int32_t K, double* host_rho, int32_t* host_iv) {
+  if (!h || K < 1 || !host_rho) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
+  const size_t N = size_t(h->d.N), per_site = size_t(K) * (2 * sizeof(double) + sizeof(int32_t));
+  // scratch: the idle next-configuration slots, filled by chunks of sites
+  const size_t room = N * size_t(h->d.cap) * sizeof(uint64_t);
+  const size_t chunk = std::min(N, room / per_site);
+  if (chunk == 0) return PMWA_EINVAL;
+  double* rho = reinterpret_cast<double*>(h->d.keyB);
+  int32_t* iv = host_iv ? reinterpret_cast<int32_t*>(rho + 2 * chunk * size_t(K)) : nullptr;
+  for (size_t s0 = 0; s0 < N; s0 += chunk) {
+    const size_t ns = std::min(chunk, N - s0), nk = ns * size_t(K);
+    if (launch_rho_alpha(h->d, K, int(s0), int(ns), rho, iv, h->stream)) return PMWA_ECUDA;
+    if (cudaStreamSynchronize(h->stream) ||
+        cudaMemcpy(host_rho + 2 * s0 * size_t(K), rho, 2 * nk * sizeof(double), cudaMemcpyDeviceToHost) ||
+        (iv && cudaMemcpy(host_iv + s0 * size_t(K), iv, nk * sizeof(int32_t), cudaMemcpyDeviceToHost)))
+      return PMWA_ECUDA;
+  }
+  return PMWA_OK;
+}
+
+int pmwa_green_tau(pmwa_handle* h, int32_t K, int32_t rmax, double* host_g) {
+  if (!h || K < 1 || K > kMaxGreenSlices || rmax < 0 || !host_g) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
+  if (rmax > std::min(h->p.Lx, h->p.Ly) / 2) return PMWA_EINVAL;
+  const size_t N = size_t(h->d.N), NK = N * size_t(K);
+  const size_t nsum = size_t(2) * size_t(rmax + 1) * size_t(K);
+  // scratch: the idle next-configuration slots hold rho (rmax >= 1), then the sums
+  const size_t need = ((rmax > 0 ? 2 * NK : 0) + nsum) * sizeof(double);
+  if (need > N * size_t(h->d.cap) * sizeof(uint64_t)) return PMWA_EINVAL;
+  double* rho = reinterpret_cast<double*>(h->d.keyB);
+  double* sums = rho + (rmax > 0 ? 2 * NK : 0);
+  if (launch_green_tau(h->d, K, rmax, rho, sums, h->stream)) return PMWA_ECUDA;
+  std::vector<double> out(nsum);
+  if (cudaStreamSynchronize(h->stream) ||
+      cudaMemcpy(out.data(), sums, nsum * sizeof(double), cudaMemcpyDeviceToHost))
+    return PMWA_ECUDA;
+  const double eta = h->p.eta, norm = double(N) * double(K);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int r = 0; r <= rmax; ++r)
+      for (int dk = 0; dk < K; ++dk) {
+        // r = 0 is the same for both directions (accumulated once, under dir 0)
+        const double v = out[(size_t(r == 0 ? 0 : dir) * size_t(rmax + 1) + size_t(r)) * size_t(K) + size_t(dk)];
+        host_g[(size_t(dir) * size_t(rmax + 1) + size_t(r)) * size_t(K) + size_t(dk)] = v / norm / (eta * eta);
+      }
   return PMWA_OK;
 }
 

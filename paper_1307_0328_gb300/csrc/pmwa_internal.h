@@ -113,6 +113,7 @@ void build_zig(Zig* z);
 // Kernel launchers (pmwa_kernels.cu).  All return a cudaError_t as int.
 int upload_zig(const Zig& z);       // constants of pmwa_kernels.cu
 int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
+int upload_zig_green(const Zig& z); // constants of pmwa_green.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_tile(const Dev& d, int stop, void* stream);
 int tile_class(int domain_sites);
@@ -128,6 +129,10 @@ int launch_rho(const Dev& d, int K, double* out, void* stream);
 // Invariant check of the current configuration (codes as PMWA_CHECK_*):
 // *out = ~0 when all hold, else min over failing sites of site << 4 | code.
 int launch_check(const Dev& d, unsigned long long* out, void* stream);
+// Supplement S-I estimators resolved by the component of Q (pmwa_green.cu)
+constexpr int kMaxGreenSlices = 64;
+int launch_rho_alpha(const Dev& d, int K, int s0, int ns, double* rho, int32_t* iv, void* stream);
+int launch_green_tau(const Dev& d, int K, int rmax, double* rho, double* sums, void* stream);
 constexpr int kCheckNone = 0x7fffffff;
 constexpr int kCheckCapacity = 1, kCheckTag = 2, kCheckOrder = 3, kCheckContinuity = 4, kCheckBase = 5,
               kCheckBond = 6, kCheckPartner = 7, kCheckConservation = 8;

@@ -437,6 +437,25 @@ def main():
     e_job, nv_e2e_job = over_ranks(e_t, nv_e2e, world, dev)
     e2e_val = nv_e2e_job / e_job
 
+    # estimators outside the timed region (Supplement S-I): the order
+    # parameter of every measured sweep, then the equal-time G(r) with the
+    # plaquette function and the unequal-time single-particle G(r, tau)
+    est = None
+    if rank == 0:
+        ob = P.observables(rows, sim.params)
+        rmax = min(4, min(kw["Lx"], kw["Ly"]) // 2)
+        t0 = time.perf_counter()
+        gx, gy, plaq = P.pmwa_green(sim.h, 16, rmax)
+        t_eq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        gt = P.pmwa_green_tau(sim.h, 8, rmax)
+        t_tau = time.perf_counter() - t0
+        est = dict(order_parameter_Q_per_site=float(ob["Q_impr"].mean()),
+                   green_equal_time=dict(slices=16, rmax=rmax, ms=1000.0 * t_eq, G_QQ_x=[float(v) for v in gx],
+                                         plaquette=float(plaq)),
+                   green_tau=dict(slices=8, rmax=rmax, ms=1000.0 * t_tau,
+                                  G_bbdag_r0=[float(v) for v in gt[0, 0]], G_bbdag_x_r1=[float(v) for v in gt[0, 1]]))
+
     if rank == 0:
         kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
         top = max((k for k in kernels if k != "sweep"), key=lambda k: kernels[k]["ms_total"])
@@ -470,7 +489,7 @@ def main():
             tile_phase_cycles=phases,
             e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=64),
             gpu_launches=int(sum(v["launches"] for k, v in kernels.items() if k != "sweep")),
-            clocks=clk, wall_s=wall,
+            clocks=clk, wall_s=wall, estimators=est,
         )
         if not args.no_batch:
             line["batched"] = batched_vs_plain(P, min(args.steps, 20), args.warmup)

@@ -238,12 +238,14 @@ def _rebuild(P, reps, snaps):
 def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
     """The 512-replica workload (L in {16..64}, beta t in {1..16}, mu in
     [-2, 2], V in {0, 1}, eta in {0.05, 0.1, 0.2}) swept (a) batched: one
-    launch per kernel per sweep, replayed from a CUDA graph, and (b) plain:
-    the same instances one after another, each with its own launches.
-    Vertex updates/s from device time (CUDA events).  A pilot sets each
-    instance's N_cycle and leg-count hint, and the tuner picks its domains
-    again with the hint; if a hint turns out too small (PMWA_ECAPACITY) the
-    batch falls back to the a-priori plans, from the same configurations."""
+    launch per kernel per sweep and launch group, replayed from a CUDA graph,
+    and (b) plain: the same instances one after another, each with its own
+    launches.  Vertex updates/s from device time (CUDA events).  A pilot
+    sets each instance's N_cycle and, where its vertex count has settled,
+    its leg-count hint, and the tuner picks its domains again with the hint;
+    if a hint turns out too small (PMWA_ECAPACITY, in the warm-up or the
+    timed sweeps) the batch starts again from the same configurations with
+    the a-priori plans."""
     from paper_1307_0328_gb300 import autotune as A
     reps0 = A.replica_set(n_reps)
     batch = P.Batch(reps0)
@@ -254,36 +256,52 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
         half = r[len(r) // 2:]
         nc = A.n_cycle_rule(half["n_v"].mean(), half["n_w"].mean())
         ncs.append(nc)
-        p = dict(reps0[i], n_cycle=nc, legs_hint=legs_hint(r[3 * len(r) // 4:]["n_v"].max(), reps0[i], slack=1.3))
+        q = len(r) // 4
+        settled = r[3 * q:]["n_v"].mean() <= 1.01 * max(r[2 * q:3 * q]["n_v"].mean(), 1.0)
+        hint = legs_hint(r[3 * q:]["n_v"].max(), reps0[i], slack=1.3) if settled else 0
+        p = dict(reps0[i], n_cycle=nc, legs_hint=hint)
         p.update(A.tune(p))
         reps.append(p)
         snaps.append((batch.export(i), P.pmwa_get_sweep(batch.handles[i])))
     batch.close()
     G = graph_sweeps or steps
+
+    def timed(reps):
+        b = _rebuild(P, reps, snaps)
+        try:
+            b.graph(G)
+            b.sweep(G * max(1, -(-warmup // G)))
+            for i in range(b.n):
+                b.rows(i)
+            b.sweep(steps)
+        except P.PmwaError:
+            b.close()
+            raise
+        return b
+
     hinted = True
-    batch = _rebuild(P, reps, snaps)
     try:
-        batch.graph(G)
-        batch.sweep(G * max(1, -(-warmup // G)))
+        batch = timed(reps)
     except P.PmwaError as e:
         if e.status != P.PMWA_ECAPACITY:
             raise
-        batch.close()
         hinted = False
         reps = [dict(reps0[i], n_cycle=ncs[i]) for i in range(len(reps0))]
-        batch = _rebuild(P, reps, snaps)
-        batch.graph(G)
-        batch.sweep(G * max(1, -(-warmup // G)))
-    for i in range(batch.n):
-        batch.rows(i)
-    batch.sweep(steps)
+        batch = timed(reps)
     ms_b = batch.last_ms()
     nv_b = sum(float(batch.rows(i)["n_v"].sum()) for i in range(batch.n))
-    # plain: each instance alone, its own launches, same number of sweeps
+    footprint = batch.arena.numel() / 1e9
+    batch.close()
+    # plain: each instance alone, its own launches, from the same
+    # configurations with the same plans and warm-up, so the chains are the
+    # batched ones bit for bit
+    batch = _rebuild(P, reps, snaps)
     ms_p = 0.0
     nv_p = 0.0
     for i in range(batch.n):
         h = batch.handles[i]
+        P.pmwa_sweep(h, G * max(1, -(-warmup // G)))
+        P.pmwa_measure(h)
         P.pmwa_profile(h, True)
         P.pmwa_profile_read(h)
         P.pmwa_sweep(h, steps)
@@ -295,7 +313,7 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
                value=nv_b / (ms_b / 1000.0), unit=UNIT, ms_per_step=ms_b / steps, graph_sweeps=G,
                plain_value=nv_p / (ms_p / 1000.0), plain_ms_per_step=ms_p / steps,
                speedup=(nv_b / ms_b) / (nv_p / ms_p), vertices_per_sweep=nv_b / steps,
-               n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=batch.arena.numel() / 1e9,
+               n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=footprint,
                leg_hints=hinted, mean_domain_sites=sum(p["dom_x"] * p["dom_y"] for p in reps) / len(reps))
     batch.close()
     return out

@@ -1,13 +1,19 @@
 """Domain-shape tuning and the synthetic replica sets of the batched workloads.
 
-The tuner picks, per instance, the domain edge and the Step-5 sub-block edge:
-the largest square domain that divides L and whose shared-memory plan
-(pmwa_tile_smem) fits two CTAs per SM, at least 4 sites wide when the lattice
-allows it, with 2x2 shifted sub-blocks; a measured leg count (legs_hint)
-shrinks the plan and can admit larger domains.  Results are cached per
-(L, beta, t, V, mu, eta, c_off, legs_hint) class.  N_cycle follows the rule "every
-vertex leg reached once per sweep on average", N_cycle = ceil(2 <n_v> / <n_w>),
-from a short pilot of the instance itself, capped at 512.
+The tuner picks, per instance, the domain edge and the Step-5 sub-block edge.
+A CTA's time is set mostly by per-site chains (the legs of one site are
+handled in order), which do not depend on the domain's size, so a batch's
+throughput follows the number of sites resident per SM: CTAs per SM (shared
+memory of the plan, pmwa_tile_smem; about 80 registers a thread; the 32-CTA
+limit) times the sites of a domain.  Among the square domains that divide L,
+at most 16 and at least 4 sites wide when the lattice allows it, the tuner
+takes the most sites per SM, then the most warps per SM, then the larger
+domain (fewer bonds between domains), with 2x2 shifted sub-blocks.  A
+measured leg count (legs_hint) shrinks the plan.  Results are cached per
+(L, beta, t, V, mu, eta, c_off, legs_hint) class.  N_cycle follows the rule
+"every vertex leg reached once per sweep on average",
+N_cycle = ceil(2 <n_v> / <n_w>), from a short pilot of the instance itself,
+capped at 512.
 """
 import math
 
@@ -15,12 +21,35 @@ import numpy as np
 
 from . import _lib
 
-SMEM_TWO_PER_SM = 113 * 1024
+SM_SMEM = 228 * 1024
 _cache = {}
 
 
 def _divisors(L):
     return [s for s in range(L, 1, -1) if L % s == 0]
+
+
+def _threads(sites):
+    return 64 if sites <= 32 else (128 if sites <= 96 else 256)
+
+
+def per_sm(smem, sites):
+    """CTAs of a domain plan per SM: shared memory (1 KB reserved a CTA),
+    registers (about 80 a thread) and the 32-CTA limit."""
+    by_regs = 65536 // (80 * _threads(sites))
+    return min(SM_SMEM // (smem + 1024), by_regs, 32)
+
+
+def legs_wanted(p, sites):
+    """Vertex legs the library plans a domain's leg table for: the measured
+    mean (legs_hint per site) plus 8 standard deviations, else 1.1 times the
+    bound 4 beta (D + t) per site (D the largest diagonal vertex density)."""
+    hint = int(p.get("legs_hint", 0) or 0)
+    if hint > 0:
+        m = float(hint) * sites
+        return m + 8.0 * math.sqrt(m) + 128.0
+    D = _lib.pmwa_tables(**{k: v for k, v in p.items() if k in _lib.DEFAULTS})["D"]
+    return 1.1 * 4.0 * float(p["beta"]) * (D + float(p.get("t", 1.0))) * sites + 256.0
 
 
 def tune(p):
@@ -31,21 +60,31 @@ def tune(p):
     if key in _cache:
         return dict(_cache[key])
     Lx, Ly = int(p["Lx"]), int(p["Ly"])
-    best = None
+    best, best_score = None, None
     for sx in _divisors(Lx):
         if sx > 16 or (sx < Lx and sx < 2):
             continue
         sy = sx if Ly % sx == 0 else Lx if Lx == Ly else None
         if sy is None or (sy < Ly and sy < 2):
             continue
+        if min(sx, sy) < 4 and any(d >= 4 and d <= 16 for d in _divisors(Lx)):
+            continue
         B = 2 if (sx % 2 == 0 and sy % 2 == 0 and min(sx, sy) >= 4) else 0
         trial = dict(p, dom_x=sx, dom_y=sy, sub_block=B)
-        sm = _lib.pmwa_tile_smem(**{k: v for k, v in trial.items() if k in _lib.DEFAULTS})
-        if sm and sm <= SMEM_TWO_PER_SM:
-            best = dict(dom_x=sx, dom_y=sy, sub_block=B)
-            break
-        if sm and best is None:
-            best = dict(dom_x=sx, dom_y=sy, sub_block=B)  # fits one CTA per SM
+        try:
+            plan = _lib.pmwa_tile_plan(**{k: v for k, v in trial.items() if k in _lib.DEFAULTS})
+        except _lib.PmwaError:
+            continue  # no plan fits shared memory
+        sm = plan["smem"]
+        sites = sx * sy
+        # the plan must hold the legs it is made for (else the sweep stops
+        # with PMWA_ECAPACITY)
+        if not sm or plan["legcap"] < min(int(legs_wanted(trial, sites)), 65000):
+            continue
+        k = per_sm(sm, sites)
+        score = (k * sites, k * _threads(sites), sites)
+        if best_score is None or score > best_score:
+            best, best_score = dict(dom_x=sx, dom_y=sy, sub_block=B), score
     if best is None:
         raise ValueError("no domain shape fits shared memory for %r" % (p,))
     _cache[key] = best

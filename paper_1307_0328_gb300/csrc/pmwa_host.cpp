@@ -827,13 +827,14 @@ struct pmwa_batch {
   Dev* devs = nullptr;
   BatchBase* base = nullptr;
   DevErr* errs = nullptr;
-  int2* tile_work = nullptr;  // grouped by CTA-size class
+  int2* tile_work = nullptr;  // grouped by launch group (see batch_group)
   int2* bwork[2] = {nullptr, nullptr};
   int n_tile = 0, n_bwork[2] = {0, 0}, cap_max = 0;
-  int cls_off[3] = {0, 0, 0}, cls_n[3] = {0, 0, 0}, cls_smem[3] = {0, 0, 0};
-  int bcls_off[2][3] = {{0, 0, 0}, {0, 0, 0}}, bcls_n[2][3] = {{0, 0, 0}, {0, 0, 0}};
-  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};  // one capture branch per CTA-size class
-  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+  // per launch group: work range, CTA-size class, dynamic shared memory
+  int cls_off[kBatchGroups] = {}, cls_n[kBatchGroups] = {}, cls_smem[kBatchGroups] = {}, cls_thr[kBatchGroups] = {};
+  int bcls_off[2][kBatchGroups] = {}, bcls_n[2][kBatchGroups] = {};
+  cudaStream_t cs[kBatchGroups] = {};  // one capture branch per launch group
+  cudaEvent_t fork = nullptr, join[kBatchGroups] = {};
   cudaGraphExec_t graph = nullptr;
   int graph_sweeps = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -882,16 +883,28 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   return true;
 }
 
-// work items grouped by CTA-size class, each group in decreasing estimated
+// Launch group of an instance: its CTA-size class (threads per CTA) and the
+// number of its CTAs that fit an SM by shared memory (1, 2, 3, 4, 6 or 8+).
+// A launch reserves the largest plan of its group for every CTA, so instances
+// whose plans allow different residencies go to different launches: a few
+// large plans then do not cut the residency of all the others.
+int batch_group(const Dev& d) {
+  const int c = tile_class(d.dom_x * d.dom_y);
+  const int per_sm = int((228LL * 1024) / (static_cast<long long>(d.sm_total) + 1024));
+  const int r = per_sm >= 8 ? 5 : per_sm >= 6 ? 4 : per_sm >= 4 ? 3 : per_sm >= 3 ? 2 : per_sm >= 2 ? 1 : 0;
+  return c * kResidencyLevels + r;
+}
+
+// work items grouped by launch group, each group in decreasing estimated
 // cost, so that the longest CTAs start first
 void build_tile_work(pmwa_batch* b, std::vector<int2>* work) {
   work->clear();
-  for (int c = 0; c < 3; ++c) {
+  for (int g = 0; g < kBatchGroups; ++g) {
     std::vector<std::pair<double, int2>> items;
     int smem = 0;
     for (int i = 0; i < b->n; ++i) {
       const Dev& d = b->h[size_t(i)]->d;
-      if (tile_class(d.dom_x * d.dom_y) != c) continue;
+      if (batch_group(d) != g) continue;
       smem = std::max(smem, d.sm_total);
       const double cost = double(d.dom_x * d.dom_y) * b->h[size_t(i)]->p.beta *
                           (d.dvw[0] + d.tkink + 1.0) * double(d.n_cycle + 4);
@@ -899,30 +912,31 @@ void build_tile_work(pmwa_batch* b, std::vector<int2>* work) {
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) { return x.first > y.first; });
-    b->cls_off[c] = int(work->size());
-    b->cls_n[c] = int(items.size());
-    b->cls_smem[c] = smem;
+    b->cls_off[g] = int(work->size());
+    b->cls_n[g] = int(items.size());
+    b->cls_smem[g] = smem;
+    b->cls_thr[g] = g / kResidencyLevels;
     for (const auto& it : items) work->push_back(it.second);
   }
 }
 
 // Boundary work of both directions: blocks of bonds per instance, grouped
-// by the instance's CTA-size class (its domains all have one size), so that
-// each class can run as its own chain of launches.
+// by the instance's launch group, so that each group can run as its own
+// chain of launches.
 int build_boundary_work(pmwa_batch* b) {
   std::vector<int2> bw;
   const int bpb = boundary_bonds_per_block(b->cap_max);
   for (int dir = 0; dir < 2; ++dir) {
     bw.clear();
-    for (int c = 0; c < 3; ++c) {
-      b->bcls_off[dir][c] = int(bw.size());
+    for (int g = 0; g < kBatchGroups; ++g) {
+      b->bcls_off[dir][g] = int(bw.size());
       for (int i = 0; i < b->n; ++i) {
         const Dev& d = b->h[size_t(i)]->d;
-        if (tile_class(d.dom_x * d.dom_y) != c) continue;
+        if (batch_group(d) != g) continue;
         const int nb = dir == 0 ? (d.ndx > 1 ? d.ndx * d.Ly : 0) : (d.ndy > 1 ? d.ndy * d.Lx : 0);
         for (int t0 = 0; t0 < nb; t0 += bpb) bw.push_back(make_int2(i, t0));
       }
-      b->bcls_n[dir][c] = int(bw.size()) - b->bcls_off[dir][c];
+      b->bcls_n[dir][g] = int(bw.size()) - b->bcls_off[dir][g];
     }
     b->n_bwork[dir] = int(bw.size());
     if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
@@ -935,9 +949,9 @@ int batch_streams(pmwa_batch* b) {
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) || cudaEventCreate(&b->ev0) ||
       cudaEventCreate(&b->ev1) || cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming))
     return PMWA_ECUDA;
-  for (int c = 0; c < 3; ++c)
-    if (cudaStreamCreateWithFlags(&b->cs[c], cudaStreamNonBlocking) ||
-        cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming))
+  for (int g = 0; g < kBatchGroups; ++g)
+    if (cudaStreamCreateWithFlags(&b->cs[g], cudaStreamNonBlocking) ||
+        cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming))
       return PMWA_ECUDA;
   return PMWA_OK;
 }
@@ -947,12 +961,12 @@ void batch_free_streams(pmwa_batch* b) {
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->fork) cudaEventDestroy(b->fork);
-  for (int c = 0; c < 3; ++c) {
-    if (b->cs[c]) cudaStreamDestroy(b->cs[c]);
-    if (b->join[c]) cudaEventDestroy(b->join[c]);
+  for (int g = 0; g < kBatchGroups; ++g) {
+    if (b->cs[g]) cudaStreamDestroy(b->cs[g]);
+    if (b->join[g]) cudaEventDestroy(b->join[g]);
   }
   b->cap = nullptr; b->ev0 = b->ev1 = b->fork = nullptr;
-  for (int c = 0; c < 3; ++c) { b->cs[c] = nullptr; b->join[c] = nullptr; }
+  for (int g = 0; g < kBatchGroups; ++g) { b->cs[g] = nullptr; b->join[g] = nullptr; }
 }
 
 int batch_upload(pmwa_batch* b) {
@@ -964,8 +978,12 @@ int batch_upload(pmwa_batch* b) {
   if (cudaMemcpy(b->devs, devs.data(), devs.size() * sizeof(Dev), cudaMemcpyHostToDevice) ||
       cudaMemcpy(b->tile_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
+  // the largest reservation of each CTA-size class is its kernel's allowance
+  int allow[3] = {0, 0, 0};
+  for (int g = 0; g < kBatchGroups; ++g)
+    if (b->cls_n[g]) allow[b->cls_thr[g]] = std::max(allow[b->cls_thr[g]], b->cls_smem[g]);
   for (int c = 0; c < 3; ++c)
-    if (b->cls_n[c] && prepare_tile_batch(c, b->cls_smem[c])) return PMWA_ECUDA;
+    if (allow[c] && prepare_tile_batch(c, allow[c])) return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -975,15 +993,14 @@ void batch_drop_graph(pmwa_batch* b) {
   b->graph_sweeps = 0;
 }
 
-// one batched sweep at iteration `it` (boundary x, boundary y, tile)
-// One sweep of the instances of class c: boundary x, boundary y, tile.
-int batch_launch_class(pmwa_batch* b, int it, int c, cudaStream_t st) {
+// One sweep of the instances of launch group g: boundary x, boundary y, tile.
+int batch_launch_class(pmwa_batch* b, int it, int g, cudaStream_t st) {
   for (int dir = 0; dir < 2; ++dir)
-    if (b->bcls_n[dir][c] && launch_boundary_batch(b->devs, b->base, b->bwork[dir] + b->bcls_off[dir][c],
-                                                   b->bcls_n[dir][c], it, dir, b->cap_max, st))
+    if (b->bcls_n[dir][g] && launch_boundary_batch(b->devs, b->base, b->bwork[dir] + b->bcls_off[dir][g],
+                                                   b->bcls_n[dir][g], it, dir, b->cap_max, st))
       return PMWA_ECUDA;
-  if (b->cls_n[c] && launch_tile_batch(c, b->devs, b->base, b->tile_work + b->cls_off[c], b->cls_n[c],
-                                       b->cls_smem[c], it, 6, st))
+  if (b->cls_n[g] && launch_tile_batch(b->cls_thr[g], b->devs, b->base, b->tile_work + b->cls_off[g], b->cls_n[g],
+                                       b->cls_smem[g], it, 6, st))
     return PMWA_ECUDA;
   return PMWA_OK;
 }
@@ -993,9 +1010,9 @@ int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
     if (b->n_bwork[dir] &&
         launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, b->cap_max, st))
       return PMWA_ECUDA;
-  for (int c = 2; c >= 0; --c)
-    if (b->cls_n[c] && launch_tile_batch(c, b->devs, b->base, b->tile_work + b->cls_off[c], b->cls_n[c],
-                                         b->cls_smem[c], it, 6, st))
+  for (int g = kBatchGroups - 1; g >= 0; --g)
+    if (b->cls_n[g] && launch_tile_batch(b->cls_thr[g], b->devs, b->base, b->tile_work + b->cls_off[g], b->cls_n[g],
+                                         b->cls_smem[g], it, 6, st))
       return PMWA_ECUDA;
   return PMWA_OK;
 }
@@ -1158,18 +1175,18 @@ int pmwa_batch_graph(pmwa_batch* b, int32_t sweeps) {
     if (rc) return rc;
     b->dirty = false;
   }
-  // one branch per CTA-size class: the classes hold different instances, so
+  // one branch per launch group: the groups hold different instances, so
   // each runs its S sweeps as its own chain of launches and their tails
   // overlap; the branches join before the advance kernel
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) return PMWA_ECUDA;
   int rc = PMWA_OK;
   if (cudaEventRecord(b->fork, b->cap)) rc = PMWA_ECUDA;
-  for (int c = 0; c < 3 && rc == PMWA_OK; ++c) {
-    if (!b->cls_n[c] && !b->bcls_n[0][c] && !b->bcls_n[1][c]) continue;
-    if (cudaStreamWaitEvent(b->cs[c], b->fork, 0)) { rc = PMWA_ECUDA; break; }
-    for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_class(b, it, c, b->cs[c]);
-    if (rc == PMWA_OK && (cudaEventRecord(b->join[c], b->cs[c]) || cudaStreamWaitEvent(b->cap, b->join[c], 0)))
+  for (int g = 0; g < kBatchGroups && rc == PMWA_OK; ++g) {
+    if (!b->cls_n[g] && !b->bcls_n[0][g] && !b->bcls_n[1][g]) continue;
+    if (cudaStreamWaitEvent(b->cs[g], b->fork, 0)) { rc = PMWA_ECUDA; break; }
+    for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_class(b, it, g, b->cs[g]);
+    if (rc == PMWA_OK && (cudaEventRecord(b->join[g], b->cs[g]) || cudaStreamWaitEvent(b->cap, b->join[g], 0)))
       rc = PMWA_ECUDA;
   }
   if (rc == PMWA_OK && launch_advance(b->base, b->n, sweeps, b->cap)) rc = PMWA_ECUDA;

@@ -117,6 +117,9 @@ int upload_zig_green(const Zig& z); // constants of pmwa_green.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_tile(const Dev& d, int stop, void* stream);
 int tile_class(int domain_sites);
+// batch launch groups: 3 CTA-size classes x residency levels by shared memory
+constexpr int kResidencyLevels = 6;
+constexpr int kBatchGroups = 3 * kResidencyLevels;
 int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem,
                       int it, int stop, void* stream);
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,

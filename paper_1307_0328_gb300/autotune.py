@@ -34,10 +34,11 @@ def _threads(sites):
 
 
 def per_sm(smem, sites):
-    """CTAs of a domain plan per SM: shared memory (1 KB reserved a CTA),
+    """CTAs of a domain plan per SM: shared memory (1 KB the hardware
+    reserves a CTA, up to 1 KB of the kernels' static shared memory),
     registers (about 80 a thread) and the 32-CTA limit."""
     by_regs = 65536 // (80 * _threads(sites))
-    return min(SM_SMEM // (smem + 1024), by_regs, 32)
+    return min(SM_SMEM // (smem + 2048), by_regs, 32)
 
 
 def legs_wanted(p, sites):

@@ -890,7 +890,8 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
 // large plans then do not cut the residency of all the others.
 int batch_group(const Dev& d) {
   const int c = tile_class(d.dom_x * d.dom_y);
-  const int per_sm = int((228LL * 1024) / (static_cast<long long>(d.sm_total) + 1024));
+  // (1 KB the hardware reserves a CTA, up to 1 KB of static shared memory)
+  const int per_sm = int((228LL * 1024) / (static_cast<long long>(d.sm_total) + 2048));
   const int r = per_sm >= 8 ? 5 : per_sm >= 6 ? 4 : per_sm >= 4 ? 3 : per_sm >= 3 ? 2 : per_sm >= 2 ? 1 : 0;
   return c * kResidencyLevels + r;
 }

@@ -911,10 +911,11 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
   const long long want = std::min<long long>((long long)legs_want, 65000);
   const long long limit = (long long)kSmemLimit - 1024;
-  // CTAs per SM: shared memory, registers (about 80 a thread: 3, 6 or 12
+  // CTAs per SM: shared memory (1 KB the hardware reserves a CTA and up to
+  // 1 KB of static shared memory), registers (about 80 a thread: 3, 6 or 12
   // CTAs of 256, 128 or 64 threads) and the 32-CTA limit
   const long long by_regs = nds <= 32 ? 12 : (nds <= 96 ? 6 : 3);
-  auto per_sm = [&](long long bytes) { return std::min(std::min((228LL * 1024) / (bytes + 1024), by_regs), 32LL); };
+  auto per_sm = [&](long long bytes) { return std::min(std::min((228LL * 1024) / (bytes + 2048), by_regs), 32LL); };
   // without staging
   const long long uni0 = (long long)std::max(worm_bytes, pool_bytes);
   const long long room = limit - (long long)fixed - uni0;

@@ -388,7 +388,11 @@ def main():
         r = pilot.rows()
         half = r[len(r) // 2:]
         nc = ncycle_rule(half["n_v"].mean(), half["n_w"].mean())
-        kw["legs_hint"] = legs_hint(r[3 * len(r) // 4:]["n_v"].max(), kw)
+        # a leg-count hint only from a settled pilot (last quarter within 1 %
+        # of the quarter before); a chain still growing keeps the a-priori plan
+        q = len(r) // 4
+        if r[3 * q:]["n_v"].mean() <= 1.01 * max(r[2 * q:3 * q]["n_v"].mean(), 1.0):
+            kw["legs_hint"] = legs_hint(r[3 * q:]["n_v"].max(), kw)
         snap = pilot.export()
         s_idx = pilot.sweep_index
         pilot.close()

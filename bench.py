@@ -388,11 +388,7 @@ def main():
         r = pilot.rows()
         half = r[len(r) // 2:]
         nc = ncycle_rule(half["n_v"].mean(), half["n_w"].mean())
-        # a leg-count hint only from a settled pilot (last quarter within 1 %
-        # of the quarter before); a chain still growing keeps the a-priori plan
-        q = len(r) // 4
-        if r[3 * q:]["n_v"].mean() <= 1.01 * max(r[2 * q:3 * q]["n_v"].mean(), 1.0):
-            kw["legs_hint"] = legs_hint(r[3 * q:]["n_v"].max(), kw)
+        kw["legs_hint"] = legs_hint(r[3 * len(r) // 4:]["n_v"].max(), kw)
         snap = pilot.export()
         s_idx = pilot.sweep_index
         pilot.close()
@@ -403,61 +399,84 @@ def main():
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    # warm-up; a leg table sized from the pilot that turns out too small
-    # (PMWA_ECAPACITY) is replaced by the a-priori bound, from the same state
     snap0, idx0 = sim.export(), sim.sweep_index
-    try:
-        sim.sweep(args.warmup)
-    except P.PmwaError as e:
-        if e.status != P.PMWA_ECAPACITY:
-            raise
+
+    def attempt(sim):
+        """Warm-up, the timed sweeps and the end-to-end sweeps.  A leg table
+        sized from the pilot that turns out too small (PMWA_ECAPACITY) stops
+        this rank's sweeps, but the rank still joins every collective, and
+        the attempt is void on all ranks (None)."""
+        failed = False
+
+        def guarded(fn):
+            nonlocal failed
+            if failed:
+                return
+            try:
+                fn()
+            except P.PmwaError as e:
+                if e.status != P.PMWA_ECAPACITY:
+                    raise
+                failed = True
+
+        guarded(lambda: (sim.sweep(args.warmup), sim.rows()))
+        # timed region: per-sweep device spans (library events on its stream)
+        P.pmwa_profile(sim.h, True)
+        P.pmwa_profile_read(sim.h)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 (256 MB > 129 MB) between timed sweeps
+            guarded(lambda: sim.sweep(1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        prof = P.pmwa_profile_read(sim.h)
+        phases = P.pmwa_profile_phases(sim.h)
+        P.pmwa_profile(sim.h, False)
+        clk = clocks.stop()
+        rows = sim.rows() if not failed else None
+        nv = float(rows["n_v"].sum()) if rows is not None else 0.0
+        t_job, nv_job = over_ranks(prof["sweep"][0] / 1000.0, nv, world, dev)
+
+        # e2e through the public API: sweep + read the step's measurement row
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        nv_e2e = 0.0
+        for _ in range(args.steps):
+            def step():
+                nonlocal nv_e2e
+                sim.sweep(1)
+                nv_e2e += float(sim.rows()["n_v"].sum())
+            guarded(step)
+        e_t = time.perf_counter() - e0
+        e_job, nv_e2e_job = over_ranks(e_t, nv_e2e, world, dev)
+        if world > 1:
+            flag = torch.tensor([1.0 if failed else 0.0], device=dev)
+            dist.all_reduce(flag, op=dist.ReduceOp.MAX)
+            failed = flag.item() > 0
+        if failed:
+            return None
+        return dict(wall=wall, prof=prof, phases=phases, clk=clk, rows=rows, t_job=t_job, nv_job=nv_job,
+                    e2e_val=nv_e2e_job / e_job)
+
+    res = attempt(sim)
+    if res is None:
         sim.close()
         kw["legs_hint"] = 0
         sim = P.Sim(n_cycle=nc, **kw)
         sim.import_(snap0)
         sim.sweep_index = idx0
-        sim.sweep(args.warmup)
-    sim.rows()
-    stream = sim.stream
-    # timed region: per-sweep device spans (library events on its stream)
-    P.pmwa_profile(sim.h, True)
-    P.pmwa_profile_read(sim.h)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 (256 MB > 129 MB) between timed sweeps
-        sim.sweep(1)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    prof = P.pmwa_profile_read(sim.h)
-    phases = P.pmwa_profile_phases(sim.h)
-    P.pmwa_profile(sim.h, False)
-    clk = clocks.stop()
-    rows = sim.rows()
-    span_ms = prof["sweep"][0]
-    nv = float(rows["n_v"].sum())
+        res = attempt(sim)
+        if res is None:
+            raise RuntimeError("PMWA_ECAPACITY with the a-priori leg table")
+    wall, prof, phases, clk, rows = res["wall"], res["prof"], res["phases"], res["clk"], res["rows"]
     nw = float(rows["n_w"].mean())
-    t_local = span_ms / 1000.0
-    t_job, nv_job = over_ranks(t_local, nv, world, dev)
+    t_job, nv_job, e2e_val = res["t_job"], res["nv_job"], res["e2e_val"]
     value = nv_job / t_job
-
-    # e2e through the public API: sweep + read the step's measurement row
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    nv_e2e = 0.0
-    for _ in range(args.steps):
-        sim.sweep(1)
-        r = sim.rows()
-        nv_e2e += float(r["n_v"].sum())
-    e_t = time.perf_counter() - e0
-    e2e_local = nv_e2e / e_t
-    e_job, nv_e2e_job = over_ranks(e_t, nv_e2e, world, dev)
-    e2e_val = nv_e2e_job / e_job
 
     # estimators outside the timed region (Supplement S-I): the order
     # parameter of every measured sweep, then the equal-time G(r) with the

@@ -146,9 +146,10 @@ def pmwa_tile(h, stop_after):
 
 
 def pmwa_measure(h, max_rows=1 << 20):
+    """Drain up to max_rows pending measurement rows (oldest first)."""
     chunks = []
     while True:
-        buf = np.zeros(min(max_rows, 65536), dtype=ROW_DTYPE)
+        buf = np.empty(min(max_rows, 4096), dtype=ROW_DTYPE)
         n = C.c_int64()
         _check("pmwa_measure", load().pmwa_measure(h, buf.ctypes.data, len(buf), C.byref(n)))
         chunks.append(buf[: n.value])

@@ -470,9 +470,12 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   if (cudaMemcpy(d.err, &z, sizeof z, cudaMemcpyHostToDevice) ||
       cudaMemcpy(const_cast<uint64_t*>(d.TH), g.TH, sizeof g.TH, cudaMemcpyHostToDevice) ||
       cudaMemcpy(d.cntA, cnt.data(), cnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) ||
-      cudaMemset(d.cntB, 0, cnt.size() * sizeof(uint32_t)) ||  // every count stays <= cap at all times
-      cudaMemset(h->phase, 0, 8 * sizeof(uint64_t)) ||
-      cudaMemset(d.rows, 0, size_t(h->rows_cap) * sizeof(pmwa_row))) {
+      // clears ordered on the handle's stream (which may be a non-blocking
+      // one) and finished before the first launch
+      cudaMemsetAsync(d.cntB, 0, cnt.size() * sizeof(uint32_t), h->stream) ||  // counts stay <= cap at all times
+      cudaMemsetAsync(h->phase, 0, 8 * sizeof(uint64_t), h->stream) ||
+      cudaMemsetAsync(d.rows, 0, size_t(h->rows_cap) * sizeof(pmwa_row), h->stream) ||
+      cudaStreamSynchronize(h->stream)) {
     delete h;
     return PMWA_ECUDA;
   }
@@ -524,7 +527,8 @@ int pmwa_profile(pmwa_handle* h, int32_t enable) {
   h->timed.clear();
   h->profiling = enable != 0;
   h->d.phase_cycles = h->profiling ? h->phase : nullptr;
-  if (cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) return PMWA_ECUDA;
+  if (cudaMemsetAsync(h->phase, 0, 8 * sizeof(uint64_t), h->stream) || cudaStreamSynchronize(h->stream))
+    return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -532,7 +536,8 @@ int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n) {
   if (!h || !cycles || n < 8) return PMWA_EINVAL;
   if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
   if (cudaMemcpy(cycles, h->phase, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
-  if (cudaMemset(h->phase, 0, 8 * sizeof(uint64_t))) return PMWA_ECUDA;
+  if (cudaMemsetAsync(h->phase, 0, 8 * sizeof(uint64_t), h->stream) || cudaStreamSynchronize(h->stream))
+    return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -612,7 +617,12 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
       return PMWA_ECUDA;
   }
   h->rows_pending = rest;
-  if (cudaMemset(h->d.rows + rest, 0, size_t(h->rows_cap - rest) * sizeof(pmwa_row))) return PMWA_ECUDA;
+  // rows past the pending ones are kept zeroed (the sweeps add into them):
+  // clear the n rows just freed, ordered on the handle's stream, and finish
+  // before returning (a batch may launch on another stream)
+  if (n && (cudaMemsetAsync(h->d.rows + rest, 0, size_t(n) * sizeof(pmwa_row), h->stream) ||
+            cudaStreamSynchronize(h->stream)))
+    return PMWA_ECUDA;
   *n_rows = n;
   return PMWA_OK;
 }
@@ -1058,7 +1068,9 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     hi->err = hi->d.err = b->errs + i;  // one contiguous error array for the batch
     b->cap_max = std::max(b->cap_max, hi->d.cap);
   }
-  if (rc == PMWA_OK && cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (cudaMemsetAsync(b->errs, 0, size_t(n) * sizeof(DevErr), b->stream) ||
+                        cudaStreamSynchronize(b->stream)))
+    rc = PMWA_ECUDA;
   if (rc == PMWA_OK) rc = build_boundary_work(b);
   if (rc == PMWA_OK) rc = batch_upload(b);
   if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
@@ -1121,7 +1133,8 @@ int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* arena, size
     hs[i]->err = hs[i]->d.err = b->errs + i;
     b->cap_max = std::max(b->cap_max, hs[i]->d.cap);
   }
-  if (cudaMemset(b->errs, 0, size_t(n) * sizeof(DevErr))) rc = PMWA_ECUDA;
+  if (cudaMemsetAsync(b->errs, 0, size_t(n) * sizeof(DevErr), b->stream) || cudaStreamSynchronize(b->stream))
+    rc = PMWA_ECUDA;
   for (int dir = 0; dir < 2; ++dir) {
     b->bwork[dir] = reinterpret_cast<int2*>(base + o);
     int nb_total = 0;
@@ -1250,7 +1263,8 @@ int pmwa_batch_sweep(pmwa_batch* b, int64_t n) {
       b->h[i]->broken = true;  // undefined until pmwa_import on its handle
       if (rc == PMWA_OK) rc = e[i].code;
     }
-  if (rc) cudaMemset(b->errs, 0, e.size() * sizeof(DevErr));
+  if (rc && (cudaMemsetAsync(b->errs, 0, e.size() * sizeof(DevErr), b->stream) || cudaStreamSynchronize(b->stream)))
+    return PMWA_ECUDA;
   return rc;
 }
 

@@ -749,9 +749,12 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           seg[r + 1] = v;
         }
       }
-      // merge legs with worms (stop 3: the old worms)
+      // merge legs with worms (stop 3: the old worms); the occupied time of
+      // the intervals between consecutive events is summed as they are
+      // written (Step 6), the interval round the circle after the last one
       int il = 0, iw = 0, io = 0, no = 0;
       bool bad = false;
+      uint64_t occ = 0, first_pk = 0, prev = 0;
       for (;;) {
         uint64_t wk = ~0ull;
         if (stop >= 4) { if (iw < nws) wk = T.W[seg[iw]].key; }
@@ -765,6 +768,9 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         if (kpk(lk) < kpk(wk) || wk == ~0ull) { key = lk; ++il; }
         else { key = wk; if (stop >= 4) ++iw; else ++io; }
         if (no >= d.cap) { bad = true; break; }
+        if (no == 0) first_pk = kpk(key);
+        else if (kab(prev)) occ += (kpk(key) - kpk(prev)) & kMask62;
+        prev = key;
         OUT[no++] = key;
       }
       if (bad) { tile_fail(misc, PMWA_ECAPACITY, 6); continue; }
@@ -775,13 +781,9 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       if (stop < 6) continue;
       // Step 6, per site: occupied time (at most 2^62 a site, summed in 128
       // bits), worms; a site without legs is one interval of sigma = 0
-      uint64_t occ = (no == 0 && base) ? kTwo62 : 0;
-      for (int k = 0; k < no; ++k) {
-        const uint64_t key = OUT[k];
-        const uint64_t nx = kpk(OUT[k + 1 == no ? 0 : k + 1]);
-        const uint64_t len = (no == 1) ? kTwo62 : ((nx - kpk(key)) & kMask62);
-        if (kab(key)) occ += len;
-      }
+      if (no == 0) occ = base ? kTwo62 : 0;
+      else if (no == 1) occ = kab(prev) ? kTwo62 : 0;
+      else if (kab(prev)) occ += (first_pk - kpk(prev)) & kMask62;
       add128(olo, ohi, occ, 0);
       nwc += uint64_t(no - nl);
       if (nl == 0) {

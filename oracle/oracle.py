@@ -175,6 +175,29 @@ class Oracle:
         self._ok(lib().or_rho_slices(self.h, K, out.ctypes.data), "or_rho_slices")
         return out
 
+    def npoint(self, K, tuples):
+        """Supplement S-I for n distinct sites at equal time:
+        <Q_i1(tau) ... Q_in(tau)> = eta^-n <rho_i1(tau) ... rho_in(tau)>,
+        averaged over the K slices, for each row of `tuples` (m x n site
+        indices).  Distinct sites never share an interval, so the densities
+        multiply.  Per tuple: for each slice the product over the sites in
+        row order from 1.0, summed over the slices in order, divided by K and
+        then by eta^n (eta multiplied n times from 1.0)."""
+        t = np.asarray(tuples, dtype=np.int64)
+        m, n = t.shape
+        rho = self.rho_slices(K)
+        eta = self.params.eta
+        acc = np.zeros(m)
+        for k in range(K):
+            p = np.ones(m)
+            for c in range(n):
+                p = p * rho[t[:, c], k]
+            acc = acc + p
+        etan = 1.0
+        for _ in range(n):
+            etan = etan * eta
+        return (acc / float(K)) / etan
+
     def rho_alpha(self, K):
         """(rho (N, K, 2) with [..., 0] for b and [..., 1] for b+, iv (N, K))."""
         N = self.params.Lx * self.params.Ly

@@ -160,6 +160,20 @@ int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, 
    race; each call overwrites every value it returns. */
 int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out);
 
+/* Supplement S-I n-point functions of listed site tuples at equal time:
+     host_out[j] = < Q_i1(tau) ... Q_in(tau) > = eta^-n < rho_i1(tau) ... rho_in(tau) >,
+   averaged over the K slices tau_k = k beta / K, for tuple j of n sites
+   host_sites[j n + c] (row-major, m tuples, caller-owned), rho the density
+   of pmwa_rho_slices.  Distinct sites never share an interval, so the
+   densities multiply; a tuple that names one site twice, or a site outside
+   0..N-1, returns PMWA_EINVAL.  1 <= n <= 16, m >= 0; host_out holds m
+   doubles (caller-owned).  Per tuple: for each slice the product over the
+   sites in tuple order, summed over the slices in order, divided by K and
+   then by eta^n.  Scratch: the idle next-configuration slots (the densities,
+   8 K bytes per site, then chunks of tuples); PMWA_EINVAL when the densities
+   leave no room for one tuple.  Synchronous. */
+int pmwa_npoint(pmwa_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* host_sites, double* host_out);
+
 /* Supplement S-I resolved by the component of Q = b + b+ (a = 0: Q_b = b,
    which takes a site from 1 to 0; a = 1: Q_b+ = b+): at the K slices
    tau_k = k beta / K of every site,

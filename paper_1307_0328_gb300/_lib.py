@@ -71,6 +71,7 @@ def load(build=True):
         "pmwa_rho_alpha": (C.c_int, [vp, C.c_int32, vp, vp]),
         "pmwa_slot_capacity": (C.c_int, [P(Params), P(C.c_int32)]),
         "pmwa_green_tau": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
+        "pmwa_npoint": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int64, vp, vp]),
         "pmwa_get_sweep": (C.c_int, [vp, P(C.c_uint64)]),
         "pmwa_set_sweep": (C.c_int, [vp, C.c_uint64]),
         "pmwa_destroy": (C.c_int, [vp]),
@@ -187,6 +188,17 @@ def pmwa_green_tau(h, K, rmax):
     g = np.zeros((2, rmax + 1, K), dtype=np.float64)
     _check("pmwa_green_tau", load().pmwa_green_tau(h, K, rmax, g.ctypes.data))
     return g
+
+
+def pmwa_npoint(h, K, tuples):
+    """<Q_i1 ... Q_in> at equal time for each row of `tuples` (m x n distinct
+    sites), averaged over K slices: an array (m,)."""
+    t = np.ascontiguousarray(tuples, dtype=np.int32)
+    if t.ndim != 2:
+        raise ValueError("tuples must be an (m, n) array of site indices")
+    out = np.zeros(t.shape[0], dtype=np.float64)
+    _check("pmwa_npoint", load().pmwa_npoint(h, K, t.shape[1], t.shape[0], t.ctypes.data, out.ctypes.data))
+    return out
 
 
 def pmwa_rho_slices_static(h, N, K):
@@ -358,6 +370,9 @@ class Sim:
 
     def green_tau(self, K, rmax):
         return pmwa_green_tau(self.h, K, rmax)
+
+    def npoint(self, K, tuples):
+        return pmwa_npoint(self.h, K, tuples)
 
     @property
     def sweep_index(self):

@@ -188,7 +188,35 @@ __global__ void k_green_tau_r(int Lx, int Ly, int K, int rmax, const double* __r
   if ((threadIdx.x & 31) == 0) atomicAdd(sums + (size_t(dir) * (rmax + 1) + r) * K + dk, acc);
 }
 
+// Supplement S-I n-point functions of distinct sites at equal time: tuple j
+// holds n sites (sites[j n + c]); out[j] = (sum_k prod_c rho[s_c K + k] / K)
+// / eta^n, the product in tuple order from 1.0, the sum over the slices in
+// order, eta^n by n multiplications from 1.0.  Distinct sites never share an
+// interval, so the densities multiply.
+__global__ void k_npoint(int K, int n, int m, const double* __restrict__ rho, const int32_t* __restrict__ sites,
+                         double eta, double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int32_t* t = sites + size_t(j) * n;
+  double acc = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double p = 1.0;
+    for (int c = 0; c < n; ++c) p = __dmul_rn(p, rho[size_t(t[c]) * K + k]);
+    acc = __dadd_rn(acc, p);
+  }
+  double etan = 1.0;
+  for (int c = 0; c < n; ++c) etan = __dmul_rn(etan, eta);
+  out[j] = __ddiv_rn(__ddiv_rn(acc, double(K)), etan);
+}
+
 }  // namespace
+
+int launch_npoint(int K, int n, int m, const double* rho, const int32_t* sites, double eta, double* out,
+                  void* stream) {
+  if (m <= 0) return 0;
+  k_npoint<<<(m + 127) / 128, 128, 0, cudaStream_t(stream)>>>(K, n, m, rho, sites, eta, out);
+  return int(cudaGetLastError());
+}
 
 // this translation unit's copy of the constant tables (expm1_det reads them)
 int upload_zig_green(const Zig& z) { return upload_constants(z); }

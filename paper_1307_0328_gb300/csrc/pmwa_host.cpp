@@ -806,6 +806,41 @@ int pmwa_green_tau(pmwa_handle* h, int32_t K, int32_t rmax, double* host_g) {
   return PMWA_OK;
 }
 
+int pmwa_npoint(pmwa_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* sites, double* out) {
+  if (!h || K < 1 || n < 1 || n > kMaxNpoint || m < 0 || (m > 0 && (!sites || !out))) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
+  const size_t N = size_t(h->d.N);
+  for (int64_t j = 0; j < m; ++j) {
+    const int32_t* t = sites + size_t(j) * size_t(n);
+    for (int c = 0; c < n; ++c) {
+      if (t[c] < 0 || size_t(t[c]) >= N) return PMWA_EINVAL;
+      for (int c2 = 0; c2 < c; ++c2)
+        if (t[c2] == t[c]) return PMWA_EINVAL;  // one site twice: not a product of densities
+    }
+  }
+  if (m == 0) return PMWA_OK;
+  // scratch: the idle next-configuration slots hold rho (N K doubles), then a
+  // chunk of tuples and their results
+  const size_t room = N * size_t(h->d.cap) * sizeof(uint64_t), rho_bytes = N * size_t(K) * sizeof(double);
+  const size_t per = size_t(n) * sizeof(int32_t) + sizeof(double);
+  if (room < rho_bytes + per + 16) return PMWA_EINVAL;
+  const size_t chunk = std::min(std::min(size_t(m), (room - rho_bytes - 16) / per), size_t(1) << 30);
+  double* rho = reinterpret_cast<double*>(h->d.keyB);
+  int32_t* tup = reinterpret_cast<int32_t*>(rho + N * size_t(K));
+  double* res = reinterpret_cast<double*>(h->d.keyB) +
+                (rho_bytes + ((chunk * size_t(n) * sizeof(int32_t) + 7) & ~size_t(7))) / sizeof(double);
+  if (launch_rho(h->d, K, rho, h->stream)) return PMWA_ECUDA;
+  for (size_t j0 = 0; j0 < size_t(m); j0 += chunk) {
+    const size_t c = std::min(chunk, size_t(m) - j0);
+    if (cudaStreamSynchronize(h->stream) ||
+        cudaMemcpy(tup, sites + j0 * size_t(n), c * size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice) ||
+        launch_npoint(K, n, int(c), rho, tup, h->p.eta, res, h->stream) || cudaStreamSynchronize(h->stream) ||
+        cudaMemcpy(out + j0, res, c * sizeof(double), cudaMemcpyDeviceToHost))
+      return PMWA_ECUDA;
+  }
+  return PMWA_OK;
+}
+
 int pmwa_check(pmwa_handle* h, int64_t* site, int32_t* what) {
   if (!h || !site || !what) return PMWA_EINVAL;
   *site = -1;

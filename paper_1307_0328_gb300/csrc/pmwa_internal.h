@@ -136,6 +136,9 @@ int launch_check(const Dev& d, unsigned long long* out, void* stream);
 constexpr int kMaxGreenSlices = 64;
 int launch_rho_alpha(const Dev& d, int K, int s0, int ns, double* rho, int32_t* iv, void* stream);
 int launch_green_tau(const Dev& d, int K, int rmax, double* rho, double* sums, void* stream);
+constexpr int kMaxNpoint = 16;
+int launch_npoint(int K, int n, int m, const double* rho, const int32_t* sites, double eta, double* out,
+                  void* stream);
 constexpr int kCheckNone = 0x7fffffff;
 constexpr int kCheckCapacity = 1, kCheckTag = 2, kCheckOrder = 3, kCheckContinuity = 4, kCheckBase = 5,
               kCheckBond = 6, kCheckPartner = 7, kCheckConservation = 8;

@@ -11,7 +11,7 @@ takes the most sites per SM, then the most warps per SM, then the larger
 domain (fewer bonds between domains), with 2x2 shifted sub-blocks.  A
 measured leg count (legs_hint) shrinks the plan.  Results are cached per
 (L, beta, t, V, mu, eta, c_off, legs_hint) class.  N_cycle follows the rule
-"every vertex leg reached once per sweep on average",
+that every vertex leg is reached about once per sweep on average,
 N_cycle = ceil(2 <n_v> / <n_w>), from a short pilot of the instance itself,
 capped at 512.
 """

@@ -44,7 +44,7 @@ struct Dev {
   int poolcap;  // Step-3 candidates per domain in shared memory
   // shared-memory carve-up of the tile kernel (byte offsets)
   int sm_th, sm_zig, sm_off, sm_base, sm_bcnt, sm_boff, sm_misc, sm_nbr, sm_sub, sm_tinfo, sm_leg, sm_wcnt, sm_pool,
-      sm_worm, sm_idx, sm_ord, sm_wsb, sm_wrk, sm_rw, sm_bkt, sm_fill, sm_total;
+      sm_worm, sm_idx, sm_ord, sm_wsb, sm_wrk, sm_rw, sm_bkt, sm_cnt, sm_fill, sm_total;
   int sm_soff, sm_old;  // staged current configuration of the domain (phases 1-2)
   int sm_part;          // [legcap] u16: index of each vertex leg's partner leg (Step 5)
   int use_part;         // 1: the partner table is planned; 0: Step 5 searches for partners

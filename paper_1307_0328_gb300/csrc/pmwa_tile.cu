@@ -108,6 +108,7 @@ struct Tile {
   uint16_t* wrk;   // [wcap] rank of the k-th worm inside its sub-block (a pass)
   uint64_t* rw;    // [2 wcap] Philox words of each grouped position (a pass)
   int* bkt;        // [max(nsub, nds) + 1]
+  int* cnt;        // [warps x nsub] per 32-worm chunk: pass stamp << 16 | worms of sub-block u
   int* fill;       // [max(nsub, nds)]
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
   uint8_t* tinfo;  // [6 nds] per leg tag: 1 = lower site of the bond, 2 = bond leaves the domain
@@ -400,6 +401,66 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
   if (lane == 31) T.fill[n] = v;
 }
 
+// The grouping of rank_pass by the whole block, for nw <= blockDim.x worms
+// (called by every thread; contains one block barrier).  Warp c ranks the
+// 32 worms of chunk c of the label order among themselves (__match_any_sync)
+// and its group leaders record the chunk's count of each sub-block in
+// cnt[c][u], stamped with the pass (an entry with another stamp counts 0).
+// After the barrier every worm adds the counts of the earlier chunks to its
+// rank, while warp 0 (whose worms add nothing) forms fill[] from the totals.
+// wsb, wrk and fill come out as rank_pass makes them; bkt[] is scratch.
+__device__ void rank_pass_block(const Tile& T, int nw, int q, int pass) {
+  const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int W = (nw + 31) >> 5, n = T.nsub;
+  const int stamp = (pass + 1) << 16;
+  const int k = tid;
+  int u = -1, r = 0;
+  if (c < W) {  // warp-uniform
+    u = (k < nw) ? int(T.sub[T.W[T.ord[k]].site * 4 + q]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, u);
+    r = __popc(peers & lt);
+    if (u >= 0 && (peers & lt) == 0) T.cnt[c * n + u] = stamp | __popc(peers);
+  }
+  __syncthreads();
+  if (c > 0 && u >= 0) {
+    for (int c2 = 0; c2 < c; ++c2) {
+      const int v = T.cnt[c2 * n + u];
+      if ((v & ~0xffff) == stamp) r += v & 0xffff;
+    }
+  }
+  if (u >= 0) {
+    T.wsb[k] = uint16_t(u);
+    T.wrk[k] = uint16_t(r);
+  }
+  if (c == 0) {
+    const int chunk = (n + 31) / 32;
+    const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) {
+      int tot = 0;
+      for (int c2 = 0; c2 < W; ++c2) {
+        const int v = T.cnt[c2 * n + i];
+        if ((v & ~0xffff) == stamp) tot += v & 0xffff;
+      }
+      T.bkt[i] = tot;
+      sum += tot;
+    }
+    int v = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += x;
+    }
+    int run = v - sum;
+    for (int i = lo; i < hi; ++i) {
+      T.fill[i] = run;
+      run += T.bkt[i];
+      T.bkt[i] = 0;
+    }
+    if (lane == 31) T.fill[n] = v;
+  }
+}
+
 // All N_cycle passes of a domain holding nw <= 32 worms, run by one warp
 // (lane = threadIdx.x < 32) with no block barrier.  Lane k holds the k-th
 // worm in label order; __match_any_sync over the sub-blocks gives each worm
@@ -462,6 +523,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.wrk = reinterpret_cast<uint16_t*>(sm + d.sm_wrk);
   T.rw = reinterpret_cast<uint64_t*>(sm + d.sm_rw);
   T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
+  T.cnt = reinterpret_cast<int*>(sm + d.sm_cnt);
   T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
   T.tinfo = reinterpret_cast<uint8_t*>(sm + d.sm_tinfo);
@@ -676,6 +738,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       // label order; the r-th move of sub-block u draws Philox block r of
       // stream (unit = domain * n_sub + u, scatter | pass).
       for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
+      for (int i = tid; i < (NT >> 5) * T.nsub; i += NT) T.cnt[i] = 0;  // no stamp of this sweep
       __syncthreads();
       if (nw > 0 && nw <= 32) {  // few worms: one warp, no block barrier per pass
         if (tid < 32) {
@@ -687,7 +750,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       }
       for (int pass = 0; pass < (nw > 32 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         const int q = pass & 3;
-        if (tid < 32) rank_pass(T, nw, q, tid);
+        if (nw <= NT) rank_pass_block(T, nw, q, pass);  // all warps, one chunk each
+        else if (tid < 32) rank_pass(T, nw, q, tid);
         __syncthreads();
         const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
         for (int k = tid; k < nw; k += NT) {
@@ -908,8 +972,12 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const size_t fixed = o;
   // worm side of the union: table, index, label order, sub-block ids and
   // ranks, Philox words, two bucket arrays
+  // (and the per-chunk sub-block counts of the block-wide grouping: one row
+  // per warp of the domain's CTA)
+  const int warps = (nds <= 32 ? 64 : (nds <= 96 ? 128 : 256)) / 32;
+  const size_t cnt_bytes = up16(size_t(warps) * size_t(nsub) * sizeof(int));
   const size_t worm_bytes = up16(size_t(d->wcap) * sizeof(WormRec)) + 4 * up16(size_t(d->wcap) * 2) +
-                            up16(size_t(d->wcap) * 16) + 2 * up16(size_t(nb) * sizeof(int));
+                            up16(size_t(d->wcap) * 16) + 2 * up16(size_t(nb) * sizeof(int)) + cnt_bytes;
   const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
   const long long want = std::min<long long>((long long)legs_want, 65000);
   const long long limit = (long long)kSmemLimit - 1024;
@@ -956,6 +1024,7 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   d->sm_wrk = int(w); w = up16(w + size_t(d->wcap) * 2);
   d->sm_rw = int(w); w = up16(w + size_t(d->wcap) * 16);
   d->sm_bkt = int(w); w = up16(w + size_t(nb) * sizeof(int));
+  d->sm_cnt = int(w); w += cnt_bytes;
   d->sm_fill = int(w); w = up16(w + size_t(nb) * sizeof(int));
   o = std::max(w, o + pool_bytes + (staged ? size_t(stage) : 0));
   d->sm_total = int(o);

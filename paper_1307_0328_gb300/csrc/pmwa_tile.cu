@@ -407,9 +407,11 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
 // and its group leaders record the chunk's count of each sub-block in
 // cnt[c][u], stamped with the pass (an entry with another stamp counts 0).
 // After the barrier every worm adds the counts of the earlier chunks to its
-// rank, while warp 0 (whose worms add nothing) forms fill[] from the totals.
-// wsb, wrk and fill come out as rank_pass makes them; bkt[] is scratch.
-__device__ void rank_pass_block(const Tile& T, int nw, int q, int pass) {
+// rank, while one warp forms fill[] from the totals: the last warp when it
+// holds no worms, else warp 0 (whose worms add nothing).  The worm of thread
+// k = threadIdx.x gets its sub-block u (-1: no worm) and rank r; fill comes
+// out as rank_pass makes it (after a barrier); bkt[] is scratch.
+__device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_out, int& r_out) {
   const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int W = (nw + 31) >> 5, n = T.nsub;
@@ -429,11 +431,10 @@ __device__ void rank_pass_block(const Tile& T, int nw, int q, int pass) {
       if ((v & ~0xffff) == stamp) r += v & 0xffff;
     }
   }
-  if (u >= 0) {
-    T.wsb[k] = uint16_t(u);
-    T.wrk[k] = uint16_t(r);
-  }
-  if (c == 0) {
+  u_out = u;
+  r_out = r;
+  const int nwarps = int(blockDim.x) >> 5;
+  if (c == (W < nwarps ? nwarps - 1 : 0)) {
     const int chunk = (n + 31) / 32;
     const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
     int sum = 0;
@@ -750,16 +751,31 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       }
       for (int pass = 0; pass < (nw > 32 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         const int q = pass & 3;
-        if (nw <= NT) rank_pass_block(T, nw, q, pass);  // all warps, one chunk each
-        else if (tid < 32) rank_pass(T, nw, q, tid);
-        __syncthreads();
         const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
-        for (int k = tid; k < nw; k += NT) {
-          const int u = T.wsb[k], r = T.wrk[k], at = T.fill[u] + r;
-          T.idx[at] = T.ord[k];
-          const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
-          T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
-          T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+        if (nw <= NT) {
+          // all warps, one chunk each; each worm's Philox block depends only
+          // on its rank and sub-block, so it is drawn while fill[] is formed
+          int u, r;
+          rank_pass_block(T, nw, q, pass, u, r);
+          P4 b{0u, 0u, 0u, 0u};
+          if (u >= 0) b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+          __syncthreads();
+          if (u >= 0) {
+            const int at = T.fill[u] + r;
+            T.idx[at] = T.ord[tid];
+            T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
+            T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+          }
+        } else {
+          if (tid < 32) rank_pass(T, nw, q, tid);
+          __syncthreads();
+          for (int k = tid; k < nw; k += NT) {
+            const int u = T.wsb[k], r = T.wrk[k], at = T.fill[u] + r;
+            T.idx[at] = T.ord[k];
+            const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+            T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
+            T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+          }
         }
         __syncthreads();
         phase_tick(d, 5, tclk);

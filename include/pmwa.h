@@ -128,8 +128,11 @@ int pmwa_sweep(pmwa_handle* h, int64_t n_sweeps);
 int pmwa_boundary(pmwa_handle* h);
 int pmwa_tile(pmwa_handle* h, int32_t stop_after);
 
-/* Copy up to max_rows pending rows to host memory `rows`, oldest first, and
-   drop them from the device buffer; *n_rows = number copied. */
+/* Copy up to max_rows pending rows to host memory `rows` (caller-owned,
+   max_rows rows), oldest first, and drop them from the device buffer;
+   *n_rows = number copied.  The freed rows are cleared on the handle's
+   stream before the call returns (later sweeps add into them), so the call
+   is ordered with sweeps on any stream.  Synchronous. */
 int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_rows);
 
 /* Supplement S-I worm density at K equal-time slices tau_k = k beta / K:

@@ -47,7 +47,6 @@ DESCR = {
 }
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TILE_PROFILE = os.path.join(ROOT, "profiles", "k_tile_256x256_bt4.md")
 TILE_SOURCES = ["pmwa_tile.cu", "pmwa_device.cuh", "pmwa_internal.h"]
 
 
@@ -63,12 +62,12 @@ def tile_source_hash():
 
 def tile_traffic(wl, events):
     """DRAM bytes (read + write) per k_tile launch: the bytes per event of
-    the committed ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-    of one launch / that launch's events) times this run's mean events per
-    launch, when the capture was taken on this workload from the current
-    kernel sources; else None."""
+    the committed ncu capture for this workload (profiles/k_tile_<wl>.md,
+    dram__bytes_read.sum + dram__bytes_write.sum of one launch / that
+    launch's events) times this run's mean events per launch, when the
+    capture was taken from the current kernel sources; else None."""
     try:
-        with open(TILE_PROFILE) as f:
+        with open(os.path.join(ROOT, "profiles", "k_tile_%s.md" % wl)) as f:
             txt = f.read()
     except OSError:
         return None
@@ -78,12 +77,26 @@ def tile_traffic(wl, events):
             for kv in line.split(":", 1)[1].split():
                 k, _, v = kv.partition("=")
                 vals[k] = v
-    if vals.get("workload") != wl or vals.get("sources_sha256") != tile_source_hash():
+    if vals.get("sources_sha256") != tile_source_hash():
         return None
     try:
         return float(vals["dram_bytes_per_event"]) * events
     except (KeyError, ValueError):
         return None
+
+
+def tile_bytes(n_v, n_w, dom_x):
+    """Algorithmic bytes of one k_tile launch by the count of the hot-path
+    scope table: the whole configuration read and written once, two 16-byte
+    leg records per vertex (64 B a vertex), 16 B a worm, and the boundary
+    halo (one read of 32 B a vertex over the domain width)."""
+    return 64.0 * n_v + 16.0 * n_w + 32.0 * n_v / float(dom_x)
+
+
+def encoding_bytes(n_v, n_w):
+    """The bytes this implementation's 8-byte event keys move per k_tile
+    launch: every event (two legs a vertex, one a worm) read and written."""
+    return 16.0 * (2.0 * n_v + n_w)
 
 
 def peaks():
@@ -179,13 +192,43 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle legs
-def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
-    """Time the CPU oracle (as it stands, one thread) on the workload:
-    vertices summed over the timed sweeps / wall time."""
+THERM_SMALL = 64      # edge of the lattice the oracle thermalises before tiling
+THERM_SWEEPS = 100   # oracle sweeps on it (the 64x64, beta t = 4 chain settles in ~100)
+
+
+def oracle_thermalised(wl, n_cycle):
+    """An oracle instance of the workload in a thermalised state: the oracle
+    runs the same parameters on a 64x64 lattice for 100 sweeps, and that
+    configuration is repeated over the full lattice (oracle.tile_config);
+    workloads that are not a multiple of 64 wide start cold.  Returns the
+    instance and a description of the start."""
     from oracle import oracle as O
     kw = dict(WORKLOADS[wl])
-    o = O.Oracle(n_cycle=n_cycle, **kw)
-    o.sweep(max(1, warmup))
+    L = kw["Lx"]
+    if L % THERM_SMALL or L == THERM_SMALL or THERM_SMALL % kw["dom_x"]:
+        o = O.Oracle(n_cycle=n_cycle, **kw)
+        o.sweep(1)
+        o.rows()
+        return o, "cold start + 1 sweep"
+    small = dict(kw, Lx=THERM_SMALL, Ly=THERM_SMALL)
+    o = O.Oracle(n_cycle=n_cycle, **small)
+    o.sweep(THERM_SWEEPS)
+    big = O.tile_config(o.export(), THERM_SMALL, L // THERM_SMALL)
+    del o
+    ob = O.Oracle(n_cycle=n_cycle, **kw)
+    ob.import_(big)
+    ob.sweep_index = THERM_SWEEPS
+    return ob, "thermalised: %d oracle sweeps on %dx%d, tiled %dx%d" % (
+        THERM_SWEEPS, THERM_SMALL, THERM_SMALL, L // THERM_SMALL, L // THERM_SMALL)
+
+
+def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
+    """Time the CPU oracle (as it stands, one thread) on the workload from a
+    thermalised configuration: vertices summed over the timed sweeps / wall
+    time."""
+    o, start = oracle_thermalised(wl, n_cycle)
+    if warmup:
+        o.sweep(warmup)
     o.rows()
     t0 = time.perf_counter()
     steps = 0
@@ -196,7 +239,38 @@ def oracle_rate(wl, n_cycle, seconds, max_steps=None, warmup=0):
         if (max_steps and steps >= max_steps) or (not max_steps and el >= seconds):
             break
     r = o.rows()
-    return float(r["n_v"].sum()) / el, steps, el
+    return float(r["n_v"].sum()) / el, steps, el, start
+
+
+def _oracle_replica_worker(args):
+    """One process of the all-core baseline: replica i of the 512-replica
+    set swept by the oracle for about `seconds`; returns (vertices, seconds)."""
+    i, seconds = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_1307_0328_gb300 import autotune as A
+    p = A.replica_set(512)[i]
+    o = O.Oracle(**p)
+    o.sweep(2)
+    o.rows()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.sweep(1)
+    el = time.perf_counter() - t0
+    return float(o.rows()["n_v"].sum()), el
+
+
+def oracle_all_cores(seconds=10.0):
+    """The oracle on every host core at once: one process per core (spawned,
+    so no process forks after CUDA is up), each sweeping its own replica of
+    the 512-replica set; the aggregate is the sum of the per-process rates."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        out = pool.map(_oracle_replica_worker, [(i, seconds) for i in range(cores)])
+    return dict(value=sum(v / t for v, t in out), unit=UNIT, cores=cores, kind="oracle",
+                sample="replicas 0..%d of the 512-replica set, one oracle process each, %.0f s each "
+                       "after 2 sweeps" % (cores - 1, seconds))
 
 
 def oracle_pilot_n_cycle(wl, pilot):
@@ -215,8 +289,9 @@ def run_reference(args, wl, n_cycle):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rate, steps, el = oracle_rate(wl, n_cycle, 0, max_steps=args.steps, warmup=args.warmup)
-    sample = "%d oracle sweeps (%d warm-up) of the %s workload, N_cycle=%d" % (steps, args.warmup, wl, n_cycle)
+    rate, steps, el, start = oracle_rate(wl, n_cycle, 0, max_steps=args.steps, warmup=args.warmup)
+    sample = "%d oracle sweeps (%d warm-up) of the %s workload, N_cycle=%d, %s" % (
+        steps, args.warmup, wl, n_cycle, start)
     line = dict(metric=METRIC, value=rate, unit=UNIT, impl="reference", n_gpus=args.gpus,
                 steps=steps, warmup=args.warmup, ms_per_step=1000.0 * el / steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u64",
@@ -254,7 +329,7 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
     for i in range(batch.n):
         r = batch.rows(i)
         half = r[len(r) // 2:]
-        nc = A.n_cycle_rule(half["n_v"].mean(), half["n_w"].mean())
+        nc = A.n_cycle_rule(reps0[i], half)
         ncs.append(nc)
         q = len(r) // 4
         settled = r[3 * q:]["n_v"].mean() <= 1.01 * max(r[2 * q:3 * q]["n_v"].mean(), 1.0)
@@ -336,6 +411,94 @@ def serving_run(n_jobs, scale, budget_gb=64.0):
 
 
 # --------------------------------------------------------------------------- GPU leg
+def pilot_sim(P, kw, pilot, n_cycle=0):
+    """Thermalise the workload on the GPU and apply the N_cycle rule
+    (pmwa_n_cycle over the second half of the pilot) and the leg-count hint;
+    returns (sim, n_cycle, kw with the hint)."""
+    kw = dict(kw)
+    if n_cycle:
+        sim = P.Sim(n_cycle=n_cycle, **kw)
+        sim.sweep(pilot)
+        sim.rows()
+        return sim, n_cycle, kw
+    p0 = P.Sim(n_cycle=16, **kw)
+    p0.sweep(pilot)
+    r = p0.rows()
+    nc = P.n_cycle(P.make_params(n_cycle=16, **kw), r[len(r) // 2:])
+    kw["legs_hint"] = legs_hint(r[3 * len(r) // 4:]["n_v"].max(), kw)
+    snap = p0.export()
+    s_idx = p0.sweep_index
+    p0.close()
+    del p0
+    sim = P.Sim(n_cycle=nc, **kw)
+    sim.import_(snap)
+    sim.sweep_index = s_idx
+    return sim, nc, kw
+
+
+def roofline_of(kernels, rows, kw, wl, peak, which):
+    """Roofline of the dominant kernel: the algorithmic bytes of one launch
+    (tile_bytes for k_tile; for the boundary kernel the lists of the two
+    sites of every bond between domains at 64 B a vertex leg pair) over its
+    mean launch time (CUDA events on the library's stream)."""
+    top = max((k for k in kernels if k != "sweep"), key=lambda k: kernels[k]["ms_total"])
+    n_v, n_w = float(rows["n_v"].mean()), float(rows["n_w"].mean())
+    N = kw["Lx"] * kw["Ly"]
+    nbsites = 2 * max((kw["Lx"] // kw["dom_x"]) * kw["Ly"] if kw["Lx"] > kw["dom_x"] else 0,
+                      (kw["Ly"] // kw["dom_y"]) * kw["Lx"] if kw["Ly"] > kw["dom_y"] else 0)
+    alg = dict(tile=tile_bytes(n_v, n_w, kw["dom_x"]), boundary=(32.0 * n_v / N + 16.0 * n_w / N) * nbsites)
+    enc = dict(tile=encoding_bytes(n_v, n_w), boundary=16.0 * (2.0 * n_v + n_w) / N * nbsites)
+    tk = kernels[top]
+    sec = tk["ms_total"] / tk["launches"] / 1000.0
+    achieved = alg[top] / sec / 1e9
+    events = 2.0 * n_v + n_w
+    return dict(bound="hbm", kernel=top, achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                traffic=tile_traffic(wl, events) if top == "tile" else None,
+                alg_bytes_per_launch=alg[top],
+                byte_model="64 B per vertex (two 16-B leg records read and written) + 16 B per worm "
+                           "+ 32 B per vertex / domain width (halo)",
+                encoding=dict(bytes_per_launch=enc[top], achieved=enc[top] / sec / 1e9,
+                              frac=enc[top] / sec / 1e9 / peak,
+                              note="the 8-byte event keys this implementation moves: 16 B per event "
+                                   "(2 n_v + n_w events)"),
+                launch_ms=1000.0 * sec,
+                peak_source=(which + " MEASURED_PEAKS.json hbm_gbs") if which == "measured" else "fallback 6.8 TB/s")
+
+
+def large_leg(P, args, flush):
+    """The 2048x2048, beta t = 16 workload (128x128 domains of 16x16 sites):
+    pilot, then timed sweeps through the library's per-sweep CUDA events.
+    Its configuration (~4 GB of events) is far larger than L2."""
+    wl = "2048x2048_bt16"
+    kw = dict(WORKLOADS[wl])
+    sim, nc, kw = pilot_sim(P, kw, args.large_pilot)
+    sim.sweep(args.warmup)
+    sim.rows()
+    P.pmwa_profile(sim.h, True)
+    P.pmwa_profile_read(sim.h)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    for _ in range(args.large_steps):
+        sim.sweep(1)
+    prof = P.pmwa_profile_read(sim.h)
+    P.pmwa_profile(sim.h, False)
+    clk = clocks.stop()
+    rows = sim.rows()
+    kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
+    t = prof["sweep"][0] / 1000.0
+    peak, which = peaks()
+    ob = P.summary(rows, sim.params, bins=min(10, len(rows)))
+    out = dict(workload=DESCR[wl], value=float(rows["n_v"].sum()) / t, unit=UNIT, steps=args.large_steps,
+               ms_per_step=1000.0 * t / args.large_steps, n_cycle=nc, legs_hint=kw["legs_hint"],
+               pilot_sweeps=args.large_pilot, mean_vertices=float(rows["n_v"].mean()),
+               mean_worms=float(rows["n_w"].mean()), worms_per_domain=ob["w_dom_mean"],
+               worms_per_domain_min=ob["w_dom_min"], empty_domain_fraction=ob["dom_empty_frac"],
+               l2="configuration larger than L2 (no flush needed)",
+               roofline=roofline_of(kernels, rows, kw, wl, peak, which), kernels=kernels, clocks=clk)
+    sim.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,6 +511,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-replica comparison")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048x2048 beta t = 16 leg")
+    ap.add_argument("--large-pilot", type=int, default=150)
+    ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--serve-jobs", type=int, default=24, help="jobs of the serving trace to run (0: skip)")
     ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on each job's sweep count")
     args = ap.parse_args()
@@ -359,7 +525,6 @@ def main():
         run_reference(args, wl, nc)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -376,26 +541,7 @@ def main():
 
     kw = dict(WORKLOADS[wl])
     kw["replica"] = rank  # independent replicas, one per GPU
-    # pilot: thermalise and apply the N_cycle rule
-    if args.n_cycle:
-        nc = args.n_cycle
-        sim = P.Sim(n_cycle=nc, **kw)
-        sim.sweep(args.pilot)
-        sim.rows()
-    else:
-        pilot = P.Sim(n_cycle=16, **kw)
-        pilot.sweep(args.pilot)
-        r = pilot.rows()
-        half = r[len(r) // 2:]
-        nc = ncycle_rule(half["n_v"].mean(), half["n_w"].mean())
-        kw["legs_hint"] = legs_hint(r[3 * len(r) // 4:]["n_v"].max(), kw)
-        snap = pilot.export()
-        s_idx = pilot.sweep_index
-        pilot.close()
-        del pilot
-        sim = P.Sim(n_cycle=nc, **kw)
-        sim.import_(snap)
-        sim.sweep_index = s_idx
+    sim, nc, kw = pilot_sim(P, kw, args.pilot, args.n_cycle)
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -478,12 +624,13 @@ def main():
     t_job, nv_job, e2e_val = res["t_job"], res["nv_job"], res["e2e_val"]
     value = nv_job / t_job
 
-    # estimators outside the timed region (Supplement S-I): the order
-    # parameter of every measured sweep, then the equal-time G(r) with the
-    # plaquette function and the unequal-time single-particle G(r, tau)
+    # estimators outside the timed region (Step 6 and Supplement S-I): the
+    # observables of the measured sweeps with binned errors, then the
+    # equal-time G(r) with the plaquette function and the unequal-time
+    # single-particle G(r, tau)
     est = None
     if rank == 0:
-        ob = P.observables(rows, sim.params)
+        ob = P.summary(rows, sim.params, bins=10)
         rmax = min(4, min(kw["Lx"], kw["Ly"]) // 2)
         t0 = time.perf_counter()
         gx, gy, plaq = P.pmwa_green(sim.h, 16, rmax)
@@ -491,7 +638,7 @@ def main():
         t0 = time.perf_counter()
         gt = P.pmwa_green_tau(sim.h, 8, rmax)
         t_tau = time.perf_counter() - t0
-        est = dict(order_parameter_Q_per_site=float(ob["Q_impr"].mean()),
+        est = dict(observables=ob, order_parameter_Q_per_site=ob["Q_impr"],
                    green_equal_time=dict(slices=16, rmax=rmax, ms=1000.0 * t_eq, G_QQ_x=[float(v) for v in gx],
                                          plaquette=float(plaq)),
                    green_tau=dict(slices=8, rmax=rmax, ms=1000.0 * t_tau,
@@ -499,20 +646,7 @@ def main():
 
     if rank == 0:
         kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
-        top = max((k for k in kernels if k != "sweep"), key=lambda k: kernels[k]["ms_total"])
         peak, which = peaks()
-        # algorithmic bytes per launch: the tile kernel reads the whole current
-        # configuration and writes the whole next one (8-byte event keys: two
-        # vertex legs per vertex plus the worms); a boundary launch reads and
-        # writes the lists of the two sites of every bond between domains
-        ev = float(2 * rows["n_v"].mean() + rows["n_w"].mean())
-        per_site = ev / (kw["Lx"] * kw["Ly"])
-        nbsites = 2 * max((kw["Lx"] // kw["dom_x"]) * kw["Ly"] if kw["Lx"] > kw["dom_x"] else 0,
-                          (kw["Ly"] // kw["dom_y"]) * kw["Lx"] if kw["Ly"] > kw["dom_y"] else 0)
-        alg = dict(tile=16.0 * ev, boundary=16.0 * per_site * nbsites)
-        tk = kernels[top]
-        per_launch_ms = tk["ms_total"] / tk["launches"]
-        achieved = alg.get(top, 0.0) / (per_launch_ms / 1000.0) / 1e9
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=1000.0 * t_job / args.steps, higher_is_better=True, scaling="weak",
@@ -522,25 +656,26 @@ def main():
                         l2="flushed before every timed sweep (256 MB write)",
                         mean_vertices=float(rows["n_v"].mean()), mean_worms=nw,
                         plain_per_instance=True),
-            roofline=dict(bound="hbm", kernel=top, achieved=achieved, peak=peak, unit="GB/s",
-                          frac=achieved / peak, traffic=tile_traffic(wl, ev) if top == "tile" else None,
-                          alg_bytes_per_launch=alg.get(top, 0.0),
-                          peak_source=which + " MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"),
+            roofline=roofline_of(kernels, rows, kw, wl, peak, which),
             kernels=kernels,
             tile_phase_cycles=phases,
             e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=64),
             gpu_launches=int(sum(v["launches"] for k, v in kernels.items() if k != "sweep")),
             clocks=clk, wall_s=wall, estimators=est,
         )
+        sim.close()
+        if not args.no_large:
+            line["large"] = large_leg(P, args, flush)
         if not args.no_batch:
             line["batched"] = batched_vs_plain(P, min(args.steps, 20), args.warmup)
         if args.serve_jobs > 0:
             line["serving"] = serving_run(args.serve_jobs, args.serve_scale)
         if not args.no_cpu:
-            rate, steps, el = oracle_rate(wl, nc, args.cpu_seconds, warmup=1)
+            rate, steps, el, start = oracle_rate(wl, nc, args.cpu_seconds, warmup=1)
             line["cpu_baseline"] = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
-                                        sample="%d oracle sweeps of the %s workload (N_cycle=%d), %.1f s"
-                                        % (steps, wl, nc, el))
+                                        sample="%d oracle sweeps of the %s workload (N_cycle=%d, %s), %.1f s"
+                                        % (steps, wl, nc, start, el),
+                                        all_cores=oracle_all_cores())
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

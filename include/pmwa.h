@@ -99,7 +99,10 @@ typedef struct {
   uint64_t occ_hi;  /*   beta / 2^62, as a 128-bit integer (hi:lo)              */
   double   q_impr;  /* Supplement S-I: sum over intervals of x g_sigma(x),
                        x = I eta, g_0 = tanh, g_1 = coth; <Q> = q_impr/(beta eta) */
-  double   pad;
+  uint32_t w_dom_min; /* fewest worms held by one domain after Step 5 (the
+                         paper's health figure of O(10)-O(100) worms per domain,
+                         discussion of Fig. 3)                                  */
+  uint32_t dom_empty; /* domains without a worm after Step 5                   */
 } pmwa_row;
 
 typedef struct pmwa_handle pmwa_handle;
@@ -345,6 +348,82 @@ int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
    words), 6 the moves of Step 5; n >= 8 entries,
    cleared after reading.  No paper counterpart: measurement plumbing. */
 int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n);
+
+/* ---- Step 6: observables from the measurement rows (host only).
+   Definitions (pseudo code Step 6; Supplement S-I; model of Eq. 5 written per
+   bond as E(n_a, n_b) = V n_a n_b - (mu/4)(n_a + n_b), C = max E + c_off,
+   N sites, N_b = 2 N bonds):
+     E      = (N_b C - n_v / beta) / N            energy of H per site
+     E_eta  = E - eta Q_impr                       energy of H_eta = H - eta Q per site
+     n      = occupied time / (beta N)             density
+     Q_raw  = n_w / (beta eta N)                   <Q>/N from the worm count
+     Q_impr = q_impr / (beta eta N)                <Q>/N, Supplement S-I estimator
+     kin    = n_k / (beta t N_b)                   <b+_i b_j + h.c.> per bond (0 if t = 0)
+   pmwa_row_observables writes these six per row, out[r * PMWA_SERIES + k]
+   with k = PMWA_S_E, ... (n_rows * PMWA_SERIES doubles, caller-owned). */
+#define PMWA_SERIES   6
+#define PMWA_S_E      0
+#define PMWA_S_E_ETA  1
+#define PMWA_S_N      2
+#define PMWA_S_Q_RAW  3
+#define PMWA_S_Q_IMPR 4
+#define PMWA_S_KIN    5
+int pmwa_row_observables(const pmwa_params* p, const pmwa_row* rows, int64_t n_rows, double* out);
+
+/* Means and binned standard errors of the six series over the first
+   bins * floor(n_rows / bins) rows (the remainder at the end is left out):
+   the rows are cut into `bins` consecutive bins of equal length, x_err =
+   sqrt(sum_b (m_b - m)^2 / (bins (bins - 1))) over the bin means m_b.
+   Also the mean vertices and worms per sweep and the worms-per-domain figures
+   the paper uses to judge a decomposition (O(10)-O(100) worms per domain and a
+   small chance of an empty domain; discussion of Fig. 3): the mean over the
+   used rows of n_w / domains, the smallest w_dom_min, and the fraction of
+   (domain, sweep) pairs without a worm.  Domains = (Lx / dom_x)(Ly / dom_y).
+   2 <= bins <= n_rows; PMWA_EINVAL otherwise or for invalid parameters. */
+typedef struct {
+  int64_t rows;                 /* rows used                                   */
+  int32_t bins, pad;
+  double  E, E_err;
+  double  E_eta, E_eta_err;
+  double  n, n_err;
+  double  Q_raw, Q_raw_err;
+  double  Q_impr, Q_impr_err;
+  double  kin, kin_err;
+  double  n_v, n_w;             /* mean vertices and worms per sweep            */
+  double  w_dom_mean;           /* mean worms per domain                        */
+  double  w_dom_min;            /* fewest worms seen in one domain              */
+  double  dom_empty_frac;       /* fraction of (domain, sweep) pairs without worms */
+} pmwa_obs;
+int pmwa_observables(const pmwa_params* p, const pmwa_row* rows, int64_t n_rows, int32_t bins, pmwa_obs* out);
+
+/* N_cycle, the Step-5 passes per sweep, by the rule that every part of the
+   space-time is visited about once per sweep (pseudo code Step 5): a move
+   lands a worm on one vertex leg, a sweep holds 2 n_v legs and n_w worms move
+   per pass, so N_cycle = ceil(2 <n_v> / <n_w>) with the means over the given
+   rows (e.g. the second half of a pilot), <n_w> at least 1; with no rows
+   (n_rows = 0) the a-priori estimate from <n_v> = N_b beta (d_mean + t/2)
+   (d_mean the mean of d(s) = C - E(s) over the four states) and
+   <n_w> = beta eta N / 2.  Capped to 1..512.  Host only. */
+int pmwa_n_cycle(const pmwa_params* p, const pmwa_row* rows, int64_t n_rows, int32_t* n_cycle);
+
+/* Caps of the bounded device loops of this handle: words drawn for one
+   exponential deviate (1..64, the specification's 64 by default) and
+   proposals of the Eq. 1 worm-number sampler (1..128, default 128).  The
+   defaults are part of the deterministic specification; smaller caps exist
+   to exercise the PMWA_ETIMEOUT path, which then leaves the configuration
+   undefined until pmwa_import (see above).  Takes effect at the next plain
+   call on the handle (a batch copies its instances' settings when it is
+   created).  No paper counterpart: test plumbing. */
+int pmwa_set_loop_caps(pmwa_handle* h, int32_t zig_words, int32_t worm_tries);
+
+/* n Philox4x32-10 blocks computed by the device code every kernel draws
+   from: host_in[6 j .. 6 j + 6) = counter words c0..c3 and key words k0, k1
+   of block j, host_out[4 j .. 4 j + 4) = its four output words
+   (caller-owned host buffers).  Scratch: the handle's idle
+   next-configuration slots (40 bytes per block; PMWA_EINVAL beyond them).
+   Synchronous.  No paper counterpart: it lets a test compare the device
+   generator with published known-answer vectors. */
+int pmwa_philox_blocks(pmwa_handle* h, int64_t n, const uint32_t* host_in, uint32_t* host_out);
 
 const char* pmwa_strerror(int status);
 

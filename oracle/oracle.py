@@ -45,11 +45,12 @@ class Params(C.Structure):
 class Row(C.Structure):
     _fields_ = [("sweep", C.c_uint64), ("n_v", C.c_uint64), ("n_k", C.c_uint64),
                 ("n_w", C.c_uint64), ("occ_lo", C.c_uint64), ("occ_hi", C.c_uint64),
-                ("q_impr", C.c_double), ("pad", C.c_double)]
+                ("q_impr", C.c_double), ("w_dom_min", C.c_uint32), ("dom_empty", C.c_uint32)]
 
 
 ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
-                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("pad", "<f8")])
+                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("w_dom_min", "<u4"),
+                      ("dom_empty", "<u4")])
 
 DEFAULTS = dict(Lx=4, Ly=4, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1,
                 dom_x=0, dom_y=0, exchange_every=2, n_cycle=8, sub_block=0,
@@ -233,6 +234,37 @@ class Oracle:
                 for d, j in ((0, (x + r) % Lx + Lx * y), (1, x + Lx * ((y + r) % Ly))):
                     G[d, r, dk] = (rho[j][:, k2, 0] * rho[:, :, 1]).sum() / (N * K) / eta ** 2
         return G
+
+
+def tile_config(buf, L, T):
+    """A configuration of the L x L lattice repeated T x T times on the
+    (T L) x (T L) lattice: every site copies its event list, and the legs of
+    the bonds that wrapped round the small torus take the tags of the bonds
+    they become on the large one (class 2 only at the last column or row).
+    A way to start a large lattice from a locally thermalised state that the
+    oracle reaches in seconds on the small one."""
+    N = L * L
+    lists, k = [], 1
+    for s in range(N):
+        n = int(buf[k] & np.uint64(0x7fffffff))
+        lists.append((buf[k], buf[k + 1:k + 1 + n].copy()))
+        k += 1 + n
+    LL = T * L
+    out = [np.array([LL * LL], dtype=np.uint64)]
+    for y in range(LL):
+        for x in range(LL):
+            hd, ev = lists[(x % L) + L * (y % L)]
+            ev = ev.copy()
+            tag = (ev >> np.uint64(2)) & np.uint64(7)
+            for d, c in ((0, x), (1, y)):
+                # the wrap bond of the small torus joins c = L-1 (mod L) to c = 0
+                # (mod L); on the large torus only c = LL-1 / 0 keeps class 2
+                if (c % L == L - 1 and c != LL - 1) or (c % L == 0 and c != 0):
+                    m = tag == np.uint64(3 * d + 2)
+                    ev[m] = (ev[m] & ~np.uint64(7 << 2)) | np.uint64((3 * d + 1) << 2)
+            out.append(np.array([hd], dtype=np.uint64))
+            out.append(ev)
+    return np.concatenate(out)
 
 
 def philox(ctr, key):

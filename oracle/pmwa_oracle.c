@@ -840,6 +840,18 @@ static void measure(or_handle* h, or_row* r) {
   r->occ_lo = (uint64_t)occ;
   r->occ_hi = (uint64_t)(occ >> 64);
   r->q_impr = q;
+  /* worms held by each domain (the paper's health figure of O(10)-O(100)
+     worms per domain, discussion of Fig. 3): the fewest, and the empty ones */
+  uint64_t* wd = (uint64_t*)calloc((size_t)h->ndom, sizeof(uint64_t));
+  for (int s = 0; s < h->N; s++)
+    for (int k = 0; k < h->site[s].n; k++) wd[dom_of(h, s)] += kworm(h->site[s].key[k]);
+  uint64_t wmin = UINT64_MAX;
+  for (int D = 0; D < h->ndom; D++) {
+    if (wd[D] < wmin) wmin = wd[D];
+    if (wd[D] == 0) r->dom_empty++;
+  }
+  r->w_dom_min = (uint32_t)wmin;
+  free(wd);
 }
 
 static void push_row(or_handle* h, const or_row* r) {

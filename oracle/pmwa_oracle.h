@@ -55,7 +55,8 @@ typedef struct {
   uint64_t occ_lo;    /* sum_i of occupied imaginary time, in units          */
   uint64_t occ_hi;    /*   beta / 2^62, as a 128-bit integer                  */
   double   q_impr;    /* sum over intervals of x g_sigma(x), x = I eta        */
-  double   pad;
+  uint32_t w_dom_min; /* fewest worms in one domain                           */
+  uint32_t dom_empty; /* domains without a worm                               */
 } or_row;
 
 typedef struct or_handle or_handle;

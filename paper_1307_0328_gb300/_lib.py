@@ -35,7 +35,17 @@ class Params(C.Structure):
 
 
 ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
-                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("pad", "<f8")])
+                      ("occ_lo", "<u8"), ("occ_hi", "<u8"), ("q_impr", "<f8"), ("w_dom_min", "<u4"),
+                      ("dom_empty", "<u4")])
+
+class Obs(C.Structure):
+    _fields_ = [("rows", C.c_int64), ("bins", C.c_int32), ("pad", C.c_int32)] + [
+        (k, C.c_double) for k in ("E", "E_err", "E_eta", "E_eta_err", "n", "n_err", "Q_raw", "Q_raw_err",
+                                  "Q_impr", "Q_impr_err", "kin", "kin_err", "n_v", "n_w", "w_dom_mean",
+                                  "w_dom_min", "dom_empty_frac")]
+
+
+SERIES = ("E", "E_eta", "n", "Q_raw", "Q_impr", "kin")
 
 DEFAULTS = dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1, dom_x=0, dom_y=0,
                 exchange_every=2, n_cycle=8, sub_block=0, init=1, init_seed=1, c_off=-1.0,
@@ -94,6 +104,11 @@ def load(build=True):
         "pmwa_batch_from_handles": (C.c_int, [vp, C.c_int32, vp, sz, vp, P(vp)]),
         "pmwa_profile_read": (C.c_int, [vp, vp, vp, C.c_int32]),
         "pmwa_profile_phases": (C.c_int, [vp, vp, C.c_int32]),
+        "pmwa_row_observables": (C.c_int, [P(Params), vp, C.c_int64, vp]),
+        "pmwa_observables": (C.c_int, [P(Params), vp, C.c_int64, C.c_int32, P(Obs)]),
+        "pmwa_n_cycle": (C.c_int, [P(Params), vp, C.c_int64, P(C.c_int32)]),
+        "pmwa_set_loop_caps": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "pmwa_philox_blocks": (C.c_int, [vp, C.c_int64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -450,20 +465,51 @@ class Batch:
             pass
 
 
+def _rows_arg(rows):
+    rows = np.ascontiguousarray(rows, dtype=ROW_DTYPE)
+    return rows, (rows.ctypes.data if len(rows) else None)
+
+
 def observables(rows, p):
-    """Physical observables per measured sweep (same definitions as the
-    paper's Step 6): E/N = (N_b C - n_v/beta)/N, density, <Q>/N raw and
-    improved, kinetic <b+_i b_j + h.c.> per bond."""
-    N = p.Lx * p.Ly
-    Nb = 2 * N
-    c_off = 0.5 * p.t if p.c_off < 0 else p.c_off
-    E = [p.V * (s & 1) * (s >> 1) - (p.mu / 4.0) * ((s & 1) + (s >> 1)) for s in range(4)]
-    Cc = max(E) + c_off
-    occ = rows["occ_lo"].astype(np.float64) + rows["occ_hi"].astype(np.float64) * 2.0 ** 64
-    out = dict(E=(Nb * Cc - rows["n_v"].astype(np.float64) / p.beta) / N,
-               n=occ / (2.0 ** 62 * N),
-               Q_raw=rows["n_w"].astype(np.float64) / (p.beta * p.eta * N),
-               Q_impr=rows["q_impr"] / (p.beta * p.eta * N))
-    if p.t > 0:
-        out["kin"] = rows["n_k"].astype(np.float64) / (p.beta * p.t * Nb)
+    """The Step-6 observables of every measured sweep (pmwa_row_observables):
+    a dict of arrays E, E_eta, n, Q_raw, Q_impr and, when t > 0, kin."""
+    rows, ptr = _rows_arg(rows)
+    out = np.zeros((len(rows), len(SERIES)), dtype=np.float64)
+    _check("pmwa_row_observables", load().pmwa_row_observables(C.byref(p), ptr, len(rows),
+                                                               out.ctypes.data if len(rows) else None))
+    d = {k: out[:, i].copy() for i, k in enumerate(SERIES)}
+    if p.t <= 0:
+        del d["kin"]
+    return d
+
+
+def summary(rows, p, bins=32):
+    """Means with binned standard errors and the worms-per-domain figures
+    (pmwa_observables), as a dict."""
+    rows, ptr = _rows_arg(rows)
+    o = Obs()
+    _check("pmwa_observables", load().pmwa_observables(C.byref(p), ptr, len(rows), bins, C.byref(o)))
+    return {k: getattr(o, k) for k, _ in Obs._fields_ if k != "pad"}
+
+
+def n_cycle(p, rows=None):
+    """N_cycle by the library's rule: from measured rows, else a priori."""
+    nc = C.c_int32()
+    if rows is None or len(rows) == 0:
+        _check("pmwa_n_cycle", load().pmwa_n_cycle(C.byref(p), None, 0, C.byref(nc)))
+    else:
+        rows, ptr = _rows_arg(rows)
+        _check("pmwa_n_cycle", load().pmwa_n_cycle(C.byref(p), ptr, len(rows), C.byref(nc)))
+    return nc.value
+
+
+def pmwa_set_loop_caps(h, zig_words=64, worm_tries=128):
+    _check("pmwa_set_loop_caps", load().pmwa_set_loop_caps(h, zig_words, worm_tries))
+
+
+def pmwa_philox_blocks(h, ctr_key):
+    """Device Philox4x32-10 of each row (c0, c1, c2, c3, k0, k1): an (n, 4) array."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((len(a), 4), dtype=np.uint32)
+    _check("pmwa_philox_blocks", load().pmwa_philox_blocks(h, len(a), a.ctypes.data, out.ctypes.data))
     return out

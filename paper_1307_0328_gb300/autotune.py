@@ -92,12 +92,12 @@ def tune(p):
     return dict(best)
 
 
-def n_cycle_rule(n_v, n_w):
-    """ceil(2 <n_v> / <n_w>), capped at 512 passes: an instance with almost no
-    worms (small beta eta on a small lattice) is far outside the regime of
-    O(10)-O(100) worms per domain that the method is made for, and more
-    passes would only repeat moves of the same few worms."""
-    return max(1, min(512, int(math.ceil(2.0 * float(n_v) / max(float(n_w), 1.0)))))
+def n_cycle_rule(p, rows):
+    """N_cycle of instance p from measured rows (pmwa_n_cycle: ceil(2 <n_v> /
+    <n_w>), capped at 512 passes for instances with almost no worms, which
+    lie far outside the O(10)-O(100) worms per domain the method is made
+    for)."""
+    return _lib.n_cycle(_lib.make_params(**{k: v for k, v in p.items() if k in _lib.DEFAULTS}), rows)
 
 
 def replica_set(n=512, seed=3):

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpmwa.so")
-SOURCES = ["pmwa_kernels.cu", "pmwa_tile.cu", "pmwa_green.cu", "pmwa_host.cpp"]
+SOURCES = ["pmwa_kernels.cu", "pmwa_tile.cu", "pmwa_green.cu", "pmwa_host.cpp", "pmwa_obs.cpp"]
 DEPS = SOURCES + ["pmwa_device.cuh", "pmwa_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17",

@@ -215,19 +215,21 @@ __device__ __forceinline__ bool xg_fix(int sigma, uint64_t I, GridScale XQ, uint
 struct ZigTab {
   const unsigned long long* K;   // [256] inner-rectangle threshold
   const unsigned long long* XF;  // [256] X[i] 2^58
+  int zcap;                      // words per deviate (64; Dev::zig_cap)
+  int wtries;                    // proposals of the Eq. 1 sampler (128; Dev::worm_tries)
 };
 constexpr int kZigBytes = 256 * 8 + 256 * 8;
 
 // copy the tables into `buf` (kZigBytes, 8-byte aligned); all threads
 // participate; the caller synchronises before use
-__device__ inline ZigTab zig_stage(unsigned char* buf) {
+__device__ inline ZigTab zig_stage(unsigned char* buf, int zcap = 64, int wtries = 128) {
   unsigned long long* K = reinterpret_cast<unsigned long long*>(buf);
   unsigned long long* XF = reinterpret_cast<unsigned long long*>(buf + 256 * 8);
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     K[i] = c_zK[i];
     XF[i] = c_zXF[i];
   }
-  return ZigTab{K, XF};
+  return ZigTab{K, XF, zcap, wtries};
 }
 
 __device__ __forceinline__ uint64_t zfix_add(uint64_t a, uint64_t b) { return (a > ~0ull - b) ? ~0ull : a + b; }
@@ -237,10 +239,10 @@ __device__ __forceinline__ uint64_t zfix_add(uint64_t a, uint64_t b) { return (a
 // uniform u from its high bits, the point x = u X[i] / 2^53 as the exact
 // product (u XF[i]) >> 53; accept when u < K[i]; strip 0 past R restarts at
 // R + new deviate; else a binary64 wedge test y < e^-x with a second word.
-// <= 64 words.
+// <= z.zcap (64) words.
 __device__ inline uint64_t zig_exp(const ZigTab& z, Stream& s, int* bad) {
   uint64_t acc = 0;
-  for (int tries = 0; tries < 64; ++tries) {
+  for (int tries = 0; tries < z.zcap; ++tries) {
     const uint64_t w = s.word();
     const unsigned i = unsigned(w & 255u);
     const uint64_t u = w >> 11;
@@ -285,7 +287,7 @@ template <int MAXN>
 __device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, GridScale SW, uint64_t SWI,
                             uint64_t* offs, int* bad) {
   if (M == 0) { if (sigma) { *bad = PMWA_EINVARIANT; return -1; } return 0; }
-  for (int tries = 0; tries < 128; ++tries) {
+  for (int tries = 0; tries < z.wtries; ++tries) {
     int n = 0;
     bool first = true;
     uint64_t pos = 0;

@@ -433,6 +433,8 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.bufk[0] = d.keyA; d.bufk[1] = d.keyB;
   d.bufc[0] = d.cntA; d.bufc[1] = d.cntB;
   d.exchange_every = p->exchange_every;
+  d.zig_cap = 64;
+  d.worm_tries = 128;
   h->err = d.err;
   h->phase = reinterpret_cast<unsigned long long*>(base + L.phase);
   d.phase_cycles = nullptr;
@@ -517,6 +519,28 @@ int pmwa_set_n_cycle(pmwa_handle* h, int32_t n_cycle) {
   if (!h || n_cycle < 0 || n_cycle > 4095) return PMWA_EINVAL;
   h->d.n_cycle = n_cycle;
   h->p.n_cycle = n_cycle;
+  return PMWA_OK;
+}
+
+int pmwa_set_loop_caps(pmwa_handle* h, int32_t zig_words, int32_t worm_tries) {
+  if (!h || zig_words < 1 || zig_words > 64 || worm_tries < 1 || worm_tries > 128) return PMWA_EINVAL;
+  h->d.zig_cap = zig_words;
+  h->d.worm_tries = worm_tries;
+  return PMWA_OK;
+}
+
+int pmwa_philox_blocks(pmwa_handle* h, int64_t n, const uint32_t* host_in, uint32_t* host_out) {
+  if (!h || n < 0 || (n && (!host_in || !host_out))) return PMWA_EINVAL;
+  if (n == 0) return PMWA_OK;
+  const size_t scratch = size_t(h->d.N) * size_t(h->d.cap) * sizeof(uint64_t);
+  if (size_t(n) > scratch / 40) return PMWA_EINVAL;
+  uint32_t* din = reinterpret_cast<uint32_t*>(h->d.keyB);
+  uint32_t* dout = din + size_t(n) * 6;
+  if (cudaMemcpyAsync(din, host_in, size_t(n) * 6 * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream) ||
+      launch_philox(din, dout, n, h->stream) ||
+      cudaMemcpyAsync(host_out, dout, size_t(n) * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream) ||
+      cudaStreamSynchronize(h->stream))
+    return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -609,6 +633,9 @@ int pmwa_measure(pmwa_handle* h, pmwa_row* rows, int64_t max_rows, int64_t* n_ro
   if (cudaStreamSynchronize(h->stream)) return PMWA_ECUDA;
   const int n = int(std::min<int64_t>(max_rows, h->rows_pending));
   if (n && cudaMemcpy(rows, h->d.rows, size_t(n) * sizeof(pmwa_row), cudaMemcpyDeviceToHost)) return PMWA_ECUDA;
+  // the device keeps the fewest worms per domain as its complement, so that
+  // zeroed rows and an atomic maximum give the minimum
+  for (int r = 0; r < n; ++r) rows[r].w_dom_min = ~rows[r].w_dom_min;
   const int rest = h->rows_pending - n;
   if (rest > 0) {
     std::vector<pmwa_row> tail(static_cast<size_t>(rest));
@@ -1271,13 +1298,23 @@ int pmwa_batch_sweep(pmwa_batch* b, int64_t n) {
   if (cudaMemcpy(b->base, b->hbase.data(), b->hbase.size() * sizeof(BatchBase), cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
   cudaEventRecord(b->ev0, b->stream);
+  // A launch that fails part-way leaves the work queued before it running:
+  // the instances' host state (sweep, rows, buffer parity) can then no longer
+  // be trusted, so wait for that work and mark every active instance broken
+  // (pmwa_import restores it).
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < b->n; ++i)
+      if (b->active[size_t(i)]) b->h[size_t(i)]->broken = true;
+    return code;
+  };
   if (b->graph && n % b->graph_sweeps == 0) {
     for (int64_t r = 0; r < n / b->graph_sweeps; ++r)
-      if (cudaGraphLaunch(b->graph, b->stream)) return PMWA_ECUDA;
+      if (cudaGraphLaunch(b->graph, b->stream)) return fail(PMWA_ECUDA);
   } else {
     for (int64_t it = 0; it < n; ++it) {
       const int rc = batch_launch_sweep(b, int(it), b->stream);
-      if (rc) return rc;
+      if (rc) return fail(rc);
     }
   }
   cudaEventRecord(b->ev1, b->stream);

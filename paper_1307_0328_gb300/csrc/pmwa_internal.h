@@ -74,6 +74,11 @@ struct Dev {
   uint64_t* bufk[2];
   uint32_t* bufc[2];
   int exchange_every;
+  // caps of the bounded device loops (a stuck loop ends in PMWA_ETIMEOUT):
+  // words of one exponential deviate (ziggurat) and proposals of the Eq. 1
+  // sampler; the deterministic specification fixes 64 and 128, smaller
+  // values exist only to exercise the error path
+  int zig_cap, worm_tries;
 };
 
 // Per-instance state at the start of a batched call: the sweep index, the
@@ -129,6 +134,8 @@ int prepare_boundary(int cap);
 int prepare_tile_batch(int cls, int smem);
 int launch_advance(BatchBase* base, int n, int S, void* stream);
 int launch_rho(const Dev& d, int K, double* out, void* stream);
+// n Philox4x32-10 blocks: in[6 j ..] = c0..c3, k0, k1; out[4 j ..] = output
+int launch_philox(const uint32_t* in, uint32_t* out, int64_t n, void* stream);
 // Invariant check of the current configuration (codes as PMWA_CHECK_*):
 // *out = ~0 when all hold, else min over failing sites of site << 4 | code.
 int launch_check(const Dev& d, unsigned long long* out, void* stream);

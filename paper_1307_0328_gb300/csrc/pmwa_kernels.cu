@@ -338,7 +338,7 @@ constexpr int kBoundaryWarps = 4;  // bonds (warps) per block
 __global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary(const __grid_constant__ Dev d, int dir) {
   extern __shared__ __align__(16) unsigned char bsm[];
   if (instance_failed(d.err)) return;
-  const ZigTab Z = zig_stage(bsm);
+  const ZigTab Z = zig_stage(bsm, d.zig_cap, d.worm_tries);
   __syncthreads();
   const int wid = threadIdx.x >> 5;
   uint64_t* stage = reinterpret_cast<uint64_t*>(bsm + kZigBytes) + size_t(2 * wid) * d.cap;
@@ -357,8 +357,10 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary_batch(const De
   const BatchBase bb = base[w.x];
   if (!bb.active) return;
   if (threadIdx.x == 0) sd = at_iteration(devs[w.x], bb, it);
-  const ZigTab Z = zig_stage(bsm);
+  ZigTab Z = zig_stage(bsm);
   __syncthreads();
+  Z.zcap = sd.zig_cap;
+  Z.wtries = sd.worm_tries;
   if (instance_failed(sd.err)) return;
   if (sd.ndom < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
   const int wid = threadIdx.x >> 5;
@@ -495,6 +497,25 @@ int launch_green(int Lx, int Ly, int K, int rmax, const double* rho, double* sum
   const int N = Lx * Ly;
   const int bx = N < 256 * 152 ? blocks_for(N, 256) : 152;
   k_green<<<dim3(bx, rmax + 1), 256, 0, cudaStream_t(stream)>>>(Lx, Ly, K, rmax, rho, sums);
+  return int(cudaGetLastError());
+}
+
+// The generator every kernel draws from, applied to listed counters and keys
+// (compared on the host with published known-answer vectors).
+__global__ void k_philox(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, long long n) {
+  const long long j = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t* c = in + 6 * j;
+  const P4 b = philox(c[0], c[1], c[2], c[3], c[4], c[5]);
+  out[4 * j] = b.x;
+  out[4 * j + 1] = b.y;
+  out[4 * j + 2] = b.z;
+  out[4 * j + 3] = b.w;
+}
+
+int launch_philox(const uint32_t* in, uint32_t* out, int64_t n, void* stream) {
+  if (n <= 0) return 0;
+  k_philox<<<blocks_for(n, 128), 128, 0, cudaStream_t(stream)>>>(in, out, (long long)n);
   return int(cudaGetLastError());
 }
 

@@ -540,7 +540,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   Misc* misc = T.misc;
 
   long long tclk = clock64();
-  const ZigTab Z = zig_stage(sm + d.sm_zig);
+  const ZigTab Z = zig_stage(sm + d.sm_zig, d.zig_cap, d.worm_tries);
   for (int k = tid; k < 256; k += NT) T.th[k] = d.TH[k];
   if (tid == 0) { misc->pool_used = 0; misc->nworms = 0; misc->err = 0; misc->where = 0; }
   // per-site tables: bond partners by leg tag, sub-blocks by offset pattern
@@ -926,6 +926,13 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         atomicAdd(&r->q_impr, q);
       }
       if (dom == 0 && tid == 0) d.rows[d.row].sweep = d.sweep;
+      if (tid == 0) {
+        // worms per domain: the fewest (kept as a complement, so that the
+        // zeroed row and an atomic maximum give the minimum) and the empty ones
+        pmwa_row* r = d.rows + d.row;
+        atomicMax(&r->w_dom_min, ~uint32_t(nw));
+        if (nw == 0) atomicAdd(&r->dom_empty, 1u);
+      }
     }
     __syncthreads();
     phase_tick(d, 4, tclk);

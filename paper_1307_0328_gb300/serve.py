@@ -12,7 +12,6 @@ runs beside it: every random draw is keyed by the job's own seed, replica id,
 sweep and unit.
 """
 import ctypes as C
-import math
 import time
 
 import numpy as np
@@ -38,14 +37,9 @@ class Job:
 
 
 def n_cycle_estimate(p):
-    """N_cycle = 2 <n_v> / <n_w> with the a-priori estimates <n_v> = N_b beta
-    (d_mean + t/2) and <n_w> = beta eta N / 2 (order parameter ~ 1/2), capped
-    as in the tuner; used when a job names no N_cycle."""
-    V, mu, t, eta = p.get("V", 0.0), p.get("mu", 0.0), p.get("t", 1.0), p.get("eta", 0.1)
-    E = [V * (s & 1) * (s >> 1) - mu / 4.0 * ((s & 1) + (s >> 1)) for s in range(4)]
-    C_ = max(E) + (t / 2 if p.get("c_off", -1.0) < 0 else p["c_off"])
-    d_mean = sum(C_ - e for e in E) / 4.0
-    return max(1, min(512, int(math.ceil(2.0 * 2.0 * (d_mean + t / 2.0) / (eta / 2.0)))))
+    """The library's a-priori N_cycle (pmwa_n_cycle without rows) for a job
+    that names none."""
+    return _lib.n_cycle(_lib.make_params(**{k: v for k, v in p.items() if k in _lib.DEFAULTS}))
 
 
 class Server:

@@ -68,3 +68,69 @@ def test_tile_plan_sizes_from_the_hint_and_keeps_occupancy():
     assert small["oldcap"] >= small["legcap"] > 12 * 64
     with pytest.raises(P.PmwaError):
         P.pmwa_tile_plan(**kw, legs_hint=-1)
+
+
+def _oracle_rows(**kw):
+    o = O.Oracle(**kw)
+    o.sweep(96)
+    return o.rows()
+
+
+@pytest.mark.parametrize("kw", [dict(Lx=4, Ly=4, beta=2.0, eta=0.2, n_cycle=6, seed=3),
+                                dict(Lx=8, Ly=4, beta=1.0, eta=0.3, V=1.0, mu=0.6, t=0.7, dom_x=4,
+                                     dom_y=2, n_cycle=4, seed=5),
+                                dict(Lx=4, Ly=4, beta=1.0, eta=0.4, t=0.0, mu=0.5, n_cycle=3, seed=8)])
+def test_step6_observables_follow_their_definitions(kw):
+    """pmwa_row_observables / pmwa_observables (host code of the library)
+    against the Step-6 definitions restated here from the model (Eq. 5 per
+    bond, C = max E + c_off) and a plain binning, on rows of the oracle."""
+    rows = _oracle_rows(**kw)
+    p = P.make_params(**kw)
+    N = kw["Lx"] * kw["Ly"]
+    t, V, mu, beta, eta = kw.get("t", 1.0), kw.get("V", 0.0), kw.get("mu", 0.0), kw["beta"], kw["eta"]
+    Es = [V * (s & 1) * (s >> 1) - mu / 4.0 * ((s & 1) + (s >> 1)) for s in range(4)]
+    C = max(Es) + t / 2.0
+    nv = rows["n_v"].astype(float)
+    occ = rows["occ_lo"].astype(float) + rows["occ_hi"].astype(float) * 2.0 ** 64
+    Q = rows["q_impr"] / (beta * eta * N)
+    want = dict(E=(2 * N * C - nv / beta) / N, n=occ / 2.0 ** 62 / N,
+                Q_raw=rows["n_w"].astype(float) / (beta * eta * N), Q_impr=Q)
+    want["E_eta"] = want["E"] - eta * Q
+    if t > 0:
+        want["kin"] = rows["n_k"].astype(float) / (beta * t * 2 * N)
+    got = P.observables(rows, p)
+    assert set(got) == set(want)
+    for k in want:
+        assert np.allclose(got[k], want[k], rtol=1e-13, atol=1e-13), k
+    s = P.summary(rows, p, bins=8)
+    m = len(rows) // 8
+    for k in want:
+        b = want[k][: 8 * m].reshape(8, m).mean(axis=1)
+        assert s[k] == pytest.approx(b.mean(), rel=1e-12, abs=1e-13), k
+        assert s[k + "_err"] == pytest.approx(b.std(ddof=1) / np.sqrt(8), rel=1e-9, abs=1e-15), k
+    nd = (kw["Lx"] // kw.get("dom_x", kw["Lx"])) * (kw["Ly"] // kw.get("dom_y", kw["Ly"]))
+    used = rows[: 8 * m]
+    assert s["w_dom_mean"] == pytest.approx(used["n_w"].mean() / nd, rel=1e-12)
+    assert s["w_dom_min"] == used["w_dom_min"].min()
+    assert s["dom_empty_frac"] == pytest.approx(used["dom_empty"].sum() / (len(used) * nd), rel=1e-12, abs=0)
+    if nd == 1:  # one domain: its worms are all worms
+        assert np.array_equal(rows["w_dom_min"], rows["n_w"])
+        assert np.array_equal(rows["dom_empty"], (rows["n_w"] == 0).astype(np.uint32))
+    with pytest.raises(P.PmwaError):
+        P.summary(rows[:1], p, bins=2)
+
+
+def test_n_cycle_rule():
+    """N_cycle = ceil(2 <n_v> / <n_w>) over the given rows, at least 1 and at
+    most 512; the a-priori form from <n_v> = N_b beta (d_mean + t/2) and
+    <n_w> = beta eta N / 2."""
+    kw = dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=6, seed=1)
+    rows = _oracle_rows(**kw)
+    p = P.make_params(**kw)
+    half = rows[len(rows) // 2:]
+    want = int(np.ceil(2.0 * half["n_v"].mean() / max(half["n_w"].mean(), 1.0)))
+    assert P.n_cycle(p, half) == max(1, min(512, want))
+    # a priori at V = mu = 0, t = 1: d(s) = t/2 for every s, so
+    # N_cycle = ceil(2 * 2N beta (1/2 + 1/2) / (beta eta N / 2)) = ceil(8 / eta)
+    assert P.n_cycle(p) == int(np.ceil(8.0 / 0.2))
+    assert P.n_cycle(P.make_params(**dict(kw, eta=0.001))) == 512

@@ -18,6 +18,8 @@ from oracle import oracle as O  # noqa: E402
 import paper_1307_0328_gb300 as P  # noqa: E402
 
 REL = 1e-12
+# integer fields of a measurement row, compared exactly
+ROW_FIELDS = ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi", "w_dom_min", "dom_empty")
 
 GEOMS = [
     # the 8x8, beta t = 2, eta = 0.2 workload, one domain
@@ -90,7 +92,7 @@ def test_steps_bit_exact(kw):
             _same(g.export(), o.export(), "Steps 3..%d at sweep %d" % (stop, s))
         ro, rg = o.rows(), g.rows()
         assert len(ro) == 1 and len(rg) == 1
-        for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+        for f in ROW_FIELDS:
             assert ro[f][0] == rg[f][0], f
         assert rg["q_impr"][0] == pytest.approx(ro["q_impr"][0], rel=REL)
         o.sweep_index = s + 1
@@ -105,7 +107,7 @@ def test_sweeps_bit_exact(kw):
         g.sweep(1)
         _same(g.export(), o.export(), "after sweep %d" % s)
     ro, rg = o.rows(), g.rows()
-    for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+    for f in ROW_FIELDS:
         assert np.array_equal(ro[f], rg[f]), f
     assert np.allclose(rg["q_impr"], ro["q_impr"], rtol=REL, atol=0)
 
@@ -226,3 +228,82 @@ def test_full_size_256x256_bit_exact(legs_hint):
         for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
             assert np.array_equal(a[f], b[f]), f
         assert np.allclose(a["q_impr"], b["q_impr"], rtol=REL, atol=0)
+
+
+# Known-answer vectors of Philox4x32-10 published with Random123 (Salmon et
+# al., SC'11): counter words, key words, output words.
+PHILOX_KAT = [
+    ((0, 0, 0, 0), (0, 0), (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff,) * 4, (0xffffffff,) * 2, (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+def test_device_philox_known_answers():
+    """The device generator that every kernel draws from reproduces the
+    published known-answer vectors, and agrees with the oracle's on a sweep
+    of counters and keys."""
+    g = P.Sim(Lx=4, Ly=4, beta=1.0, eta=0.2)
+    got = P.pmwa_philox_blocks(g.h, [list(c) + list(k) for c, k, _ in PHILOX_KAT])
+    for row, (_, _, want) in zip(got, PHILOX_KAT):
+        assert [int(x) for x in row] == list(want)
+    rng = np.random.default_rng(5)
+    ck = rng.integers(0, 2 ** 32, size=(512, 6), dtype=np.uint64).astype(np.uint32)
+    dev = P.pmwa_philox_blocks(g.h, ck)
+    for j in range(len(ck)):
+        assert np.array_equal(dev[j], O.philox(ck[j, :4], ck[j, 4:])), j
+
+
+def test_config4_shape_in_small_bit_exact():
+    """The 2048x2048, beta t = 16 workload in small: 32x32 sites in 2x2
+    domains of 16x16 sites, Step 2 every 2 sweeps, 2x2 sub-blocks, eta = 0.1.
+    After the chain warms up, every domain holds more worms than the CTA has
+    threads (about 400 per domain), so Step 5 groups the worms with warp 0's
+    walk instead of the block-wide passes.  Bit-exact after each of 36
+    sweeps."""
+    kw = dict(Lx=32, Ly=32, beta=16.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=20,
+              exchange_every=2, seed=13, init=1, init_seed=11)
+    g, o = _pair(kw)
+    for s in range(36):
+        o.sweep(1)
+        g.sweep(1)
+        _same(g.export(), o.export(), "after sweep %d" % s)
+    ro, rg = o.rows(), g.rows()
+    for f in ROW_FIELDS:
+        assert np.array_equal(ro[f], rg[f]), f
+    assert np.allclose(rg["q_impr"], ro["q_impr"], rtol=REL, atol=0)
+    assert ro["w_dom_min"][-10:].min() > 256  # the many-worm grouping did run
+
+
+def test_full_size_thermalised_bit_exact():
+    """The 256x256, beta t = 4 workload in the launch configuration of the
+    benchmark (16x16-site domains, K = 2, 2x2 sub-blocks, N_cycle = 43, a leg
+    hint of 18 per site) from a thermalised configuration: the oracle
+    thermalises the same parameters on 64x64 for 120 sweeps (about 17 vertex
+    legs per site, the benchmark's density), the configuration is repeated
+    4 x 4 times, and two sweeps from it must be bit-exact."""
+    small = dict(Lx=64, Ly=64, beta=4.0, eta=0.1, dom_x=16, dom_y=16, sub_block=2, n_cycle=43,
+                 exchange_every=2, seed=7, init=1, init_seed=7)
+    o = O.Oracle(**small)
+    o.sweep(120)
+    r = o.rows()
+    assert 2.0 * r["n_v"][-20:].mean() / (64 * 64) > 15.0  # thermalised leg density
+    big = O.tile_config(o.export(), 64, 4)
+    kw = dict(small, Lx=256, Ly=256, seed=9)
+    ob = O.Oracle(**kw)
+    ob.import_(big)
+    ob.sweep_index = 120
+    assert ob.check() == 0
+    g = P.Sim(legs_hint=18, **kw)
+    g.import_(big)
+    g.sweep_index = 120
+    for s in range(2):
+        ob.sweep(1)
+        g.sweep(1)
+        _same(g.export(), ob.export(), "after sweep %d" % s)
+    ro, rg = ob.rows(), g.rows()
+    for f in ROW_FIELDS:
+        assert np.array_equal(ro[f], rg[f]), f
+    assert np.allclose(rg["q_impr"], ro["q_impr"], rtol=REL, atol=0)
+    assert 2.0 * ro["n_v"].mean() / (256 * 256) > 15.0

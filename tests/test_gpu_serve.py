@@ -1,7 +1,8 @@
 """Serving loop: jobs that arrive while others run are admitted as memory and
 slots free up, advance together with the resident ones, and each job's
 result is exactly the one it has when run alone (bit-exact integer counters,
-FP64 estimator within 1e-12)."""
+FP64 estimator within 1e-12) and the one the CPU oracle computes for the same
+job (the same parameters, domains, sub-blocks and N_cycle)."""
 import numpy as np
 import pytest
 
@@ -10,7 +11,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 import paper_1307_0328_gb300 as P  # noqa: E402
+from oracle import oracle as O  # noqa: E402
 from paper_1307_0328_gb300 import serve  # noqa: E402
+
+ROW_FIELDS = ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi", "w_dom_min", "dom_empty")
 
 
 def _jobs():
@@ -48,6 +52,14 @@ def test_each_job_same_alone_and_in_the_mix():
         alone = P.Sim(**j.params)
         alone.sweep(j.sweeps)
         want = alone.rows()
-        for f in ("sweep", "n_v", "n_k", "n_w", "occ_lo", "occ_hi"):
+        for f in ROW_FIELDS:
             assert np.array_equal(got[f], want[f]), (j.id, f)
         assert np.allclose(got["q_impr"], want["q_impr"], rtol=1e-12, atol=0), j.id
+        # the served job against the oracle run of the same job
+        o = O.Oracle(**j.params)
+        o.sweep(j.sweeps)
+        ref = o.rows()
+        for f in ROW_FIELDS:
+            assert np.array_equal(got[f], ref[f]), (j.id, f, "oracle")
+        assert np.allclose(got["q_impr"], ref["q_impr"], rtol=1e-12, atol=0), (j.id, "oracle")
+        assert np.array_equal(alone.export(), o.export()), (j.id, "configuration")

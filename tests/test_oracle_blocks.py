@@ -20,6 +20,26 @@ def _philox_words(n, key=(7, 9), unit=3):
     return out
 
 
+# Known-answer vectors of Philox4x32-10 published with the Random123 library
+# of Salmon, Moraes, Dror and Shaw (SC'11): (counter, key) -> output words.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,want", PHILOX_KAT)
+def test_philox_known_answers(ctr, key, want):
+    """The oracle's Philox4x32-10 reproduces the published known-answer
+    vectors: a wrong multiplier, Weyl constant, round count or word order
+    fails here even though it would keep the output uniform."""
+    assert [int(x) for x in O.philox(list(ctr), list(key))] == list(want)
+
+
 def test_philox_uniform_bytes_and_bits():
     """Output bytes are uniform (chi^2) and every output bit is fair."""
     w = _philox_words(20000)

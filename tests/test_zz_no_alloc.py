@@ -30,6 +30,19 @@ def test_static_scratch_rho_matches_arena_rho_twice():
         assert got.shape == want.shape
         assert np.all(np.isfinite(got)), call
         assert np.allclose(got, want, rtol=1e-12, atol=0), call
+    # after the calls above (the first one looked the array up), a call
+    # changes neither the device's free memory nor torch's allocator
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        P.pmwa_rho_slices_static(g.h, N, K)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    st1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for k in ("allocated_bytes.all.current", "reserved_bytes.all.current", "num_alloc_retries"):
+        assert st1.get(k, 0) == st0.get(k, 0), k
     # requests beyond the fixed size are refused with a clear status
     with pytest.raises(P.PmwaError) as e:
         P.pmwa_rho_slices_static(g.h, N, (1 << 20) // N + 1)

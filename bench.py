@@ -472,18 +472,35 @@ def large_leg(P, args, flush):
     wl = "2048x2048_bt16"
     kw = dict(WORKLOADS[wl])
     sim, nc, kw = pilot_sim(P, kw, args.large_pilot)
-    sim.sweep(args.warmup)
-    sim.rows()
-    P.pmwa_profile(sim.h, True)
-    P.pmwa_profile_read(sim.h)
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start()
-    for _ in range(args.large_steps):
-        sim.sweep(1)
-    prof = P.pmwa_profile_read(sim.h)
-    P.pmwa_profile(sim.h, False)
-    clk = clocks.stop()
-    rows = sim.rows()
+    snap, s_idx = sim.export(), sim.sweep_index
+
+    def timed(sim):
+        sim.sweep(args.warmup)
+        sim.rows()
+        P.pmwa_profile(sim.h, True)
+        P.pmwa_profile_read(sim.h)
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
+        for _ in range(args.large_steps):
+            sim.sweep(1)
+        prof = P.pmwa_profile_read(sim.h)
+        P.pmwa_profile(sim.h, False)
+        return prof, clocks.stop(), sim.rows()
+
+    try:
+        prof, clk, rows = timed(sim)
+    except P.PmwaError as e:
+        # the chain at beta t = 16 can outgrow a leg table sized from the
+        # pilot: start again from the pilot's configuration with the
+        # a-priori table
+        if e.status != P.PMWA_ECAPACITY:
+            raise
+        sim.close()
+        kw["legs_hint"] = 0
+        sim = P.Sim(n_cycle=nc, **kw)
+        sim.import_(snap)
+        sim.sweep_index = s_idx
+        prof, clk, rows = timed(sim)
     kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
     t = prof["sweep"][0] / 1000.0
     peak, which = peaks()

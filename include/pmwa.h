@@ -86,7 +86,12 @@ typedef struct {
                                leaves room to stage the domain's configuration in
                                shared memory; 0 = the bound.  Too small a hint
                                makes a sweep return PMWA_ECAPACITY.            */
-  int32_t  reserved[4];     /* must be 0                                          */
+  int32_t  dom_tau;         /* temporal domains N_beta (Supplement S-II), 0..64;
+                               0 and 1 mean one domain spanning beta.  With
+                               N_beta > 1, boundary k sits at the grid point
+                               floor(k 2^59 / N_beta) of every site; Step 1
+                               (Eq. 3) runs when sweep % K == 0, before Step 2 */
+  int32_t  reserved[3];     /* must be 0                                          */
 } pmwa_params;
 
 /* One row per sweep (Step 6 measurement after Step 5). */
@@ -99,7 +104,7 @@ typedef struct {
   uint64_t occ_hi;  /*   beta / 2^62, as a 128-bit integer (hi:lo)              */
   double   q_impr;  /* Supplement S-I: sum over intervals of x g_sigma(x),
                        x = I eta, g_0 = tanh, g_1 = coth; <Q> = q_impr/(beta eta) */
-  uint32_t w_dom_min; /* fewest worms held by one domain after Step 5 (the
+  uint32_t w_dom_min; /* fewest worms held by one (space-time) domain after Step 5 (the
                          paper's health figure of O(10)-O(100) worms per domain,
                          discussion of Fig. 3)                                  */
   uint32_t dom_empty; /* domains without a worm after Step 5                   */
@@ -119,15 +124,29 @@ size_t pmwa_footprint(const pmwa_params* p);
 int pmwa_create(const pmwa_params* p, void* dev_arena, size_t arena_bytes,
                 void* stream, pmwa_handle** out);
 
-/* Run n_sweeps MC steps (pseudo code Steps 1-6; Step 1 is absent because
-   every domain spans the whole of beta).  One measurement row per sweep.
-   PMWA_EROWS if the rows would not fit: drain them with pmwa_measure first. */
+/* Run n_sweeps MC steps (pseudo code Steps 1-6; Step 1 only with temporal
+   domains, dom_tau > 1).  One measurement row per sweep.
+   PMWA_EROWS if the rows would not fit: drain them with pmwa_measure first.
+   With temporal domains the worms of Step 5 turn round at the temporal
+   boundaries and every leg of Eq. 2 ends there; Step 4 draws the worms of
+   the intervals delimited by the vertex legs and the boundaries; Step 2's
+   legs end there too; and the Step-5 schedule runs each sub-block of each
+   temporal slab as its own chain (Philox unit = sub-block id * N_beta +
+   slab).  The Step-6 estimator q_impr sums over those intervals; the slice
+   estimators (pmwa_rho_*, pmwa_green*, pmwa_npoint*) use the intervals
+   between vertex legs; both are unbiased. */
 int pmwa_sweep(pmwa_handle* h, int64_t n_sweeps);
 
-/* Fine-grained steps, for parity checks: Step 2 (+ Step 3 on the boundary
-   bonds) regardless of the sweep index; and Steps 3..stop_after of one sweep
-   (stop_after in 3..6; 6 also records a row).  Neither advances the sweep
-   index. */
+/* Fine-grained steps, for parity checks: Step 1 (temporal boundaries,
+   Eq. 3; nothing with one temporal domain) and Step 2 (+ Step 3 on the
+   boundary bonds) regardless of the sweep index; and Steps 3..stop_after of
+   one sweep (stop_after in 3..6; 6 also records a row).  None advances the
+   sweep index.  Step 1: every boundary k of a site, in order k = 0, 1, ...,
+   takes the new state s' with probability f_{q s'}(I1) f_{s' p}(I2) /
+   f_{q p}(I) (I2 from the nearest vertex leg or boundary below, state p above
+   it; I1 up to the nearest one above, state q below it; worms ignored), and
+   the worms of I2 and I1 are drawn anew (Eq. 1); one warp per site. */
+int pmwa_temporal(pmwa_handle* h);
 int pmwa_boundary(pmwa_handle* h);
 int pmwa_tile(pmwa_handle* h, int32_t stop_after);
 
@@ -219,6 +238,29 @@ int pmwa_rho_alpha(pmwa_handle* h, int32_t K, double* host_rho, int32_t* host_iv
    site plus the sums fit in 8 cap bytes per site (K <= cap / 2 about; cap
    from pmwa_slot_capacity).  Synchronous. */
 int pmwa_green_tau(pmwa_handle* h, int32_t K, int32_t rmax, double* host_g);
+
+/* Supplement S-I n-point functions resolved by the component of Q at
+   arbitrary times, for listed tuples of points: tuple j holds n points
+   (site s, slice k in 0..K-1, component a: 0 = b, 1 = b+) at
+   host_pts[(j n + c) 3 + 0..2] (row-major, m tuples, caller-owned), and
+     host_out[j] = < T Q_a1(X_1) ... Q_an(X_n) >
+                 = eta^-n < prod over intervals of the joint density of the
+                   points on that interval >,
+   averaged over the K cyclic shifts of all slices (X_c at tau = ((k_c + t)
+   mod K) beta / K, t = 0..K-1; the thermal state is invariant under the
+   shift).  Points on different intervals multiply their densities (the
+   densities of pmwa_rho_alpha); several points on one interval take all
+   their operators inside the interval's matrix element,
+     eta^g <q| e^{I_g Q} Q_a[g-1] ... e^{I_1 Q} Q_a[0] e^{I_0 Q} |p> / <q| e^{I Q} |p>,
+   in time order going up from the lower leg (the case the paper leaves to
+   later work; the same derivation as the single point with g delta
+   functions), and on a site without legs the cyclic trace.  The product
+   over the groups runs in order of first appearance, the sum over shifts in
+   order, then / K / eta^n.  PMWA_EINVAL for a site or slice out of range, a
+   component other than 0 or 1, or one (site, slice) named twice in a tuple;
+   1 <= n <= 16, 1 <= K <= 2^20.  Scratch: the idle next-configuration slots
+   (12 n + 8 bytes a tuple, in chunks).  Synchronous. */
+int pmwa_npoint_alpha(pmwa_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* host_pts, double* host_out);
 
 /* Canonical configuration (format in the header comment) to / from host
    memory.  pmwa_export_bytes gives the size; pmwa_import checks the
@@ -332,12 +374,12 @@ int32_t pmwa_tile_smem(const pmwa_params* p);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
    every launch (enable = 1 turns it on, 0 off and clears).  pmwa_profile_read
-   synchronises and returns, for kernel k = 0 boundary, 1 vertex candidates,
-   2 merge + worm creation, 3 scattering, 4 measurement, 5 rho slices, and
-   6 the device span of each whole sweep of pmwa_sweep, the summed device
+   synchronises and returns, for kernel k = 0 spatial boundary (Step 2),
+   1 sweep kernel (Steps 3-6), 2 temporal boundaries (Step 1), 5 rho slices,
+   and 6 the device span of each whole sweep of pmwa_sweep, the summed device
    milliseconds ms[k] and the number of launches[k] since the last read
-   (n >= 7 entries each), then clears them.  No paper counterpart:
-   measurement plumbing. */
+   (n >= 7 entries each; 3 and 4 are unused), then clears them.  No paper
+   counterpart: measurement plumbing. */
 int pmwa_profile(pmwa_handle* h, int32_t enable);
 int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
 /* SM clock cycles spent by the sweep kernel in each of its phases, summed
@@ -378,7 +420,8 @@ int pmwa_row_observables(const pmwa_params* p, const pmwa_row* rows, int64_t n_r
    the paper uses to judge a decomposition (O(10)-O(100) worms per domain and a
    small chance of an empty domain; discussion of Fig. 3): the mean over the
    used rows of n_w / domains, the smallest w_dom_min, and the fraction of
-   (domain, sweep) pairs without a worm.  Domains = (Lx / dom_x)(Ly / dom_y).
+   (domain, sweep) pairs without a worm.  Domains = (Lx / dom_x)(Ly / dom_y)
+   times the temporal domains.
    2 <= bins <= n_rows; PMWA_EINVAL otherwise or for invalid parameters. */
 typedef struct {
   int64_t rows;                 /* rows used                                   */

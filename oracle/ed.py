@@ -139,6 +139,39 @@ def green_tau(Lx, Ly, beta, t, V, mu, eta, K, rmax):
     return G
 
 
+def correlator(Lx, Ly, beta, t, V, mu, eta, ops):
+    """Exact time-ordered correlator of H_eta,
+        < T prod_k Q_ak(tau_k) >  with Q_0 = b_i, Q_1 = b+_i at site i,
+    ops = [(site, tau, a), ...] with 0 <= tau < beta (operators at equal
+    times must sit on different sites, where they commute):
+        Tr[e^{-(beta - tau_n) H} O_n e^{-(tau_n - tau_{n-1}) H} ... O_1 e^{-tau_1 H}] / Z
+    for the operators sorted by time, tau_1 <= ... <= tau_n, H = H_eta, from
+    the eigendecomposition (energies shifted by their minimum)."""
+    N = Lx * Ly
+    H, Q = hamiltonians(Lx, Ly, t, V, mu, eta)
+    w, U = np.linalg.eigh(H - eta * Q)
+    w = w - w.min()
+    Z = np.exp(-beta * w).sum()
+    dim, states, occ = _ops(N)
+    order = sorted(range(len(ops)), key=lambda k: ops[k][1])
+    M = np.diag(np.exp(-ops[order[0]][1] * w))           # e^{-tau_1 H}
+    prev = ops[order[0]][1]
+    for j, k in enumerate(order):
+        i, tau, a = ops[k]
+        if j:
+            M = np.diag(np.exp(-(tau - prev) * w)) @ M
+            prev = tau
+        b = np.zeros((dim, dim))
+        if a == 0:   # b_i: 1 -> 0
+            src = states[((states >> i) & 1) == 1]
+        else:        # b+_i: 0 -> 1
+            src = states[((states >> i) & 1) == 0]
+        b[src ^ (1 << i), src] = 1.0
+        M = (U.T @ b @ U) @ M
+    M = np.diag(np.exp(-(beta - prev) * w)) @ M
+    return float(np.trace(M) / Z)
+
+
 def single_site(beta, mu, eta):
     """Closed form at t = 0, V = 0, where the sites decouple.  Each site is
     h = -mu n - eta (b + b+) = -mu/2 + (mu/2) sz - eta sx (sz = 1 - 2n), a spin

@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("exchange_every", C.c_int32), ("n_cycle", C.c_int32),
                 ("sub_block", C.c_int32), ("init", C.c_int32),
                 ("init_seed", C.c_uint64), ("c_off", C.c_double),
-                ("replica", C.c_uint32)]
+                ("replica", C.c_uint32), ("dom_tau", C.c_int32), ("vertex_window", C.c_double)]
 
 
 class Row(C.Structure):
@@ -54,7 +54,7 @@ ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", 
 
 DEFAULTS = dict(Lx=4, Ly=4, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1,
                 dom_x=0, dom_y=0, exchange_every=2, n_cycle=8, sub_block=0,
-                init=1, init_seed=1, c_off=-1.0, replica=0)
+                init=1, init_seed=1, c_off=-1.0, replica=0, dom_tau=1, vertex_window=0.0)
 
 _lib = None
 
@@ -68,6 +68,8 @@ def lib():
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_sweep.argtypes = [C.c_void_p, C.c_int64]
         L.or_boundary.argtypes = [C.c_void_p]
+        L.or_temporal.argtypes = [C.c_void_p]
+        L.or_pdom.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_double, C.c_void_p]
         L.or_tile.argtypes = [C.c_void_p, C.c_int]
         L.or_check.argtypes = [C.c_void_p]
         L.or_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
@@ -82,6 +84,10 @@ def lib():
         L.or_rho_slices.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
         L.or_rho_alpha.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
         L.or_rho_pair.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.or_npoint_alpha.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]
+        L.or_interval_density.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_double, C.c_double]
+        L.or_interval_density.restype = C.c_double
         L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_exp_det.argtypes = [C.c_double]
         L.or_exp_det.restype = C.c_double
@@ -106,6 +112,8 @@ def make_params(**kw):
         d["dom_x"] = d["Lx"]
     if not d["dom_y"]:
         d["dom_y"] = d["Ly"]
+    if not d["dom_tau"]:
+        d["dom_tau"] = 1
     return Params(**d)
 
 
@@ -133,6 +141,9 @@ class Oracle:
 
     def boundary(self):
         self._ok(lib().or_boundary(self.h), "or_boundary")
+
+    def temporal(self):
+        self._ok(lib().or_temporal(self.h), "or_temporal")
 
     def tile(self, stop_after=6):
         self._ok(lib().or_tile(self.h, stop_after), "or_tile")
@@ -214,6 +225,16 @@ class Oracle:
         self._ok(lib().or_rho_pair(self.h, K, out.ctypes.data), "or_rho_pair")
         return out
 
+    def npoint_alpha(self, K, pts):
+        """<Q_a1(X_1) ... Q_an(X_n)> for each tuple of n points (site, slice,
+        component) in pts (m, n, 3), averaged over the K cyclic shifts of the
+        slices: an array (m,)."""
+        a = np.ascontiguousarray(pts, dtype=np.int32)
+        m, n = a.shape[0], a.shape[1]
+        out = np.zeros(m)
+        self._ok(lib().or_npoint_alpha(self.h, K, n, m, a.ctypes.data, out.ctypes.data), "or_npoint_alpha")
+        return out
+
     def green_tau(self, K, rmax):
         """Supplement S-I: G_d(r, dk) = <b_{i + r e_d}(tau_k + dk beta/K) b+_i(tau_k)>
         estimated as the average over sites i and slices k of the two-point
@@ -273,6 +294,21 @@ def philox(ctr, key):
     o = np.zeros(4, dtype=np.uint32)
     lib().or_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
     return o
+
+
+def interval_density(p, q, M, M1, a, eta, XW):
+    """Joint density of the operators Q_a[j] at the points with M1[j] worm
+    points below them on one interval (p < 0: a site without legs, M1 = pk)."""
+    m1 = np.ascontiguousarray(M1, dtype=np.uint64)
+    aa = np.ascontiguousarray(a, dtype=np.int32)
+    return lib().or_interval_density(p, q, M, len(m1), m1.ctypes.data, aa.ctypes.data, eta, XW)
+
+
+def pdom(p, q, M1, M2, XW):
+    """Step 1's probabilities (P(s'=0), P(s'=1)) of the new boundary state."""
+    out = np.zeros(2)
+    lib().or_pdom(p, q, M1, M2, XW, out.ctypes.data)
+    return out
 
 
 def zig_tables():

@@ -31,7 +31,7 @@ typedef unsigned __int128 u128;
 #define TWO62 ((uint64_t)1 << 62)
 #define TWO32 ((uint64_t)1 << 32)
 
-enum { PH_INIT = 1, PH_BX = 2, PH_BY = 3, PH_VERTEX = 4, PH_REGEN = 5, PH_SCATTER = 6 };
+enum { PH_INIT = 1, PH_BX = 2, PH_BY = 3, PH_VERTEX = 4, PH_REGEN = 5, PH_SCATTER = 6, PH_TEMPORAL = 7 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
@@ -414,6 +414,41 @@ static uint64_t wkey(uint64_t m, int dir, int above) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Temporal domains (Supplement S-II: the space-time is cut into N_beta
+   slabs along imaginary time; Step 1 and Eq. 3).  With N_beta = dom_tau > 1
+   boundary k (k = 0..N_beta-1) sits on every site at the grid point
+   m_k = floor(k 2^59 / N_beta) with the otherwise unused tag 6, so its time
+   point tb_pk(k) = m_k << 3 | 6 is distinct from every vertex leg and worm.
+   A boundary is no event of the configuration: the state there is the state
+   of the worldline at that point, which only Step 1 changes (Steps 2, 4 and
+   5 stop at boundaries and keep the parity of every piece).  With
+   N_beta = 1 there is no boundary.                                        */
+static int ntau(const or_handle* h) { return h->p.dom_tau; }
+static uint64_t tb_pk(const or_handle* h, int k) {
+  uint64_t m = (uint64_t)(((u128)(uint64_t)k << 59) / (u128)(uint64_t)h->p.dom_tau);
+  return (m << 3) | 6u;
+}
+/* pk distance going up from a to b (b == a: the whole circle, 2^62) */
+static uint64_t up_dist(uint64_t a, uint64_t b) { return (b == a) ? TWO62 : ((b - a) & (TWO62 - 1)); }
+/* the first boundary above pk a, and the last one below it (cyclic) */
+static int tb_above(const or_handle* h, uint64_t a) {
+  for (int k = 0; k < ntau(h); k++) if (tb_pk(h, k) > a) return k;
+  return 0;
+}
+static int tb_below(const or_handle* h, uint64_t a) {
+  for (int k = ntau(h) - 1; k >= 0; k--) if (tb_pk(h, k) < a) return k;
+  return ntau(h) - 1;
+}
+/* a boundary strictly between pk a and pk b going up from a (b == a: the
+   whole circle but a) */
+static int tb_between(const or_handle* h, uint64_t a, uint64_t b) {
+  if (ntau(h) < 2) return 0;
+  return up_dist(a, tb_pk(h, tb_above(h, a))) < up_dist(a, b);
+}
+/* the temporal slab of a worm at pk w: the index of the last boundary below */
+static int slab_of(const or_handle* h, uint64_t w) { return ntau(h) < 2 ? 0 : tb_below(h, w); }
+
+/* ------------------------------------------------------------------------ */
 /* Geometry.  Site i = x + Lx y; bond b = 2 a + d joins its lower site a to
    a + x^ (d = 0) or a + y^ (d = 1), periodic.  Legs of a vertex: 0 = a below,
    1 = upper site below, 2 = a above, 3 = upper site above.  A bond's tag is
@@ -573,19 +608,52 @@ int or_tables(const or_params* p, double* d4, double* Dmax, uint64_t* TV4,
    probability d(s)/D, s the pair of occupations at that time (a point held
    by a kink of the bond is skipped).  Diagonal vertices never change the
    occupations, so every bond may be treated in any order.                 */
+/* On-the-fly vertex generation (the paper's closing discussion of
+   extensions: vertices generated only near the worms).  With
+   vertex_window = w > 0 the vertex phase of a bond is confined to the region
+   R of time points within w beta of a worm on either of its two sites (worm
+   grid points, cyclic): only the diagonal vertices inside R are erased, and
+   only the candidates inside R are placed.  R depends on the worms alone,
+   which Step 3 does not move, and a Poisson process on R is independent of
+   the one outside, so drawing it afresh on R given the rest keeps the
+   distribution; Step 4 puts worms anywhere, so every region is reached.
+   The window is a fraction of beta, held as worm grid points.              */
+typedef struct { uint64_t* m; int n; uint64_t half; } window_t;
+
+static void window_of(const or_handle* h, const site_t* A, const site_t* B, window_t* W) {
+  W->n = 0;
+  W->m = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(A->n + B->n + 1));
+  for (int k = 0; k < A->n; k++) if (kworm(A->key[k])) W->m[W->n++] = kpk(A->key[k]) >> 3;
+  for (int k = 0; k < B->n; k++) if (kworm(B->key[k])) W->m[W->n++] = kpk(B->key[k]) >> 3;
+  double w = h->p.vertex_window;
+  W->half = (w >= 0.5) ? TWO59 : (uint64_t)(w * 0x1p59);
+}
+/* is grid point pos within the window of a worm (cyclic distance)? */
+static int in_window(const window_t* W, uint64_t pos) {
+  for (int i = 0; i < W->n; i++) {
+    uint64_t d = (pos - W->m[i]) & (TWO59 - 1), e = (W->m[i] - pos) & (TWO59 - 1);
+    if ((d < e ? d : e) <= W->half) return 1;
+  }
+  return 0;
+}
+
 static int step3_bond(or_handle* h, int a, int d) {
   int bs = step(h, a, d, +1), tag = bond_tag(h, a, d);
   site_t *A = &h->site[a], *B = &h->site[bs];
+  window_t W = { NULL, 0, 0 };
+  const int otf = h->p.vertex_window > 0.0;
+  if (otf) window_of(h, A, B, &W);
   for (int k = A->n - 1; k >= 0; k--) {
     uint64_t key = A->key[k];
     if (ktag(key) != tag || kab(key) != kbl(key)) continue;
+    if (otf && !in_window(&W, kpk(key) >> 3)) continue;  /* kept outside the window */
     uint64_t pk = kpk(key);
     site_erase(A, k);
     int kb = site_find(B, pk);
-    if (kb < 0) return OR_EINVARIANT;
+    if (kb < 0) { free(W.m); return OR_EINVARIANT; }
     site_erase(B, kb);
   }
-  if (!(h->D > 0.0)) return OR_OK;
+  if (!(h->D > 0.0)) { free(W.m); return OR_OK; }
   stream_t s;
   s_init(&s, h->p.seed, (uint32_t)(2 * a + d), c2_of(PH_VERTEX, 0, h->p.replica), (uint32_t)h->sweep);
   uint64_t pos = 0;
@@ -598,6 +666,7 @@ static int step3_bond(or_handle* h, int a, int d) {
     if (nxt >= TWO59) break;
     pos = nxt;
     uint64_t pk = (pos << 3) | (uint64_t)tag;
+    if (otf && !in_window(&W, pos)) continue;
     if (site_find(A, pk) >= 0) continue;
     int na = state_at(A, pk), nb = state_at(B, pk);
     int si = na | (nb << 1);
@@ -608,6 +677,7 @@ static int step3_bond(or_handle* h, int a, int d) {
     site_add(A, (pk << 2) | ((uint64_t)na << 1) | (uint64_t)na, 0);
     site_add(B, (pk << 2) | ((uint64_t)nb << 1) | (uint64_t)nb, 0);
   }
+  free(W.m);
   return s.err;
 }
 
@@ -624,8 +694,59 @@ static int ev_cmp(const void* x, const void* y) {
    just above the lower leg.  A site without legs is one closed interval of
    length beta: its state is drawn uniformly (both weigh cosh(beta eta)) and
    n is even.  Each new worm then takes one word: label = word >> 1 (its
-   place in the Step-5 order), direction = word & 1.                        */
+   place in the Step-5 order), direction = word & 1.
+   With temporal domains the intervals are delimited by the vertex legs and
+   the temporal boundaries (pseudo code Step 4), each boundary carrying the
+   state the worldline has there before the worms are erased; the intervals
+   are taken in time order from the lowest delimiter.                       */
+static int step4_site_tau(or_handle* h, int si) {
+  site_t* S = &h->site[si];
+  const int NB = ntau(h);
+  int bs[64];
+  for (int k = 0; k < NB; k++) bs[k] = state_at(S, tb_pk(h, k));
+  int nl = 0;
+  for (int k = 0; k < S->n; k++) if (!kworm(S->key[k])) { S->key[nl] = S->key[k]; S->lab[nl] = 0; nl++; }
+  S->n = nl;
+  /* delimiters in time order: the legs and the boundaries (as keys of tag 6
+     whose state below and above is the boundary's state) */
+  int nd = nl + NB;
+  uint64_t* dl = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nd);
+  for (int k = 0; k < nl; k++) dl[k] = S->key[k];
+  for (int k = 0; k < NB; k++) dl[nl + k] = (tb_pk(h, k) << 2) | ((uint64_t)bs[k] << 1) | (uint64_t)bs[k];
+  for (int i = 1; i < nd; i++)  /* insertion sort by time */
+    for (int j = i; j > 0 && kpk(dl[j]) < kpk(dl[j - 1]); j--) { uint64_t t = dl[j]; dl[j] = dl[j - 1]; dl[j - 1] = t; }
+  stream_t st;
+  s_init(&st, h->p.seed, (uint32_t)si, c2_of(PH_REGEN, 0, h->p.replica), (uint32_t)h->sweep);
+  static uint64_t offs[MAXW];
+  ev_t* out = (ev_t*)malloc(sizeof(ev_t) * (size_t)(nl + NB * MAXW + 1));
+  int no = 0;
+  for (int k = 0; k < nd; k++) {
+    uint64_t lo = dl[k], hi = dl[(k + 1) % nd];
+    if (ktag(lo) != 6) { out[no].key = lo; out[no].lab = 0; no++; }
+    uint64_t M = wpts(kpk(lo), kpk(hi));
+    int p = kab(lo), sigma = p ^ kbl(hi);
+    int n = sample_worms(&h->z, &st, M, sigma, h->SWs, h->SWI, offs, MAXW);
+    if (n < 0) { free(out); free(dl); return st.err ? st.err : OR_ETIMEOUT; }
+    uint64_t m0 = wm_above(kpk(lo));
+    for (int j = 0; j < n; j++) {
+      uint64_t w = s_word(&st);
+      out[no].key = wkey((m0 + offs[j]) & (TWO59 - 1), (int)(w & 1), p ^ 1 ^ (j & 1));
+      out[no].lab = w >> 1;
+      no++;
+    }
+  }
+  qsort(out, (size_t)no, sizeof(ev_t), ev_cmp);
+  site_reserve(S, no);
+  for (int k = 0; k < no; k++) { S->key[k] = out[k].key; S->lab[k] = out[k].lab; }
+  S->n = no;
+  if (no) fix_base(S); else S->base = bs[0];
+  free(out);
+  free(dl);
+  return st.err;
+}
+
 static int step4_site(or_handle* h, int si) {
+  if (ntau(h) > 1) return step4_site_tau(h, si);
   site_t* S = &h->site[si];
   int nl = 0;
   for (int k = 0; k < S->n; k++) if (!kworm(S->key[k])) { S->key[nl] = S->key[k]; S->lab[nl] = 0; nl++; }
@@ -674,18 +795,25 @@ static int step4_site(or_handle* h, int si) {
 
 /* length (worm grid points) of the leg of the vertex at pk pv on site x,
    upward or downward, up to the next event other than the skipped worm;
-   the whole circle (2^59) if there is none.                               */
+   the whole circle (2^59) if there is none.  With temporal domains a leg
+   also ends at the next temporal boundary (Eq. 2 within a domain).        */
 static uint64_t leg_len(const or_handle* h, int x, uint64_t pv, int up, int skip_site, uint64_t skip_pk) {
   const site_t* S = &h->site[x];
   int iv = site_find(S, pv), n = S->n, j = iv;
+  uint64_t len = TWO59;
   for (int k = 0; k < n; k++) {
     j = up ? (j + 1) % n : (j + n - 1) % n;
     if (j == iv) break;
     uint64_t pj = kpk(S->key[j]);
     if (x == skip_site && pj == skip_pk) continue;
-    return up ? wpts(pv, pj) : wpts(pj, pv);
+    len = up ? wpts(pv, pj) : wpts(pj, pv);
+    break;
   }
-  return TWO59;
+  if (ntau(h) > 1) {
+    uint64_t lb = up ? wpts(pv, tb_pk(h, tb_above(h, pv))) : wpts(tb_pk(h, tb_below(h, pv)), pv);
+    if (lb < len) len = lb;
+  }
+  return len;
 }
 
 static void flip_leg_bit(or_handle* h, int x, uint64_t pv, int below) {
@@ -710,6 +838,8 @@ static int scatter_move(or_handle* h, int pass, int ws, uint64_t wpk, uint64_t w
   int ie = up ? (iw + 1) % n : (iw + n - 1) % n;
   uint64_t ke = S->key[ie];
   if (kworm(ke)) { S->key[iw] ^= 2u; return OR_OK; }
+  /* a temporal boundary before the next event turns it round (pseudo code Step 5) */
+  if (tb_between(h, up ? wpk : kpk(ke), up ? kpk(ke) : wpk)) { S->key[iw] ^= 2u; return OR_OK; }
   int a, d;
   leg_bond(h, ws, ktag(ke), &a, &d);
   if (!bond_active(h, a, d, pass)) { S->key[iw] ^= 2u; return OR_OK; }
@@ -754,18 +884,28 @@ static int wref_cmp(const void* x, const void* y) {
 
 /* One Step-5 pass: every sub-block (in unit order) moves each of its worms
    once, in ascending label order; the r-th move uses Philox block r of the
-   stream (unit = sub-block id, c2 = scatter | pass).                       */
+   stream (unit = sub-block id, c2 = scatter | pass).  With temporal domains
+   the unit is a sub-block of one slab, sub-block id * N_beta + slab: a worm
+   never leaves its slab (it turns round at the boundaries and every leg
+   ends there), so the slabs of a sub-block are independent chains.        */
+static uint32_t worm_unit(const or_handle* h, uint32_t sb, uint64_t wpk) {
+  return sb * (uint32_t)ntau(h) + (uint32_t)slab_of(h, wpk);
+}
+
 static int step5_pass(or_handle* h, int pass) {
   int N = h->N;
   uint32_t* unit = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   uint32_t umax = 0;
   for (int s = 0; s < N; s++) { unit[s] = sb_unit(h, s, pass); if (unit[s] > umax) umax = unit[s]; }
+  umax = (umax + 1) * (uint32_t)ntau(h) - 1;
   int64_t nw = 0;
   for (int s = 0; s < N; s++) for (int k = 0; k < h->site[s].n; k++) nw += kworm(h->site[s].key[k]);
   wref_t* W = (wref_t*)malloc(sizeof(wref_t) * (size_t)(nw + 1));
   /* bucket the worms by sub-block */
   int64_t* cnt = (int64_t*)calloc((size_t)umax + 2, sizeof(int64_t));
-  for (int s = 0; s < N; s++) for (int k = 0; k < h->site[s].n; k++) if (kworm(h->site[s].key[k])) cnt[unit[s] + 1]++;
+  for (int s = 0; s < N; s++)
+    for (int k = 0; k < h->site[s].n; k++)
+      if (kworm(h->site[s].key[k])) cnt[worm_unit(h, unit[s], kpk(h->site[s].key[k])) + 1]++;
   for (uint32_t u = 0; u <= umax; u++) cnt[u + 1] += cnt[u];
   int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)umax + 1));
   for (uint32_t u = 0; u <= umax; u++) fill[u] = cnt[u];
@@ -773,7 +913,7 @@ static int step5_pass(or_handle* h, int pass) {
     for (int k = 0; k < h->site[s].n; k++)
       if (kworm(h->site[s].key[k])) {
         wref_t r = { s, kpk(h->site[s].key[k]), h->site[s].lab[k] };
-        W[fill[unit[s]]++] = r;
+        W[fill[worm_unit(h, unit[s], r.pk)]++] = r;
       }
   int rc = OR_OK;
   for (uint32_t u = 0; u <= umax && rc == OR_OK; u++) {
@@ -821,6 +961,28 @@ static void measure(or_handle* h, or_row* r) {
       leg_bond(h, s, ktag(key), &a, &d);
       if (a == s) { r->n_v++; if (kab(key) != kbl(key)) r->n_k++; }
     }
+    if (ntau(h) > 1) {
+      /* with temporal domains the estimator runs over the intervals of
+         Step 4, delimited by the vertex legs and the temporal boundaries
+         (whose states the configuration fixes), worms ignored */
+      int NB = ntau(h), nd = nl + NB, j = 0;
+      uint64_t* dl = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nd);
+      for (int k = 0; k < S->n; k++) if (!kworm(S->key[k])) dl[j++] = S->key[k];
+      for (int k = 0; k < NB; k++) {
+        int b = state_at(S, tb_pk(h, k));
+        dl[j++] = (tb_pk(h, k) << 2) | ((uint64_t)b << 1) | (uint64_t)b;
+      }
+      for (int i = 1; i < nd; i++)
+        for (int m = i; m > 0 && kpk(dl[m]) < kpk(dl[m - 1]); m--) { uint64_t t = dl[m]; dl[m] = dl[m - 1]; dl[m - 1] = t; }
+      for (int k = 0; k < nd; k++) {
+        uint64_t lo = dl[k], hi = dl[(k + 1) % nd];
+        double x = (double)wpts(kpk(lo), kpk(hi)) * XW;
+        int sg = kab(lo) ^ kbl(hi);
+        q = q + x * (sg ? coth_det(x) : tanh_det(x));
+      }
+      free(dl);
+      continue;
+    }
     if (nl == 0) { double x = (double)TWO59 * XW; q = q + x * tanh_det(x); continue; }
     int first = -1, prev = -1;
     for (int k = 0; k < S->n; k++) {
@@ -842,11 +1004,14 @@ static void measure(or_handle* h, or_row* r) {
   r->q_impr = q;
   /* worms held by each domain (the paper's health figure of O(10)-O(100)
      worms per domain, discussion of Fig. 3): the fewest, and the empty ones */
-  uint64_t* wd = (uint64_t*)calloc((size_t)h->ndom, sizeof(uint64_t));
+  /* (a domain is a spatial domain times a temporal slab) */
+  int nsd = h->ndom * ntau(h);
+  uint64_t* wd = (uint64_t*)calloc((size_t)nsd, sizeof(uint64_t));
   for (int s = 0; s < h->N; s++)
-    for (int k = 0; k < h->site[s].n; k++) wd[dom_of(h, s)] += kworm(h->site[s].key[k]);
+    for (int k = 0; k < h->site[s].n; k++)
+      if (kworm(h->site[s].key[k])) wd[dom_of(h, s) * ntau(h) + slab_of(h, kpk(h->site[s].key[k]))]++;
   uint64_t wmin = UINT64_MAX;
-  for (int D = 0; D < h->ndom; D++) {
+  for (int D = 0; D < nsd; D++) {
     if (wd[D] < wmin) wmin = wd[D];
     if (wd[D] == 0) r->dom_empty++;
   }
@@ -880,6 +1045,19 @@ static void site_legs(const or_handle* h, int x, uint64_t pv, legs_t* L) {
   for (int k = 0; k < n; k++) { jn = (jn + 1) % n; if (jn == iv || !kworm(S->key[jn])) break; }
   for (int k = 0; k < n; k++) { jp = (jp + n - 1) % n; if (jp == iv || !kworm(S->key[jp])) break; }
   L->single = (jn == iv);
+  if (ntau(h) > 1) {
+    /* with temporal domains a leg also ends at the nearest temporal
+       boundary; its far state is the worldline's state there */
+    uint64_t bu = tb_pk(h, tb_above(h, pv)), bd = tb_pk(h, tb_below(h, pv));
+    if (L->single || up_dist(pv, bu) < up_dist(pv, kpk(S->key[jn]))) { L->phi = bu; L->far_up = state_at(S, bu); }
+    else { L->phi = kpk(S->key[jn]); L->far_up = kbl(S->key[jn]); }
+    if (L->single || up_dist(bd, pv) < up_dist(kpk(S->key[jp]), pv)) { L->plo = bd; L->far_dn = state_at(S, bd); }
+    else { L->plo = kpk(S->key[jp]); L->far_dn = kab(S->key[jp]); }
+    L->single = 0;
+    L->Iup = wpts(pv, L->phi);
+    L->Idn = wpts(L->plo, pv);
+    return;
+  }
   if (L->single) { L->Ifull = TWO59; L->plo = L->phi = pv; return; }
   L->phi = kpk(S->key[jn]); L->far_up = kbl(S->key[jn]); L->Iup = wpts(pv, L->phi);
   L->plo = kpk(S->key[jp]); L->far_dn = kab(S->key[jp]); L->Idn = wpts(L->plo, pv);
@@ -905,6 +1083,83 @@ static int regen_interval(or_handle* h, stream_t* st, int x, uint64_t lo, uint64
 }
 
 static double fsig(int sigma, double em1) { return sigma ? -em1 : 2.0 + em1; }
+
+/* ------------------------------------------------------------------------ */
+/* Step 1 (temporal-boundary update, Eq. 3) on one site.  Boundary k lies in
+   the interval I = I2 + I1 between the nearest delimiters below and above it
+   (vertex legs or other temporal boundaries, worms ignored): I2 from the lower
+   delimiter (state p just above it) up to the boundary, I1 from the boundary
+   up to the upper delimiter (state q just below it).  The new state s' at the
+   boundary is drawn with P(s') = f_{q s'}(I1) f_{s' p}(I2) / f_{q p}(I), where
+   f_{ab}(I) = <a| e^{I eta Q} |b> is cosh or sinh of x = I eta; written as
+   e^x F(a ^ b, x) / 2 with F(0, x) = 2 + expm1(-2x), F(1, x) = -expm1(-2x),
+   the factors e^x / 2 are common to both s' and drop out.  The worms of I2
+   and I1 are then drawn anew with the Eq. 1 sampler (I2 first).  The
+   boundaries of a site are updated one after the other, k = 0, 1, ..., each
+   with the current states of the others (each update is a heat bath, so the
+   sequence keeps the distribution); different sites are independent.      */
+static void pdom_weights(int p, int q, uint64_t M1, uint64_t M2, double XW, double w[2]) {
+  double e1 = or_expm1_det(-2.0 * ((double)M1 * XW)), e2 = or_expm1_det(-2.0 * ((double)M2 * XW));
+  for (int sn = 0; sn < 2; sn++) w[sn] = fsig(q ^ sn, e1) * fsig(sn ^ p, e2);
+}
+
+void or_pdom(int p, int q, uint64_t M1, uint64_t M2, double XW, double out[2]) {
+  double w[2];
+  pdom_weights(p, q, M1, M2, XW, w);
+  double tot = w[0] + w[1];
+  out[0] = w[0] / tot;
+  out[1] = w[1] / tot;
+}
+
+/* nearest delimiter of boundary point B going down (up = 0) or up (up = 1):
+   its pk and the state on the side facing B */
+static void tb_delim(const or_handle* h, const site_t* S, int k, int up, uint64_t* pk, int* st) {
+  uint64_t B = tb_pk(h, k);
+  int kb = up ? (k + 1) % ntau(h) : (k + ntau(h) - 1) % ntau(h);
+  uint64_t best = tb_pk(h, kb);
+  int from_leg = -1;
+  for (int i = 0; i < S->n; i++) {
+    if (kworm(S->key[i])) continue;
+    uint64_t q = kpk(S->key[i]);
+    if (up ? (up_dist(B, q) < up_dist(B, best)) : (up_dist(q, B) < up_dist(best, B))) { best = q; from_leg = i; }
+  }
+  *pk = best;
+  if (from_leg >= 0) *st = up ? kbl(S->key[from_leg]) : kab(S->key[from_leg]);
+  else *st = state_at(S, best);
+}
+
+static int step1_site(or_handle* h, int si) {
+  site_t* S = &h->site[si];
+  stream_t st;
+  s_init(&st, h->p.seed, (uint32_t)si, c2_of(PH_TEMPORAL, 0, h->p.replica), (uint32_t)h->sweep);
+  double XW = xw_of(h);
+  for (int k = 0; k < ntau(h); k++) {
+    uint64_t B = tb_pk(h, k), lo, hi;
+    int p, q;
+    tb_delim(h, S, k, 0, &lo, &p);
+    tb_delim(h, S, k, 1, &hi, &q);
+    double w[2];
+    pdom_weights(p, q, wpts(B, hi), wpts(lo, B), XW, w);
+    double tot = w[0] + w[1];
+    if (!(tot > 0.0)) return OR_EINVARIANT;
+    double u = ((double)(s_word(&st) >> 11) * 0x1p-53) * tot;
+    int sn = (u < w[0]) ? 0 : 1;
+    int rc = regen_interval(h, &st, si, lo, B, p, sn);
+    if (rc == OR_OK) rc = regen_interval(h, &st, si, B, hi, sn, q);
+    if (rc) return rc;
+    if (S->n == 0) S->base = sn;
+  }
+  return st.err;
+}
+
+int or_temporal(or_handle* h) {
+  if (ntau(h) < 2) return OR_OK;
+  for (int s = 0; s < h->N; s++) {
+    int rc = step1_site(h, s);
+    if (rc) return rc;
+  }
+  return OR_OK;
+}
 
 static int step2_bond(or_handle* h, int a, int d) {
   int b = step(h, a, d, +1), tag = bond_tag(h, a, d);
@@ -996,8 +1251,9 @@ int or_tile(or_handle* h, int stop_after) {
 
 int or_sweep(or_handle* h, int64_t n) {
   for (int64_t k = 0; k < n; k++) {
-    if ((h->ndx > 1 || h->ndy > 1) && h->sweep % (uint64_t)h->K == 0) {
-      int rc = or_boundary(h);
+    if ((h->ndx > 1 || h->ndy > 1 || ntau(h) > 1) && h->sweep % (uint64_t)h->K == 0) {
+      int rc = or_temporal(h);                         /* Step 1 */
+      if (rc == OR_OK && (h->ndx > 1 || h->ndy > 1)) rc = or_boundary(h);  /* Step 2 */
       if (rc) return rc;
     }
     int rc = or_tile(h, 6);
@@ -1020,6 +1276,8 @@ static int validate(const or_params* p) {
   if (B && B < p->dom_x && p->dom_x % B) return OR_EINVAL;
   if (B && B < p->dom_y && p->dom_y % B) return OR_EINVAL;
   if (p->replica >= 65536 || p->init < 0 || p->init > 2) return OR_EINVAL;
+  if (p->dom_tau < 1 || p->dom_tau > 64) return OR_EINVAL;
+  if (!(p->vertex_window >= 0.0 && p->vertex_window <= 1.0)) return OR_EINVAL;
   /* the grid scales 2^59/(beta eta) and 2^59/(beta D) must lie in [2^39, 2^99] */
   if (!(p->beta * p->eta >= 0x1p-40 && p->beta * p->eta <= 0x1p20)) return OR_EINVAL;
   {
@@ -1263,6 +1521,112 @@ int or_rho_pair(or_handle* h, int32_t K, double* out) {
           }
   }
   free(z);
+  return OR_OK;
+}
+
+/* n operators Q_a[0..g) at the points of one interval of a site, ordered in
+   time going up from the interval's lower leg (Supplement S-I, with every
+   operator inserted in the interval's matrix element; the paper leaves the
+   case of several points on one interval to later work):
+     eta^g <q| e^{I_g Q} Q_a[g-1] ... e^{I_1 Q} Q_a[0] e^{I_0 Q} |p> / <q| e^{I Q} |p>,
+   where I_0 runs from the lower leg to the first point, I_j between points j-1
+   and j, I_g from the last point to the upper leg (counts of worm points,
+   M1[j] = the worm points strictly between the lower leg and point j).  Each
+   Q_a maps its in-state to its out-state, so the states between the
+   operators are fixed and the matrix element is the product of the factors
+   f = e^x F / 2 of the pieces; the e^x cancel because the counts add up to I:
+     eta^g F(q ^ out_a[g-1], I_g) ... F(in_a[j] ^ out_a[j-1], I_j) ... F(in_a[0] ^ p, I_0)
+       / (2^g F(q ^ p, I)).
+   p < 0 stands for a site without vertex legs: then the points lie on a circle
+   with no reference point (M1[j] = the time point pk of point j, increasing),
+   and the density is the cyclic trace
+     eta^g Tr[e^{I_{g-1} Q} Q_a[g-1] ... e^{I_0 Q} Q_a[0]] / Tr[e^{2^59 Q}]
+       = eta^g prod_j F(in_a[j+1] ^ out_a[j], I_j) / (2^g F(0, 2^59)),
+   I_j the worm points strictly between points j and j + 1 for j < g - 1 and
+   I_{g-1} = 2^59 minus their sum, the piece that closes the circle.        */
+static double rho_interval(int p, int q, uint64_t M, int g, const uint64_t* M1, const int* a, double eta, double XW) {
+  double num = 1.0, etag = 1.0;
+  for (int j = 0; j < g; j++) etag = etag * eta;
+  if (p < 0) {
+    uint64_t used = 0;
+    for (int j = 0; j < g; j++) {
+      int nx = (j + 1) % g;
+      uint64_t piece = (j + 1 < g) ? wpts(M1[j], M1[j + 1]) : TWO59 - used;
+      used += piece;
+      num = num * Fsig(q_in(a[nx]) ^ q_out(a[j]), piece, XW);
+    }
+    double den = 1.0;
+    for (int j = 0; j < g; j++) den = den * 2.0;
+    return etag * (num / (den * Fsig(0, TWO59, XW)));
+  }
+  num = Fsig(q_in(a[0]) ^ p, M1[0], XW);
+  for (int j = 1; j < g; j++) num = num * Fsig(q_in(a[j]) ^ q_out(a[j - 1]), M1[j] - M1[j - 1], XW);
+  num = num * Fsig(q ^ q_out(a[g - 1]), M - M1[g - 1], XW);
+  double den = 1.0;
+  for (int j = 0; j < g; j++) den = den * 2.0;
+  return etag * (num / (den * Fsig(q ^ p, M, XW)));
+}
+
+double or_interval_density(int p, int q, uint64_t M, int g, const uint64_t* M1, const int* a, double eta, double XW) {
+  return rho_interval(p, q, M, g, M1, a, eta, XW);
+}
+
+/* Supplement S-I n-point functions resolved by the component of Q at
+   arbitrary times: for tuple j of n points (site s_c, slice k_c, component
+   a_c) (pts[(j n + c) 3 + 0..2]), averaged over the K cyclic shifts t of all
+   slices (tau_c = (k_c + t mod K) beta / K),
+     out[j] = < Q_a1(X_1) ... Q_an(X_n) > = eta^-n < prod over intervals of the
+              density of the points on that interval >,
+   the points grouped by the interval (site and lower vertex leg, or the whole
+   circle of a site without legs) that holds them, each group by the interval
+   form above (a single point is rho_a of Supplement S-I), the groups
+   multiplied in order of first appearance.  Two points of one tuple at the
+   same site and slice are refused (OR_EINVAL).                              */
+int or_npoint_alpha(or_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* pts, double* out) {
+  if (K < 1 || n < 1 || n > 16 || m < 0) return OR_EINVAL;
+  double XW = xw_of(h), eta = h->p.eta;
+  for (int64_t j = 0; j < m; j++) {
+    const int32_t* t = pts + j * n * 3;
+    for (int c = 0; c < n; c++) {
+      if (t[3 * c] < 0 || t[3 * c] >= h->N || t[3 * c + 1] < 0 || t[3 * c + 1] >= K || (t[3 * c + 2] & ~1))
+        return OR_EINVAL;
+      for (int e = 0; e < c; e++)
+        if (t[3 * e] == t[3 * c] && t[3 * e + 1] == t[3 * c + 1]) return OR_EINVAL;
+    }
+    double acc = 0.0;
+    for (int sh = 0; sh < K; sh++) {
+      slice_t z[16];
+      for (int c = 0; c < n; c++) slice_of(&h->site[t[3 * c]], slice_pk(K, (t[3 * c + 1] + sh) % K), &z[c]);
+      int done[16] = {0};
+      double prod = 1.0;
+      for (int c = 0; c < n; c++) {
+        if (done[c]) continue;
+        /* the points of c's interval, in time order going up from its lower
+           leg (or from the circle's start on a site without legs) */
+        int mem[16], g = 0;
+        for (int e = c; e < n; e++)
+          if (!done[e] && t[3 * e] == t[3 * c] && z[e].iv == z[c].iv) { mem[g++] = e; done[e] = 1; }
+        for (int i = 1; i < g; i++)
+          for (int k = i; k > 0; k--) {
+            uint64_t ka = (z[c].iv < 0) ? z[mem[k]].pt : z[mem[k]].off;
+            uint64_t kb = (z[c].iv < 0) ? z[mem[k - 1]].pt : z[mem[k - 1]].off;
+            if (ka < kb) { int tmp = mem[k]; mem[k] = mem[k - 1]; mem[k - 1] = tmp; } else break;
+          }
+        uint64_t M1[16];
+        int a[16];
+        for (int i = 0; i < g; i++) {
+          const slice_t* zi = &z[mem[i]];
+          M1[i] = (z[c].iv < 0) ? zi->pt : zi->M1;
+          a[i] = t[3 * mem[i] + 2];
+        }
+        prod = prod * rho_interval(z[c].iv < 0 ? -1 : z[c].p, z[c].q, z[c].M, g, M1, a, eta, XW);
+      }
+      acc = acc + prod;
+    }
+    double etan = 1.0;
+    for (int c = 0; c < n; c++) etan = etan * eta;
+    out[j] = (acc / (double)K) / etan;
+  }
   return OR_OK;
 }
 

@@ -10,6 +10,6 @@ from ._lib import (PMWA_OK, PMWA_EINVAL, PMWA_ECAPACITY, PMWA_ETIMEOUT, PMWA_ECU
                    pmwa_export_bytes, pmwa_footprint, pmwa_get_sweep, pmwa_green, pmwa_green_tau, pmwa_import,
                    pmwa_measure, pmwa_npoint, pmwa_profile, pmwa_profile_phases, pmwa_profile_read, pmwa_rho_alpha, pmwa_rho_slices, pmwa_rho_slices_static, pmwa_set_n_cycle, pmwa_set_sweep, pmwa_slot_capacity, pmwa_tile_smem, pmwa_tile_plan, pmwa_strerror, pmwa_sweep,
                    pmwa_tables, pmwa_tile, ROW_DTYPE, KERNELS, SERIES, summary, n_cycle, pmwa_set_loop_caps,
-                   pmwa_philox_blocks)
+                   pmwa_philox_blocks, pmwa_temporal, pmwa_npoint_alpha)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("sub_block", C.c_int32), ("init", C.c_int32),
                 ("init_seed", C.c_uint64), ("c_off", C.c_double),
                 ("replica", C.c_uint32), ("cap_site", C.c_int32),
-                ("rows_cap", C.c_int32), ("legs_hint", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("rows_cap", C.c_int32), ("legs_hint", C.c_int32), ("dom_tau", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
@@ -49,7 +50,7 @@ SERIES = ("E", "E_eta", "n", "Q_raw", "Q_impr", "kin")
 
 DEFAULTS = dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1, dom_x=0, dom_y=0,
                 exchange_every=2, n_cycle=8, sub_block=0, init=1, init_seed=1, c_off=-1.0,
-                replica=0, cap_site=0, rows_cap=0, legs_hint=0)
+                replica=0, cap_site=0, rows_cap=0, legs_hint=0, dom_tau=1)
 
 _lib = None
 
@@ -69,6 +70,7 @@ def load(build=True):
         "pmwa_create": (C.c_int, [P(Params), vp, sz, vp, P(vp)]),
         "pmwa_sweep": (C.c_int, [vp, C.c_int64]),
         "pmwa_boundary": (C.c_int, [vp]),
+        "pmwa_temporal": (C.c_int, [vp]),
         "pmwa_tile": (C.c_int, [vp, C.c_int32]),
         "pmwa_measure": (C.c_int, [vp, vp, C.c_int64, P(C.c_int64)]),
         "pmwa_rho_slices": (C.c_int, [vp, C.c_int32, vp]),
@@ -82,6 +84,7 @@ def load(build=True):
         "pmwa_slot_capacity": (C.c_int, [P(Params), P(C.c_int32)]),
         "pmwa_green_tau": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
         "pmwa_npoint": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int64, vp, vp]),
+        "pmwa_npoint_alpha": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int64, vp, vp]),
         "pmwa_get_sweep": (C.c_int, [vp, P(C.c_uint64)]),
         "pmwa_set_sweep": (C.c_int, [vp, C.c_uint64]),
         "pmwa_destroy": (C.c_int, [vp]),
@@ -157,6 +160,10 @@ def pmwa_boundary(h):
     _check("pmwa_boundary", load().pmwa_boundary(h))
 
 
+def pmwa_temporal(h):
+    _check("pmwa_temporal", load().pmwa_temporal(h))
+
+
 def pmwa_tile(h, stop_after):
     _check("pmwa_tile", load().pmwa_tile(h, stop_after))
 
@@ -213,6 +220,19 @@ def pmwa_npoint(h, K, tuples):
         raise ValueError("tuples must be an (m, n) array of site indices")
     out = np.zeros(t.shape[0], dtype=np.float64)
     _check("pmwa_npoint", load().pmwa_npoint(h, K, t.shape[1], t.shape[0], t.ctypes.data, out.ctypes.data))
+    return out
+
+
+def pmwa_npoint_alpha(h, K, pts):
+    """<T Q_a1(X_1) ... Q_an(X_n)> for each tuple of n points (site, slice,
+    component) in pts (m, n, 3), averaged over the K cyclic shifts of the
+    slices: an array (m,)."""
+    a = np.ascontiguousarray(pts, dtype=np.int32)
+    if a.ndim != 3 or a.shape[2] != 3:
+        raise ValueError("pts must be an (m, n, 3) array of (site, slice, component)")
+    out = np.zeros(a.shape[0], dtype=np.float64)
+    _check("pmwa_npoint_alpha", load().pmwa_npoint_alpha(h, K, a.shape[1], a.shape[0], a.ctypes.data,
+                                                         out.ctypes.data))
     return out
 
 
@@ -292,7 +312,7 @@ def pmwa_destroy(h):
     _check("pmwa_destroy", load().pmwa_destroy(h))
 
 
-KERNELS = ("boundary", "tile", "unused2", "unused3", "unused4", "rho", "sweep")
+KERNELS = ("boundary", "tile", "temporal", "unused3", "unused4", "rho", "sweep")
 
 
 def pmwa_profile(h, enable):
@@ -362,6 +382,9 @@ class Sim:
     def boundary(self):
         pmwa_boundary(self.h)
 
+    def temporal(self):
+        pmwa_temporal(self.h)
+
     def tile(self, stop_after=6):
         pmwa_tile(self.h, stop_after)
 
@@ -388,6 +411,9 @@ class Sim:
 
     def npoint(self, K, tuples):
         return pmwa_npoint(self.h, K, tuples)
+
+    def npoint_alpha(self, K, pts):
+        return pmwa_npoint_alpha(self.h, K, pts)
 
     @property
     def sweep_index(self):

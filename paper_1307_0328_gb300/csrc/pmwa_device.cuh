@@ -352,6 +352,39 @@ __device__ __forceinline__ uint64_t wm_above(uint64_t a) { return ((a + 1) >> 3)
 __device__ __forceinline__ uint64_t wm_below(uint64_t a) { return (((a + 1) >> 3) + kTwo59 - 1) & (kTwo59 - 1); }
 
 // ---------------------------------------------------------------------------
+// Temporal domains (Supplement S-II): with N_beta = d.ntau > 1, boundary k of
+// every site sits at the grid point m_k = floor(k 2^59 / N_beta) with the
+// otherwise unused tag 6, so its time point m_k << 3 | 6 differs from every
+// vertex leg and worm; the state there is the worldline's state at that point.
+__device__ __forceinline__ uint64_t tb_pk(const Dev& d, int k) {
+  const uint64_t kk = uint64_t(k);
+  return ((kk * d.tq + (kk * d.tr) / uint64_t(d.ntau)) << 3) | 6u;
+}
+// pk distance going up from a to b (b == a: the whole circle)
+__device__ __forceinline__ uint64_t up_dist(uint64_t a, uint64_t b) {
+  return (b == a) ? kTwo62 : ((b - a) & (kTwo62 - 1));
+}
+// the temporal slab of worm grid point m: the largest k with m_k <= m, i.e.
+// k 2^59 < (m + 1) N_beta, k = floor(((m + 1) N_beta - 1) / 2^59) (128-bit)
+__device__ __forceinline__ int slab_of_m(const Dev& d, uint64_t m) {
+  if (d.ntau < 2) return 0;
+  const uint64_t a = m + 1, n = uint64_t(d.ntau);
+  uint64_t hi = __umul64hi(a, n), lo = a * n;
+  if (lo == 0) hi -= 1;
+  lo -= 1;
+  return int((hi << 5) | (lo >> 59));
+}
+// index of the first boundary above pk a / the last one below it (cyclic)
+__device__ __forceinline__ int tb_above(const Dev& d, uint64_t a) {
+  for (int k = 0; k < d.ntau; ++k) if (tb_pk(d, k) > a) return k;
+  return 0;
+}
+__device__ __forceinline__ int tb_below(const Dev& d, uint64_t a) {
+  for (int k = d.ntau - 1; k >= 0; --k) if (tb_pk(d, k) < a) return k;
+  return d.ntau - 1;
+}
+
+// ---------------------------------------------------------------------------
 // Lattice geometry: site i = x + Lx y, bond 2a + d from a to a + x^ / a + y^;
 // tag of a bond 3d + cls(c), cls(c) = 2 if c = L-1 else c & 1 (c the
 // coordinate of a along d): distinct for the four bonds of a site.

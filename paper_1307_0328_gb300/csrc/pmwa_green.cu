@@ -209,7 +209,92 @@ __global__ void k_npoint(int K, int n, int m, const double* __restrict__ rho, co
   out[j] = __ddiv_rn(__ddiv_rn(acc, double(K)), etan);
 }
 
+// Joint density of g operators Q_a[0..g) at the points z[idx[0..g)] of one
+// interval, in time order (Supplement S-I with every operator inserted in the
+// interval's matrix element):
+//   eta^g <q| e^{I_g Q} Q_a[g-1] ... Q_a[0] e^{I_0 Q} |p> / <q| e^{I Q} |p>
+//     = eta^g F(in_a[0] ^ p, I_0) prod_j F(in_a[j] ^ out_a[j-1], I_j) F(q ^ out_a[g-1], I_g)
+//       / (2^g F(q ^ p, I)),
+// I_0 the worm points below the first point, I_j between points j-1 and j,
+// I_g above the last; on a site without legs the cyclic trace
+//   eta^g prod_j F(in_a[j+1] ^ out_a[j], I_j) / (2^g F(0, 2^59)),
+// I_j between points j and j + 1 and the last piece closing the circle.
+__device__ double rho_interval(const SliceInfo* z, const int* idx, const int* a, int g, double eta, double XW) {
+  double num = 1.0, etag = 1.0, den = 1.0;
+  for (int j = 0; j < g; ++j) { etag = __dmul_rn(etag, eta); den = __dmul_rn(den, 2.0); }
+  const SliceInfo& z0 = z[idx[0]];
+  if (z0.iv < 0) {
+    uint64_t used = 0;
+    for (int j = 0; j < g; ++j) {
+      const int nx = (j + 1) % g;
+      const uint64_t piece = (j + 1 < g) ? wpts(z[idx[j]].pt, z[idx[j + 1]].pt) : kTwo59 - used;
+      used += piece;
+      num = __dmul_rn(num, Fsig(q_in(a[nx]) ^ q_out(a[j]), piece, XW));
+    }
+    return __dmul_rn(etag, __ddiv_rn(num, __dmul_rn(den, Fsig(0, kTwo59, XW))));
+  }
+  num = Fsig(q_in(a[0]) ^ z0.p, z[idx[0]].M1, XW);
+  for (int j = 1; j < g; ++j)
+    num = __dmul_rn(num, Fsig(q_in(a[j]) ^ q_out(a[j - 1]), z[idx[j]].M1 - z[idx[j - 1]].M1, XW));
+  num = __dmul_rn(num, Fsig(z0.q ^ q_out(a[g - 1]), z0.M - z[idx[g - 1]].M1, XW));
+  return __dmul_rn(etag, __ddiv_rn(num, __dmul_rn(den, Fsig(z0.q ^ z0.p, z0.M, XW))));
+}
+
+// Supplement S-I n-point functions resolved by the component of Q at
+// arbitrary times: tuple j holds n points (site, slice, component) at
+// pts[(j n + c) 3 ..]; out[j] = (sum over the K cyclic shifts of the slices of
+// the product over intervals of the joint density of their points) / K /
+// eta^n.  The points are grouped by interval (site and lower vertex leg, or
+// the whole circle of a site without legs) in order of first appearance, each
+// group's points in time order (insertion sort by the offset from the lower
+// leg, or by time point on a site without legs).
+__global__ void k_npoint_alpha(const __grid_constant__ Dev d, int K, int n, int m, const int32_t* __restrict__ pts,
+                               double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int32_t* t = pts + size_t(j) * size_t(n) * 3;
+  int last[kMaxNpoint], cnt[kMaxNpoint];
+  for (int c = 0; c < n; ++c) {
+    const uint64_t* Kk = d.keyA + size_t(t[3 * c]) * d.cap;
+    cnt[c] = min(int(d.cntA[t[3 * c]] & kCntMaskG), d.cap);
+    last[c] = -1;
+    for (int i = 0; i < cnt[c]; ++i) if (!kworm(Kk[i])) last[c] = i;
+  }
+  double acc = 0.0;
+  for (int sh = 0; sh < K; ++sh) {
+    SliceInfo z[kMaxNpoint];
+    for (int c = 0; c < n; ++c)
+      slice_one(d.keyA + size_t(t[3 * c]) * d.cap, cnt[c], last[c], K, (t[3 * c + 1] + sh) % K, &z[c]);
+    unsigned done = 0;
+    double prod = 1.0;
+    for (int c = 0; c < n; ++c) {
+      if (done & (1u << c)) continue;
+      int idx[kMaxNpoint], a[kMaxNpoint], g = 0;
+      for (int e = c; e < n; ++e)
+        if (!(done & (1u << e)) && t[3 * e] == t[3 * c] && z[e].iv == z[c].iv) { idx[g++] = e; done |= 1u << e; }
+      const bool ring = z[c].iv < 0;
+      for (int i = 1; i < g; ++i)
+        for (int k = i; k > 0; --k) {
+          const uint64_t ka = ring ? z[idx[k]].pt : z[idx[k]].off, kb = ring ? z[idx[k - 1]].pt : z[idx[k - 1]].off;
+          if (ka < kb) { const int tmp = idx[k]; idx[k] = idx[k - 1]; idx[k - 1] = tmp; } else break;
+        }
+      for (int i = 0; i < g; ++i) a[i] = t[3 * idx[i] + 2];
+      prod = __dmul_rn(prod, rho_interval(z, idx, a, g, d.eta, d.XW));
+    }
+    acc = __dadd_rn(acc, prod);
+  }
+  double etan = 1.0;
+  for (int c = 0; c < n; ++c) etan = __dmul_rn(etan, d.eta);
+  out[j] = __ddiv_rn(__ddiv_rn(acc, double(K)), etan);
+}
+
 }  // namespace
+
+int launch_npoint_alpha(const Dev& d, int K, int n, int m, const int32_t* pts, double* out, void* stream) {
+  if (m <= 0) return 0;
+  k_npoint_alpha<<<(m + 63) / 64, 64, 0, cudaStream_t(stream)>>>(d, K, n, m, pts, out);
+  return int(cudaGetLastError());
+}
 
 int launch_npoint(int K, int n, int m, const double* rho, const int32_t* sites, double eta, double* out,
                   void* stream) {

@@ -41,6 +41,7 @@ namespace {
 
 struct Derived {
   int N, ndx, ndy, ndom, dom_x, dom_y, cap, capb, wcap, poolcap;
+  int ntau;  // temporal domains (1: none)
   double legs_want, mb;  // legs wanted in a domain table; mean Step-3 candidates per bond
   double d[4], D, tkink, SV, SW, XW;
   GridScale SVs, SWs, XQ;
@@ -71,7 +72,8 @@ int validate(const pmwa_params* p) {
   if (p->replica >= 65536u || p->init < 0 || p->init > 2) return PMWA_EINVAL;
   if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
   if (p->legs_hint < 0 || p->legs_hint > (1 << 20)) return PMWA_EINVAL;
-  for (int k = 0; k < 4; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  for (int k = 0; k < 3; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  if (p->dom_tau < 0 || p->dom_tau > 64) return PMWA_EINVAL;
   // the gap arithmetic needs the mean grid spacings 2^59/(beta eta) and
   // 2^59/(beta D) in [2^39, 2^99]
   const double be = p->beta * p->eta;
@@ -136,6 +138,7 @@ void derive(const pmwa_params* p, Derived* g) {
   g->ndx = p->Lx / g->dom_x;
   g->ndy = p->Ly / g->dom_y;
   g->ndom = g->ndx * g->ndy;
+  g->ntau = p->dom_tau > 1 ? p->dom_tau : 1;
   const double c_off = (p->c_off < 0.0) ? 0.5 * p->t : p->c_off;
   // Eq. 5 per bond: E(na, nb) = V na nb - (mu/4)(na + nb)
   double E[4], Emax = -INFINITY;
@@ -197,8 +200,15 @@ void derive(const pmwa_params* p, Derived* g) {
   } else {
     g->legs_want = 1.1 * 4.0 * p->beta * (g->D + p->t) * nds + 256.0;
   }
-  g->poolcap = int(std::min(60000.0, 1.5 * mb * 2.0 * nds + 256.0));
-  g->wcap = int(std::min(16000.0, 2.0 * p->beta * p->eta * nds + 256.0));
+  // temporal boundaries sit in the leg table as delimiters
+  if (g->ntau > 1) g->legs_want += double(g->ntau) * nds;
+  // Step-3 candidates of a domain: a Poisson count of mean 2 nds beta D;
+  // worms of a domain: mean beta eta <Q> <= beta eta nds (|<b + b+>| <= 1 a
+  // site); both tables hold the mean plus 16 standard deviations (a larger
+  // count stops the sweep with PMWA_ECAPACITY)
+  const double mc = 2.0 * nds * mb, mw = p->beta * p->eta * nds;
+  g->poolcap = int(std::min(60000.0, mc + 16.0 * std::sqrt(mc) + 128.0));
+  g->wcap = int(std::min(16000.0, mw + 16.0 * std::sqrt(mw) + 128.0));
 }
 
 struct Layout {
@@ -435,6 +445,9 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.exchange_every = p->exchange_every;
   d.zig_cap = 64;
   d.worm_tries = 128;
+  d.ntau = g.ntau;
+  d.tq = kTwo59 / uint64_t(g.ntau);
+  d.tr = kTwo59 % uint64_t(g.ntau);
   h->err = d.err;
   h->phase = reinterpret_cast<unsigned long long*>(base + L.phase);
   d.phase_cycles = nullptr;
@@ -503,6 +516,7 @@ int pmwa_tile_plan(const pmwa_params* p, int32_t* smem, int32_t* legcap, int32_t
   std::memset(&d, 0, sizeof d);
   d.Lx = p->Lx; d.Ly = p->Ly; d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy;
   d.sub_block = p->sub_block; d.wcap = g.wcap; d.poolcap = g.poolcap;
+  d.ntau = g.ntau;
   if (!plan_tile_smem(&d, g.legs_want, g.mb)) return PMWA_EINVAL;
   if (smem) *smem = d.sm_total;
   if (legcap) *legcap = d.legcap;
@@ -585,7 +599,7 @@ int pmwa_sweep(pmwa_handle* h, int64_t n) {
   if (!h || n < 0) return PMWA_EINVAL;
   if (h->broken) return PMWA_EINVARIANT;
   if (h->rows_pending + n > h->rows_cap) return PMWA_EROWS;
-  const bool multi = h->d.ndom > 1;
+  const bool multi = h->d.ndom > 1 || h->d.ntau > 1;
   for (int64_t k = 0; k < n; ++k) {
     Timed span{6, nullptr, nullptr};
     if (h->profiling) {
@@ -597,6 +611,7 @@ int pmwa_sweep(pmwa_handle* h, int64_t n) {
       h->d.sweep = uint32_t(h->sweep);
       const Dev& d = h->d;
       cudaStream_t st = h->stream;
+      if (d.ntau > 1 && timed_launch(h, 2, [&] { return launch_temporal(d, st); })) return PMWA_ECUDA;
       if (d.ndx > 1 && timed_launch(h, 0, [&] { return launch_boundary(d, 0, st); })) return PMWA_ECUDA;
       if (d.ndy > 1 && timed_launch(h, 0, [&] { return launch_boundary(d, 1, st); })) return PMWA_ECUDA;
     }
@@ -608,6 +623,14 @@ int pmwa_sweep(pmwa_handle* h, int64_t n) {
     }
     h->sweep++;
   }
+  return drain_error(h);
+}
+
+int pmwa_temporal(pmwa_handle* h) {
+  if (!h) return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
+  h->d.sweep = uint32_t(h->sweep);
+  if (h->d.ntau > 1 && launch_temporal(h->d, h->stream)) return PMWA_ECUDA;
   return drain_error(h);
 }
 
@@ -868,6 +891,40 @@ int pmwa_npoint(pmwa_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* 
   return PMWA_OK;
 }
 
+int pmwa_npoint_alpha(pmwa_handle* h, int32_t K, int32_t n, int64_t m, const int32_t* pts, double* out) {
+  if (!h || K < 1 || K > (1 << 20) || n < 1 || n > kMaxNpoint || m < 0 || (m > 0 && (!pts || !out)))
+    return PMWA_EINVAL;
+  if (h->broken) return PMWA_EINVARIANT;
+  const int64_t N = h->d.N;
+  for (int64_t j = 0; j < m; ++j) {
+    const int32_t* t = pts + size_t(j) * size_t(n) * 3;
+    for (int c = 0; c < n; ++c) {
+      if (t[3 * c] < 0 || t[3 * c] >= N || t[3 * c + 1] < 0 || t[3 * c + 1] >= K || (t[3 * c + 2] & ~1))
+        return PMWA_EINVAL;
+      for (int e = 0; e < c; ++e)  // one point twice: two operators at one time on one site
+        if (t[3 * e] == t[3 * c] && t[3 * e + 1] == t[3 * c + 1]) return PMWA_EINVAL;
+    }
+  }
+  if (m == 0) return PMWA_OK;
+  // scratch: the idle next-configuration slots hold a chunk of tuples and
+  // their results
+  const size_t room = size_t(N) * size_t(h->d.cap) * sizeof(uint64_t);
+  const size_t per = size_t(n) * 3 * sizeof(int32_t) + sizeof(double);
+  if (room < per + 16) return PMWA_EINVAL;
+  const size_t chunk = std::min(std::min(size_t(m), (room - 16) / per), size_t(1) << 28);
+  int32_t* tup = reinterpret_cast<int32_t*>(h->d.keyB);
+  double* res = reinterpret_cast<double*>(h->d.keyB) + ((chunk * size_t(n) * 3 * sizeof(int32_t) + 7) / 8);
+  for (size_t j0 = 0; j0 < size_t(m); j0 += chunk) {
+    const size_t c = std::min(chunk, size_t(m) - j0);
+    if (cudaStreamSynchronize(h->stream) ||
+        cudaMemcpy(tup, pts + j0 * size_t(n) * 3, c * size_t(n) * 3 * sizeof(int32_t), cudaMemcpyHostToDevice) ||
+        launch_npoint_alpha(h->d, K, n, int(c), tup, res, h->stream) || cudaStreamSynchronize(h->stream) ||
+        cudaMemcpy(out + j0, res, c * sizeof(double), cudaMemcpyDeviceToHost))
+      return PMWA_ECUDA;
+  }
+  return PMWA_OK;
+}
+
 int pmwa_check(pmwa_handle* h, int64_t* site, int32_t* what) {
   if (!h || !site || !what) return PMWA_EINVAL;
   *site = -1;
@@ -936,6 +993,7 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   L->inst_off.resize(size_t(n));
   for (int i = 0; i < n; ++i) {
     if (validate(p + i)) return false;
+    if (p[i].dom_tau > 1) return false;  // batches run instances without temporal domains
     Derived g;
     derive(p + i, &g);
     L->n_tile += g.ndom;
@@ -1151,7 +1209,7 @@ size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n) {
   if (!hs || n < 1 || n > 65536) return 0;
   int n_tile = 0, n_bw[2] = {0, 0};
   for (int i = 0; i < n; ++i) {
-    if (!hs[i]) return 0;
+    if (!hs[i] || hs[i]->d.ntau > 1) return 0;  // batches run instances without temporal domains
     const Dev& d = hs[i]->d;
     n_tile += d.ndom;
     n_bw[0] += d.ndx > 1 ? d.ndx * d.Ly : 0;

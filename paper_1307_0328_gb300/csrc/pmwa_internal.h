@@ -15,7 +15,7 @@ constexpr uint64_t kTwo62 = uint64_t(1) << 62;
 constexpr uint64_t kTwo32 = uint64_t(1) << 32;
 
 // Philox counter word c2 = phase | pass << 4 | replica << 16.
-enum Phase : uint32_t { kInit = 1, kBx = 2, kBy = 3, kVertex = 4, kRegen = 5, kScatter = 6 };
+enum Phase : uint32_t { kInit = 1, kBx = 2, kBy = 3, kVertex = 4, kRegen = 5, kScatter = 6, kTemporal = 7 };
 
 // Error word layout on the device: first error code wins (atomicCAS).
 struct DevErr {
@@ -79,6 +79,10 @@ struct Dev {
   // sampler; the deterministic specification fixes 64 and 128, smaller
   // values exist only to exercise the error path
   int zig_cap, worm_tries;
+  // temporal domains N_beta (1: none); boundary k at grid point
+  // m_k = k tq + (k tr) / ntau with 2^59 = tq ntau + tr, i.e. floor(k 2^59 / ntau)
+  int ntau;
+  uint64_t tq, tr;
 };
 
 // Per-instance state at the start of a batched call: the sweep index, the
@@ -120,6 +124,7 @@ int upload_zig(const Zig& z);       // constants of pmwa_kernels.cu
 int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int upload_zig_green(const Zig& z); // constants of pmwa_green.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
+int launch_temporal(const Dev& d, void* stream);  // Step 1, one warp per site
 int launch_tile(const Dev& d, int stop, void* stream);
 int tile_class(int domain_sites);
 // batch launch groups: 3 CTA-size classes x residency levels by shared memory
@@ -146,6 +151,9 @@ int launch_green_tau(const Dev& d, int K, int rmax, double* rho, double* sums, v
 constexpr int kMaxNpoint = 16;
 int launch_npoint(int K, int n, int m, const double* rho, const int32_t* sites, double eta, double* out,
                   void* stream);
+// component-resolved n-point functions of listed (site, slice, component)
+// tuples at arbitrary times (pmwa_npoint_alpha)
+int launch_npoint_alpha(const Dev& d, int K, int n, int m, const int32_t* pts, double* out, void* stream);
 constexpr int kCheckNone = 0x7fffffff;
 constexpr int kCheckCapacity = 1, kCheckTag = 2, kCheckOrder = 3, kCheckContinuity = 4, kCheckBase = 5,
               kCheckBond = 6, kCheckPartner = 7, kCheckConservation = 8;

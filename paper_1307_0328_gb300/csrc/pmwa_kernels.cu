@@ -72,13 +72,26 @@ struct Legs {
 
 // the two legs of the vertex at pv on a site: to the next vertex leg below
 // and above, worms ignored; one interval round the circle if v is alone.
-__device__ __noinline__ bool site_legs(const uint64_t* K, int n, uint64_t pv, Legs* L) {
+// With temporal domains a leg also ends at the nearest temporal boundary,
+// whose far state is the worldline's state there.
+__device__ __noinline__ bool site_legs(const Dev& d, const uint64_t* K, int n, uint64_t pv, Legs* L) {
   const int iv = slot_find(K, n, pv);
   if (iv < 0) return false;
   int jn = iv, jp = iv;
   for (int k = 0; k < n; ++k) { jn = (jn + 1 == n) ? 0 : jn + 1; if (jn == iv || !kworm(K[jn])) break; }
   for (int k = 0; k < n; ++k) { jp = (jp == 0) ? n - 1 : jp - 1; if (jp == iv || !kworm(K[jp])) break; }
   L->single = (jn == iv);
+  if (d.ntau > 1) {
+    const uint64_t bu = tb_pk(d, tb_above(d, pv)), bd = tb_pk(d, tb_below(d, pv));
+    if (L->single || up_dist(pv, bu) < up_dist(pv, kpk(K[jn]))) { L->phi = bu; L->far_up = slot_state(K, n, 0, bu); }
+    else { L->phi = kpk(K[jn]); L->far_up = kbl(K[jn]); }
+    if (L->single || up_dist(bd, pv) < up_dist(kpk(K[jp]), pv)) { L->plo = bd; L->far_dn = slot_state(K, n, 0, bd); }
+    else { L->plo = kpk(K[jp]); L->far_dn = kab(K[jp]); }
+    L->single = 0;
+    L->Iup = wpts(pv, L->phi);
+    L->Idn = wpts(L->plo, pv);
+    return true;
+  }
   if (L->single) { L->plo = L->phi = pv; L->Idn = L->Iup = kTwo59; L->far_dn = L->far_up = 0; return true; }
   L->phi = kpk(K[jn]); L->far_up = kbl(K[jn]); L->Iup = wpts(pv, L->phi);
   L->plo = kpk(K[jp]); L->far_dn = kab(K[jp]); L->Idn = wpts(L->plo, pv);
@@ -195,7 +208,7 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
     last = pv;
     any = true;
     Legs La, Lb;
-    if (!site_legs(KA, nA, pv, &La) || !site_legs(KB, nB, pv, &Lb)) return PMWA_EINVARIANT;
+    if (!site_legs(d, KA, nA, pv, &La) || !site_legs(d, KB, nB, pv, &Lb)) return PMWA_EINVARIANT;
     // heat-bath over the root states (Eq. 4), one lane per leg factor and one
     // lane per state; the weights are summed in the fixed order S = 0..15
     const int lane = threadIdx.x & 31;
@@ -366,6 +379,104 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_boundary_batch(const De
   const int wid = threadIdx.x >> 5;
   uint64_t* stage = reinterpret_cast<uint64_t*>(bsm + kZigBytes) + size_t(2 * wid) * cap;
   boundary_warp(sd, dir, w.y + wid, stage, Z);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 (temporal-boundary update, Eq. 3), one warp per site, in place on
+// the current configuration.  Boundary k lies in the interval I = I2 + I1
+// between the nearest delimiters below and above it (vertex legs or other
+// temporal boundaries, worms ignored): I2 from the lower delimiter (state p
+// just above it) up to the boundary, I1 from the boundary up to the upper one
+// (state q just below it).  The new state s' is drawn with P(s') =
+// f_{q s'}(I1) f_{s' p}(I2) / f_{q p}(I); with f_{ab}(x) = e^x F(a ^ b, x) / 2,
+// F(0, x) = 2 + expm1(-2x), F(1, x) = -expm1(-2x), the e^x / 2 are common to
+// both s' and drop out.  The worms of I2 and then I1 are drawn anew (Eq. 1).
+// The boundaries of a site go in order k = 0, 1, ..., each a heat bath given
+// the current states of the others; sites are independent.  Every lane runs
+// the same update on the staged list, as in the spatial boundary step.
+
+// the nearest delimiter of boundary k going down (up = false) or up: its pk
+// and the state on the side facing the boundary
+__device__ __forceinline__ void tb_delim(const Dev& d, const uint64_t* K, int n, int base, int k, bool up,
+                                         uint64_t* pk, int* st) {
+  const uint64_t B = tb_pk(d, k);
+  const int kb = up ? (k + 1) % d.ntau : (k + d.ntau - 1) % d.ntau;
+  uint64_t best = tb_pk(d, kb);
+  int leg = -1;
+  if (n > 0) {
+    // the nearest vertex leg in that direction, cyclic (worms skipped)
+    const int i0 = slot_lower(K, n, B);  // first event above B
+    for (int c = 0; c < n; ++c) {
+      const int i = up ? (i0 + c) % n : (i0 + n - 1 - c) % n;
+      if (kworm(K[i])) continue;
+      const uint64_t q = kpk(K[i]);
+      if (up ? up_dist(B, q) < up_dist(B, best) : up_dist(q, B) < up_dist(best, B)) { best = q; leg = i; }
+      break;
+    }
+  }
+  *pk = best;
+  *st = (leg >= 0) ? (up ? kbl(K[leg]) : kab(K[leg])) : slot_state(K, n, base, best);
+}
+
+__device__ int temporal_site(const Dev& d, int s, uint64_t* K, int& n, int& base, const ZigTab& Z) {
+  Stream st;
+  st.init(d.key0, d.key1, uint32_t(s), c2_word(kTemporal, 0, d.replica), d.sweep);
+  for (int k = 0; k < d.ntau; ++k) {
+    const uint64_t B = tb_pk(d, k);
+    uint64_t lo, hi;
+    int p, q;
+    tb_delim(d, K, n, base, k, false, &lo, &p);
+    tb_delim(d, K, n, base, k, true, &hi, &q);
+    const double e1 = em1_of(wpts(B, hi), d.XW), e2 = em1_of(wpts(lo, B), d.XW);
+    const double w0 = __dmul_rn(fsig(q, e1), fsig(p, e2));
+    const double w1 = __dmul_rn(fsig(q ^ 1, e1), fsig(1 ^ p, e2));
+    const double tot = __dadd_rn(w0, w1);
+    if (!(tot > 0.0)) return PMWA_EINVARIANT;
+    const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
+    const int sn = (u < w0) ? 0 : 1;
+    int rc = regen_interval(d, Z, st, K, n, lo, B, p, sn);
+    if (!rc) rc = regen_interval(d, Z, st, K, n, B, hi, sn, q);
+    if (rc) return rc;
+    if (n == 0) base = sn;
+  }
+  if (st.pos >= (uint64_t(1) << 33)) return PMWA_ETIMEOUT;
+  return PMWA_OK;
+}
+
+constexpr int kTemporalWarps = 4;  // sites (warps) per block
+
+__global__ void __launch_bounds__(32 * kTemporalWarps) k_temporal(const __grid_constant__ Dev d) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  if (instance_failed(d.err)) return;
+  const ZigTab Z = zig_stage(tsm, d.zig_cap, d.worm_tries);
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = int(blockIdx.x) * kTemporalWarps + wid;
+  if (s >= d.N) return;
+  uint64_t* K = reinterpret_cast<uint64_t*>(tsm + kZigBytes) + size_t(wid) * d.cap;
+  const uint32_t c = d.cntA[s];
+  int n = cnt_n(c), base = cnt_base(c);
+  const uint64_t* g = d.keyA + size_t(s) * d.cap;
+  for (int k = lane; k < n; k += 32) K[k] = g[k];
+  __syncwarp();
+  const int rc = temporal_site(d, s, K, n, base, Z);
+  __syncwarp();
+  if (rc) {
+    if (lane == 0) set_err(d.err, rc, 1);
+    return;
+  }
+  uint64_t* w = d.keyA + size_t(s) * d.cap;
+  for (int k = lane; k < n; k += 32) w[k] = K[k];
+  if (lane == 0) d.cntA[s] = cnt_make(n, n ? kab(K[n - 1]) : base);
+}
+
+int launch_temporal(const Dev& d, void* stream) {
+  if (d.ntau < 2) return 0;
+  const size_t smem = size_t(kZigBytes) + size_t(kTemporalWarps) * size_t(d.cap) * 8;
+  cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e) return int(e);
+  k_temporal<<<blocks_for(d.N, kTemporalWarps), 32 * kTemporalWarps, smem, cudaStream_t(stream)>>>(d);
+  return int(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------

@@ -39,8 +39,8 @@ struct WormRec {
   uint64_t key;
   uint64_t lab;
   uint16_t site;  // local site index
-  uint16_t leg;   // leg array index of the vertex leg just below (kNone: site without legs)
-  uint32_t pad;
+  uint16_t leg;   // leg array index of the delimiter just below (kNone: site without legs)
+  uint32_t slab;  // temporal slab (0 without temporal domains); fixed through Step 5
 };
 
 struct Misc {
@@ -48,6 +48,7 @@ struct Misc {
   int nworms;
   int err;
   int where;
+  int wslab[64];  // worms of each temporal slab of the domain
 };
 
 __device__ __forceinline__ int cnt_n(uint32_t c) { return int(c & kCntMask); }
@@ -117,6 +118,7 @@ struct Tile {
   uint64_t* old;   // [oldcap] the domain's current configuration (when staged)
   bool staged;
   int x0, y0, nds, nsub;
+  int ngrp;  // Step-5 chains: sub-blocks x temporal slabs
 
   __device__ int gsite(int li) const { return (x0 + li % d->dom_x) + d->Lx * (y0 + li / d->dom_x); }
   // current events of local site li (global site s): the staged copy or HBM
@@ -237,6 +239,7 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   }
   const int iv = up ? ((L + 1 == en) ? st : L + 1) : L;
   const uint64_t pv = kpk(T.leg[iv]);
+  if (ktag(T.leg[iv]) == 6) { w.key = key ^ 2u; return PMWA_OK; }  // a temporal boundary
   const int nb = T.nbr[li * 6 + ktag(T.leg[iv])];
   if (nb < 0) { w.key = key ^ 2u; return PMWA_OK; }   // bond to another domain
   const int pl = nb >> 1;
@@ -318,6 +321,13 @@ __device__ __forceinline__ void phase_tick(const Dev& d, int k, long long& t) {
   }
 }
 
+// Step-5 chain of a worm in pass pattern q: its sub-block times N_beta plus
+// its temporal slab (a worm never leaves its slab: it turns round at the
+// boundaries and every leg ends there)
+__device__ __forceinline__ int worm_group(const Tile& T, const WormRec& w, int q) {
+  return int(T.sub[w.site * 4 + q]) * T.d->ntau + int(w.slab);
+}
+
 __device__ __forceinline__ bool worm_less(const WormRec& a, const WormRec& b) {
   if (a.lab != b.lab) return a.lab < b.lab;
   if (a.site != b.site) return a.site < b.site;
@@ -336,7 +346,7 @@ __device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t blo,
 // its bucket.  Uses bkt/fill as bucket counters and idx as scratch.
 __device__ void label_order(const Tile& T, int nw, int* wsum) {
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int cap = max(T.nsub, T.nds);
+  const int cap = max(T.ngrp, T.nds);
   int B = 0;
   while ((2 << B) <= cap && (1 << B) < nw) ++B;
   const int nbk = 1 << B;
@@ -370,7 +380,7 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
   const unsigned lt = (1u << lane) - 1u;
   for (int k0 = 0; k0 < nw; k0 += 32) {
     const int k = k0 + lane;
-    const int u = (k < nw) ? int(T.sub[T.W[T.ord[k]].site * 4 + q]) : -1;
+    const int u = (k < nw) ? worm_group(T, T.W[T.ord[k]], q) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     const int base = (u >= 0) ? T.bkt[u] : 0;
     __syncwarp();
@@ -381,7 +391,7 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
     }
     __syncwarp();
   }
-  const int n = T.nsub;
+  const int n = T.ngrp;
   const int chunk = (n + 31) / 32;
   const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
   int sum = 0;
@@ -414,12 +424,12 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
 __device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_out, int& r_out) {
   const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const int W = (nw + 31) >> 5, n = T.nsub;
+  const int W = (nw + 31) >> 5, n = T.ngrp;
   const int stamp = (pass + 1) << 16;
   const int k = tid;
   int u = -1, r = 0;
   if (c < W) {  // warp-uniform
-    u = (k < nw) ? int(T.sub[T.W[T.ord[k]].site * 4 + q]) : -1;
+    u = (k < nw) ? worm_group(T, T.W[T.ord[k]], q) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     r = __popc(peers & lt);
     if (u >= 0 && (peers & lt) == 0) T.cnt[c * n + u] = stamp | __popc(peers);
@@ -476,7 +486,7 @@ __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
   const int w = act ? T.ord[lane] : 0;
   for (int pass = 0; pass < d.n_cycle; ++pass) {
     const int q = pass & 3;
-    const int u = act ? int(T.sub[T.W[w].site * 4 + q]) : 0x7fffffff;
+    const int u = act ? worm_group(T, T.W[w], q) : 0x7fffffff;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     const int r = __popc(peers & lt), n = __popc(peers);
     int less = 0;  // worms of sub-blocks numbered below u: the start of u's group
@@ -484,7 +494,7 @@ __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
     if (act) T.idx[less + r] = uint16_t(w);
     const int maxr = __reduce_max_sync(0xffffffffu, act ? r : 0);
     P4 b{0u, 0u, 0u, 0u};
-    if (act) b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2_word(kScatter, uint32_t(pass), d.replica),
+    if (act) b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2_word(kScatter, uint32_t(pass), d.replica),
                         d.sweep, d.key0, d.key1);
     __syncwarp();
     int rc = PMWA_OK;
@@ -536,6 +546,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.y0 = (dom / d.ndx) * d.dom_y;
   T.nds = d.dom_x * d.dom_y;
   T.nsub = sb_slots(d.dom_x, d.sub_block, d.ndx) * sb_slots(d.dom_y, d.sub_block, d.ndy);
+  T.ngrp = T.nsub * d.ntau;
   const int tid = threadIdx.x, NT = blockDim.x, nds = T.nds;
   Misc* misc = T.misc;
 
@@ -543,6 +554,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   const ZigTab Z = zig_stage(sm + d.sm_zig, d.zig_cap, d.worm_tries);
   for (int k = tid; k < 256; k += NT) T.th[k] = d.TH[k];
   if (tid == 0) { misc->pool_used = 0; misc->nworms = 0; misc->err = 0; misc->where = 0; }
+  for (int k = tid; k < d.ntau; k += NT) misc->wslab[k] = 0;
   // per-site tables: bond partners by leg tag, sub-blocks by offset pattern
   for (int li = tid; li < nds; li += NT) {
     for (int t = 0; t < 6; ++t) { T.nbr[li * 6 + t] = -1; T.tinfo[li * 6 + t] = 0; }
@@ -614,6 +626,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     int lb[4];
     site_bonds(T, li, lb);
     for (int j = 0; j < 4; ++j) if (lb[j] >= 0) c += T.bcnt[lb[j]];
+    if (d.ntau > 1) c += d.ntau;  // the temporal boundaries, as delimiters of tag 6
     T.off[li] = c;
   }
   __syncthreads();
@@ -628,6 +641,11 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     site_bonds(T, li, lb);
     for (int j = 0; j < 4; ++j) cn[j] = lb[j] >= 0 ? T.bcnt[lb[j]] : 0;
     int io = 0, o = T.off[li];
+    // temporal boundaries join the legs as delimiters (tag 6) whose state
+    // above and below is the worldline's state there in the current
+    // configuration (Step 3 changes no state)
+    const int NB = d.ntau > 1 ? d.ntau : 0, base0 = cnt_base(d.cntA[s]);
+    int ib = 0;
     for (;;) {
       while (io < nO && !kept_leg(T.tinfo + li * 6, KO[io])) ++io;
       uint64_t best = ~0ull;
@@ -638,10 +656,15 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           const uint64_t p = T.pool[T.boff[lb[j]] + ci[j]] >> 2;
           if (p < best) { best = p; src = j; }
         }
+      if (ib < NB && tb_pk(d, ib) < best) { best = tb_pk(d, ib); src = 5; }
       if (src < 0) break;
       uint64_t key;
       if (src == 4) key = KO[io++];
-      else {
+      else if (src == 5) {
+        const uint64_t bst = uint64_t(slot_state(KO, nO, base0, best));
+        key = (best << 2) | (bst << 1) | bst;
+        ++ib;
+      } else {
         const uint64_t c = T.pool[T.boff[lb[src]] + ci[src]++];
         const uint64_t st = (c >> (src < 2 ? 0 : 1)) & 1;
         key = ((c >> 2) << 2) | (st << 1) | st;
@@ -671,6 +694,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       for (; j < jend; ++j) {
         while (T.off[li + 1] <= j) ++li;
         const uint64_t key = T.leg[j];
+        if (ktag(key) == 6) continue;  // a temporal boundary
         const int nb = T.nbr[li * 6 + ktag(key)];
         if (nb < 0 || (nb & 1) == 0) continue;
         const int ip = leg_index(T, nb >> 1, kpk(key));
@@ -698,6 +722,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         const int n = sample_worms<kMaxWormsPerInterval>(Z, rs, kTwo59, 0, d.SWs, d.SWI, offs, &bad);
         if (!bad && n > 0) {
           const int o = atomicAdd(&misc->nworms, n);
+          atomicAdd(&misc->wslab[0], n);
           if (o + n > d.wcap) bad = PMWA_ECAPACITY;
           for (int k = 0; k < n && !bad; ++k) {
             const uint64_t w = rs.word();
@@ -705,7 +730,9 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           }
         }
       } else {
-        T.base[li] = 0;
+        // (the state of a site whose delimiters are temporal boundaries only
+        // and which keeps no worm: all its boundary states are equal)
+        T.base[li] = uint8_t(kab(T.leg[st]));
         for (int k = 0; k < nl && !bad; ++k) {
           const uint64_t lo = T.leg[st + k], hi = T.leg[st + (k + 1 == nl ? 0 : k + 1)];
           const uint64_t M = wpts(kpk(lo), kpk(hi));
@@ -717,10 +744,13 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           const int o = atomicAdd(&misc->nworms, n);
           if (o + n > d.wcap) { bad = PMWA_ECAPACITY; break; }
           const uint64_t m0 = wm_above(kpk(lo));
+          // an interval lies inside one temporal slab (boundaries delimit it)
+          const int sl = slab_of_m(d, m0);
+          atomicAdd(&misc->wslab[sl], n);
           for (int j = 0; j < n; ++j) {
             const uint64_t w = rs.word();
             T.W[o + j] = WormRec{wkey((m0 + offs[j]) & (kTwo59 - 1), int(w & 1), p ^ 1 ^ (j & 1)), w >> 1,
-                                 uint16_t(li), uint16_t(st + k), 0u};
+                                 uint16_t(li), uint16_t(st + k), uint32_t(sl)};
           }
         }
       }
@@ -738,8 +768,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       // inside the sub-block of offset pattern p & 3 that holds its site, in
       // label order; the r-th move of sub-block u draws Philox block r of
       // stream (unit = domain * n_sub + u, scatter | pass).
-      for (int u = tid; u < T.nsub; u += NT) T.bkt[u] = 0;
-      for (int i = tid; i < (NT >> 5) * T.nsub; i += NT) T.cnt[i] = 0;  // no stamp of this sweep
+      for (int u = tid; u < T.ngrp; u += NT) T.bkt[u] = 0;
+      for (int i = tid; i < (NT >> 5) * T.ngrp; i += NT) T.cnt[i] = 0;  // no stamp of this sweep
       __syncthreads();
       if (nw > 0 && nw <= 32) {  // few worms: one warp, no block barrier per pass
         if (tid < 32) {
@@ -758,7 +788,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           int u, r;
           rank_pass_block(T, nw, q, pass, u, r);
           P4 b{0u, 0u, 0u, 0u};
-          if (u >= 0) b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+          if (u >= 0) b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
           __syncthreads();
           if (u >= 0) {
             const int at = T.fill[u] + r;
@@ -772,14 +802,14 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           for (int k = tid; k < nw; k += NT) {
             const int u = T.wsb[k], r = T.wrk[k], at = T.fill[u] + r;
             T.idx[at] = T.ord[k];
-            const P4 b = philox(uint32_t(r), uint32_t(dom * T.nsub + u), c2, d.sweep, d.key0, d.key1);
+            const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
             T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
             T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
           }
         }
         __syncthreads();
         phase_tick(d, 5, tclk);
-        for (int u = tid; u < T.nsub; u += NT) {
+        for (int u = tid; u < T.ngrp; u += NT) {
           const int lo = T.fill[u], n = T.fill[u + 1] - lo;
           const uint16_t* seg = T.idx + lo;
           for (int r = 0; r < n; ++r) {
@@ -832,7 +862,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       // merge legs with worms (stop 3: the old worms); the occupied time of
       // the intervals between consecutive events is summed as they are
       // written (Step 6), the interval round the circle after the last one
-      int il = 0, iw = 0, io = 0, no = 0;
+      int il = 0, iw = 0, io = 0, no = 0, nww = 0;
       bool bad = false;
       uint64_t occ = 0, first_pk = 0, prev = 0;
       for (;;) {
@@ -845,8 +875,15 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         const uint64_t lk = il < nl ? T.leg[st + il] : ~0ull;
         if (lk == ~0ull && wk == ~0ull) break;
         uint64_t key;
-        if (kpk(lk) < kpk(wk) || wk == ~0ull) { key = lk; ++il; }
-        else { key = wk; if (stop >= 4) ++iw; else ++io; }
+        if (kpk(lk) < kpk(wk) || wk == ~0ull) {
+          key = lk;
+          ++il;
+          if (ktag(key) == 6) continue;  // a temporal boundary is no event
+        } else {
+          key = wk;
+          ++nww;
+          if (stop >= 4) ++iw; else ++io;
+        }
         if (no >= d.cap) { bad = true; break; }
         if (no == 0) first_pk = kpk(key);
         else if (kab(prev)) occ += (kpk(key) - kpk(prev)) & kMask62;
@@ -865,7 +902,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       else if (no == 1) occ = kab(prev) ? kTwo62 : 0;
       else if (kab(prev)) occ += (first_pk - kpk(prev)) & kMask62;
       add128(olo, ohi, occ, 0);
-      nwc += uint64_t(no - nl);
+      nwc += uint64_t(nww);
       if (nl == 0) {
         uint64_t v;
         if (xg_fix(0, kTwo59, d.XQ, v)) add128(qlo, qhi, v, 0);
@@ -891,7 +928,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           while (T.off[li + 1] <= j) ++li;
           const uint64_t lo = T.leg[j];
           const uint64_t hi = T.leg[(j + 1 == T.off[li + 1]) ? T.off[li] : j + 1];
-          if (T.tinfo[li * 6 + ktag(lo)] & 1) { ++nv; if (kab(lo) != kbl(lo)) ++nk; }
+          if (ktag(lo) < 6 && (T.tinfo[li * 6 + ktag(lo)] & 1)) { ++nv; if (kab(lo) != kbl(lo)) ++nk; }
           const uint64_t I = wpts(kpk(lo), kpk(hi));
           const int sg = kab(lo) ^ kbl(hi);
           uint64_t v;
@@ -927,11 +964,17 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       }
       if (dom == 0 && tid == 0) d.rows[d.row].sweep = d.sweep;
       if (tid == 0) {
-        // worms per domain: the fewest (kept as a complement, so that the
-        // zeroed row and an atomic maximum give the minimum) and the empty ones
+        // worms per (space-time) domain: the fewest (kept as a complement, so
+        // that the zeroed row and an atomic maximum give the minimum) and the
+        // empty ones
         pmwa_row* r = d.rows + d.row;
-        atomicMax(&r->w_dom_min, ~uint32_t(nw));
-        if (nw == 0) atomicAdd(&r->dom_empty, 1u);
+        unsigned wmin = ~0u, empty = 0;
+        for (int k = 0; k < d.ntau; ++k) {
+          wmin = min(wmin, unsigned(misc->wslab[k]));
+          empty += misc->wslab[k] == 0 ? 1u : 0u;
+        }
+        atomicMax(&r->w_dom_min, ~wmin);
+        if (empty) atomicAdd(&r->dom_empty, empty);
       }
     }
     __syncthreads();
@@ -978,7 +1021,9 @@ __global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
 // shared memory of an SM over the per-CTA size plus its 1 KB reserve).
 bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const int nds = d->dom_x * d->dom_y;
-  const int nsub = sb_slots_host(d->dom_x, d->sub_block, d->ndx) * sb_slots_host(d->dom_y, d->sub_block, d->ndy);
+  // Step-5 chains: sub-blocks x temporal slabs
+  const int nsub = sb_slots_host(d->dom_x, d->sub_block, d->ndx) * sb_slots_host(d->dom_y, d->sub_block, d->ndy) *
+                   std::max(1, d->ntau);
   const int nb = std::max(nsub, nds) + 1;
   auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
   size_t o = 0;

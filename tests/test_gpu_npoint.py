@@ -76,3 +76,52 @@ def test_npoint_arguments():
             assert e.value.status == P.PMWA_EINVAL, (K, t)
     finally:
         g.close()
+
+
+# ---- resolved by the component of Q at arbitrary times (pmwa_npoint_alpha)
+
+def _alpha_tuples(rng, N, K, m, n, same_site):
+    """m tuples of n points (site, slice, component); with same_site, every
+    tuple puts its points on at most two sites, so that several share an
+    interval (the multi-point interval form) or a circle without legs."""
+    out = np.zeros((m, n, 3), dtype=np.int32)
+    for j in range(m):
+        sites = rng.choice(N, size=2, replace=False) if same_site else rng.choice(N, size=n, replace=N < n)
+        seen = set()
+        for c in range(n):
+            while True:
+                s = int(sites[rng.integers(0, len(sites))]) if same_site else int(sites[c])
+                k = int(rng.integers(0, K))
+                if (s, k) not in seen:
+                    break
+            seen.add((s, k))
+            out[j, c] = (s, k, int(rng.integers(0, 2)))
+    return out
+
+
+@pytest.mark.parametrize("kw", GEOMS + [dict(Lx=8, Ly=8, beta=4.0, eta=0.2, dom_tau=3, n_cycle=6, seed=41)])
+def test_npoint_alpha_matches_oracle(kw):
+    g, o = _pair(kw)
+    N = kw["Lx"] * kw["Ly"]
+    rng = np.random.default_rng(N)
+    for K, n, m, same in [(1, 1, 37, False), (8, 2, 130, True), (8, 3, 129, True), (12, 4, 70, True),
+                          (16, 4, 65, False), (6, 5, 33, True), (8, 16, 9, False)]:
+        if n > K * (2 if same else N):
+            continue
+        pts = _alpha_tuples(rng, N, K, m, n, same)
+        got = g.npoint_alpha(K, pts)
+        want = o.npoint_alpha(K, pts)
+        assert np.allclose(got, want, rtol=REL, atol=1e-300), (K, n, same)
+
+
+def test_npoint_alpha_argument_errors():
+    g = P.Sim(Lx=4, Ly=4, beta=1.0, eta=0.3, n_cycle=4, seed=3)
+    g.sweep(2)
+    bad = [np.array([[[0, 1, 0], [0, 1, 1]]]),   # one (site, slice) twice
+           np.array([[[16, 0, 0]]]),             # site out of range
+           np.array([[[0, 8, 0]]]),              # slice out of range
+           np.array([[[0, 0, 2]]])]              # no such component
+    for pts in bad:
+        with pytest.raises(P.PmwaError) as e:
+            g.npoint_alpha(8, pts)
+        assert e.value.status == P.PMWA_EINVAL

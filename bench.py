@@ -39,11 +39,16 @@ WORKLOADS = {
                     exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
     "8x8_bt2": dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, dom_x=8, dom_y=8,
                     exchange_every=2, sub_block=0, init=1, init_seed=1, seed=1),
+    # the 2048x2048 workload's domains and temperature on 1/16 of the sites
+    # (for profiler captures that must stay small)
+    "512x512_bt16": dict(Lx=512, Ly=512, beta=16.0, t=1.0, V=0.0, mu=0.0, eta=0.1, dom_x=16, dom_y=16,
+                    exchange_every=2, sub_block=2, init=1, init_seed=7, seed=7),
 }
 DESCR = {
     "256x256_bt4": "256x256 periodic hcBH, t=1 V=0 mu=0 beta*t=4 eta=0.1, 16x16-site domains, K=2",
     "2048x2048_bt16": "2048x2048 periodic hcBH, t=1 V=0 mu=0 beta*t=16 eta=0.1, 128x128 domains of 16x16 sites, K=2",
     "8x8_bt2": "8x8 periodic hcBH, t=1 V=0 mu=0 beta*t=2 eta=0.2, one domain",
+    "512x512_bt16": "512x512 periodic hcBH, t=1 V=0 mu=0 beta*t=16 eta=0.1, 32x32 domains of 16x16 sites, K=2",
 }
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -504,12 +509,12 @@ def large_leg(P, args, flush):
     kernels = {k: dict(ms_total=v[0], launches=v[1]) for k, v in prof.items() if v[1]}
     t = prof["sweep"][0] / 1000.0
     peak, which = peaks()
-    ob = P.summary(rows, sim.params, bins=min(10, len(rows)))
+    ob = P.summary(rows, sim.params, bins=min(10, len(rows))) if len(rows) >= 2 else {}
     out = dict(workload=DESCR[wl], value=float(rows["n_v"].sum()) / t, unit=UNIT, steps=args.large_steps,
                ms_per_step=1000.0 * t / args.large_steps, n_cycle=nc, legs_hint=kw["legs_hint"],
                pilot_sweeps=args.large_pilot, mean_vertices=float(rows["n_v"].mean()),
-               mean_worms=float(rows["n_w"].mean()), worms_per_domain=ob["w_dom_mean"],
-               worms_per_domain_min=ob["w_dom_min"], empty_domain_fraction=ob["dom_empty_frac"],
+               mean_worms=float(rows["n_w"].mean()), worms_per_domain=ob.get("w_dom_mean"),
+               worms_per_domain_min=ob.get("w_dom_min"), empty_domain_fraction=ob.get("dom_empty_frac"),
                l2="configuration larger than L2 (no flush needed)",
                roofline=roofline_of(kernels, rows, kw, wl, peak, which), kernels=kernels, clocks=clk)
     sim.close()
@@ -647,7 +652,7 @@ def main():
     # single-particle G(r, tau)
     est = None
     if rank == 0:
-        ob = P.summary(rows, sim.params, bins=10)
+        ob = P.summary(rows, sim.params, bins=min(10, len(rows))) if len(rows) >= 2 else {"Q_impr": None}
         rmax = min(4, min(kw["Lx"], kw["Ly"]) // 2)
         t0 = time.perf_counter()
         gx, gy, plaq = P.pmwa_green(sim.h, 16, rmax)

@@ -959,6 +959,9 @@ struct pmwa_batch {
   int2* tile_work = nullptr;  // grouped by launch group (see batch_group)
   int2* bwork[2] = {nullptr, nullptr};
   int n_tile = 0, n_bwork[2] = {0, 0}, cap_max = 0;
+  int2* twork = nullptr;  // Step 1: blocks of sites of instances with temporal domains
+  int n_twork = 0;
+  int tcls_off[kBatchGroups] = {}, tcls_n[kBatchGroups] = {};
   // per launch group: work range, CTA-size class, dynamic shared memory
   int cls_off[kBatchGroups] = {}, cls_n[kBatchGroups] = {}, cls_smem[kBatchGroups] = {}, cls_thr[kBatchGroups] = {};
   int bcls_off[2][kBatchGroups] = {}, bcls_n[2][kBatchGroups] = {};
@@ -976,9 +979,9 @@ struct pmwa_batch {
 namespace {
 
 struct BatchLayout {
-  size_t devs, base, errs, tile, bw[2], tables, total;
+  size_t devs, base, errs, tile, bw[2], tw, tables, total;
   std::vector<size_t> inst_off, inst_bytes;
-  int n_tile, n_bw[2];
+  int n_tile, n_bw[2], n_tw;
 };
 
 int boundary_bonds(const pmwa_params* p, const Derived& g, int dir) {
@@ -988,14 +991,14 @@ int boundary_bonds(const pmwa_params* p, const Derived& g, int dir) {
 
 bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   if (n < 1 || n > 65536 || !p) return false;
-  L->n_tile = 0; L->n_bw[0] = L->n_bw[1] = 0;
+  L->n_tile = 0; L->n_bw[0] = L->n_bw[1] = 0; L->n_tw = 0;
   L->inst_bytes.resize(size_t(n));
   L->inst_off.resize(size_t(n));
   for (int i = 0; i < n; ++i) {
     if (validate(p + i)) return false;
-    if (p[i].dom_tau > 1) return false;  // batches run instances without temporal domains
     Derived g;
     derive(p + i, &g);
+    if (g.ntau > 1) L->n_tw += g.N;  // upper bound: one site per block
     L->n_tile += g.ndom;
     for (int dir = 0; dir < 2; ++dir)
       L->n_bw[dir] += boundary_bonds(p + i, g, dir);  // upper bound: one bond per block
@@ -1007,6 +1010,7 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   L->errs = o; o = align_up(o + size_t(n) * sizeof(DevErr));
   L->tile = o; o = align_up(o + size_t(std::max(1, L->n_tile)) * sizeof(int2));
   for (int dir = 0; dir < 2; ++dir) { L->bw[dir] = o; o = align_up(o + size_t(std::max(1, L->n_bw[dir])) * sizeof(int2)); }
+  L->tw = o; o = align_up(o + size_t(std::max(1, L->n_tw)) * sizeof(int2));
   L->tables = o;
   for (int i = 0; i < n; ++i) { L->inst_off[size_t(i)] = o; o = align_up(o + L->inst_bytes[size_t(i)]); }
   L->total = o;
@@ -1073,6 +1077,21 @@ int build_boundary_work(pmwa_batch* b) {
     if (!bw.empty() && cudaMemcpy(b->bwork[dir], bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
       return PMWA_ECUDA;
   }
+  // Step 1 of the instances with temporal domains: blocks of sites
+  const int spb = temporal_sites_per_block();
+  bw.clear();
+  for (int g = 0; g < kBatchGroups; ++g) {
+    b->tcls_off[g] = int(bw.size());
+    for (int i = 0; i < b->n; ++i) {
+      const Dev& d = b->h[size_t(i)]->d;
+      if (batch_group(d) != g || d.ntau < 2) continue;
+      for (int s0 = 0; s0 < d.N; s0 += spb) bw.push_back(make_int2(i, s0));
+    }
+    b->tcls_n[g] = int(bw.size()) - b->tcls_off[g];
+  }
+  b->n_twork = int(bw.size());
+  if (!bw.empty() && cudaMemcpy(b->twork, bw.data(), bw.size() * sizeof(int2), cudaMemcpyHostToDevice))
+    return PMWA_ECUDA;
   return PMWA_OK;
 }
 
@@ -1124,8 +1143,12 @@ void batch_drop_graph(pmwa_batch* b) {
   b->graph_sweeps = 0;
 }
 
-// One sweep of the instances of launch group g: boundary x, boundary y, tile.
+// One sweep of the instances of launch group g: temporal boundaries, boundary
+// x, boundary y, tile.
 int batch_launch_class(pmwa_batch* b, int it, int g, cudaStream_t st) {
+  if (b->tcls_n[g] &&
+      launch_temporal_batch(b->devs, b->base, b->twork + b->tcls_off[g], b->tcls_n[g], it, b->cap_max, st))
+    return PMWA_ECUDA;
   for (int dir = 0; dir < 2; ++dir)
     if (b->bcls_n[dir][g] && launch_boundary_batch(b->devs, b->base, b->bwork[dir] + b->bcls_off[dir][g],
                                                    b->bcls_n[dir][g], it, dir, b->cap_max, st))
@@ -1137,6 +1160,8 @@ int batch_launch_class(pmwa_batch* b, int it, int g, cudaStream_t st) {
 }
 
 int batch_launch_sweep(pmwa_batch* b, int it, cudaStream_t st) {
+  if (b->n_twork && launch_temporal_batch(b->devs, b->base, b->twork, b->n_twork, it, b->cap_max, st))
+    return PMWA_ECUDA;
   for (int dir = 0; dir < 2; ++dir)
     if (b->n_bwork[dir] &&
         launch_boundary_batch(b->devs, b->base, b->bwork[dir], b->n_bwork[dir], it, dir, b->cap_max, st))
@@ -1174,6 +1199,7 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
   b->tile_work = reinterpret_cast<int2*>(base + L.tile);
   b->bwork[0] = reinterpret_cast<int2*>(base + L.bw[0]);
   b->bwork[1] = reinterpret_cast<int2*>(base + L.bw[1]);
+  b->twork = reinterpret_cast<int2*>(base + L.tw);
   b->n_tile = L.n_tile;
   b->n_bwork[0] = L.n_bw[0];
   b->n_bwork[1] = L.n_bw[1];
@@ -1193,7 +1219,7 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
     rc = PMWA_ECUDA;
   if (rc == PMWA_OK) rc = build_boundary_work(b);
   if (rc == PMWA_OK) rc = batch_upload(b);
-  if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (prepare_boundary(b->cap_max) || prepare_temporal(b->cap_max))) rc = PMWA_ECUDA;
   if (rc == PMWA_OK) rc = batch_streams(b);
   if (rc) {
     for (pmwa_handle* hi : b->h) if (hi) pmwa_destroy(hi);
@@ -1207,10 +1233,11 @@ int pmwa_batch_create(const pmwa_params* p, int32_t n, void* arena, size_t bytes
 
 size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n) {
   if (!hs || n < 1 || n > 65536) return 0;
-  int n_tile = 0, n_bw[2] = {0, 0};
+  int n_tile = 0, n_bw[2] = {0, 0}, n_tw = 0;
   for (int i = 0; i < n; ++i) {
-    if (!hs[i] || hs[i]->d.ntau > 1) return 0;  // batches run instances without temporal domains
+    if (!hs[i]) return 0;
     const Dev& d = hs[i]->d;
+    if (d.ntau > 1) n_tw += d.N;
     n_tile += d.ndom;
     n_bw[0] += d.ndx > 1 ? d.ndx * d.Ly : 0;
     n_bw[1] += d.ndy > 1 ? d.ndy * d.Lx : 0;
@@ -1221,6 +1248,7 @@ size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n) {
   o = align_up(o + size_t(n) * sizeof(DevErr));
   o = align_up(o + size_t(std::max(1, n_tile)) * sizeof(int2));
   for (int dir = 0; dir < 2; ++dir) o = align_up(o + size_t(std::max(1, n_bw[dir])) * sizeof(int2));
+  o = align_up(o + size_t(std::max(1, n_tw)) * sizeof(int2));
   return o;
 }
 
@@ -1264,9 +1292,10 @@ int pmwa_batch_from_handles(pmwa_handle* const* hs, int32_t n, void* arena, size
     }
     o = align_up(o + size_t(std::max(1, nb_total)) * sizeof(int2));
   }
+  b->twork = reinterpret_cast<int2*>(base + o);
   if (rc == PMWA_OK) rc = build_boundary_work(b);
   if (rc == PMWA_OK) rc = batch_upload(b);
-  if (rc == PMWA_OK && prepare_boundary(b->cap_max)) rc = PMWA_ECUDA;
+  if (rc == PMWA_OK && (prepare_boundary(b->cap_max) || prepare_temporal(b->cap_max))) rc = PMWA_ECUDA;
   if (rc == PMWA_OK) rc = batch_streams(b);
   if (rc) {
     for (int i = 0; i < n; ++i) hs[i]->err = hs[i]->d.err = b->own_err[size_t(i)];
@@ -1317,7 +1346,7 @@ int pmwa_batch_graph(pmwa_batch* b, int32_t sweeps) {
   int rc = PMWA_OK;
   if (cudaEventRecord(b->fork, b->cap)) rc = PMWA_ECUDA;
   for (int g = 0; g < kBatchGroups && rc == PMWA_OK; ++g) {
-    if (!b->cls_n[g] && !b->bcls_n[0][g] && !b->bcls_n[1][g]) continue;
+    if (!b->cls_n[g] && !b->bcls_n[0][g] && !b->bcls_n[1][g] && !b->tcls_n[g]) continue;
     if (cudaStreamWaitEvent(b->cs[g], b->fork, 0)) { rc = PMWA_ECUDA; break; }
     for (int it = 0; it < sweeps && rc == PMWA_OK; ++it) rc = batch_launch_class(b, it, g, b->cs[g]);
     if (rc == PMWA_OK && (cudaEventRecord(b->join[g], b->cs[g]) || cudaStreamWaitEvent(b->cap, b->join[g], 0)))

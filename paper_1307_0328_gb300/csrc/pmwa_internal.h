@@ -125,6 +125,10 @@ int upload_zig_tile(const Zig& z);  // constants of pmwa_tile.cu
 int upload_zig_green(const Zig& z); // constants of pmwa_green.cu
 int launch_boundary(const Dev& d, int dir, void* stream);
 int launch_temporal(const Dev& d, void* stream);  // Step 1, one warp per site
+int launch_temporal_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int cap,
+                          void* stream);
+int temporal_sites_per_block();
+int prepare_temporal(int cap);
 int launch_tile(const Dev& d, int stop, void* stream);
 int tile_class(int domain_sites);
 // batch launch groups: 3 CTA-size classes x residency levels by shared memory

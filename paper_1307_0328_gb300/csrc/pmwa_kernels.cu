@@ -445,15 +445,11 @@ __device__ int temporal_site(const Dev& d, int s, uint64_t* K, int& n, int& base
 
 constexpr int kTemporalWarps = 4;  // sites (warps) per block
 
-__global__ void __launch_bounds__(32 * kTemporalWarps) k_temporal(const __grid_constant__ Dev d) {
-  extern __shared__ __align__(16) unsigned char tsm[];
-  if (instance_failed(d.err)) return;
-  const ZigTab Z = zig_stage(tsm, d.zig_cap, d.worm_tries);
-  __syncthreads();
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = int(blockIdx.x) * kTemporalWarps + wid;
+// one warp: stage site s's list (cap keys at K), update its boundaries, and
+// write it back
+__device__ void temporal_warp(const Dev& d, int s, uint64_t* K, const ZigTab& Z) {
+  const int lane = threadIdx.x & 31;
   if (s >= d.N) return;
-  uint64_t* K = reinterpret_cast<uint64_t*>(tsm + kZigBytes) + size_t(wid) * d.cap;
   const uint32_t c = d.cntA[s];
   int n = cnt_n(c), base = cnt_base(c);
   const uint64_t* g = d.keyA + size_t(s) * d.cap;
@@ -470,12 +466,64 @@ __global__ void __launch_bounds__(32 * kTemporalWarps) k_temporal(const __grid_c
   if (lane == 0) d.cntA[s] = cnt_make(n, n ? kab(K[n - 1]) : base);
 }
 
+__global__ void __launch_bounds__(32 * kTemporalWarps) k_temporal(const __grid_constant__ Dev d) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  if (instance_failed(d.err)) return;
+  const ZigTab Z = zig_stage(tsm, d.zig_cap, d.worm_tries);
+  __syncthreads();
+  const int wid = threadIdx.x >> 5;
+  temporal_warp(d, int(blockIdx.x) * kTemporalWarps + wid,
+                reinterpret_cast<uint64_t*>(tsm + kZigBytes) + size_t(wid) * d.cap, Z);
+}
+
+// Batched form: each block serves sites t0 .. t0 + kTemporalWarps - 1 of one
+// instance, when that instance has temporal domains and its Step 1 is due at
+// iteration `it`.
+__global__ void __launch_bounds__(32 * kTemporalWarps) k_temporal_batch(const Dev* __restrict__ devs,
+                                                                        const BatchBase* __restrict__ base,
+                                                                        const int2* __restrict__ work, int it,
+                                                                        int cap) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  __shared__ Dev sd;
+  const int2 w = work[blockIdx.x];
+  const BatchBase bb = base[w.x];
+  if (!bb.active) return;
+  if (threadIdx.x == 0) sd = at_iteration(devs[w.x], bb, it);
+  ZigTab Z = zig_stage(tsm);
+  __syncthreads();
+  Z.zcap = sd.zig_cap;
+  Z.wtries = sd.worm_tries;
+  if (instance_failed(sd.err)) return;
+  if (sd.ntau < 2 || sd.sweep % uint32_t(sd.exchange_every) != 0) return;
+  const int wid = threadIdx.x >> 5;
+  temporal_warp(sd, w.y + wid, reinterpret_cast<uint64_t*>(tsm + kZigBytes) + size_t(wid) * cap, Z);
+}
+
+static size_t temporal_smem(int cap) { return size_t(kZigBytes) + size_t(kTemporalWarps) * size_t(cap) * 8; }
+
+int temporal_sites_per_block() { return kTemporalWarps; }
+
 int launch_temporal(const Dev& d, void* stream) {
   if (d.ntau < 2) return 0;
-  const size_t smem = size_t(kZigBytes) + size_t(kTemporalWarps) * size_t(d.cap) * 8;
+  const size_t smem = temporal_smem(d.cap);
   cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e) return int(e);
   k_temporal<<<blocks_for(d.N, kTemporalWarps), 32 * kTemporalWarps, smem, cudaStream_t(stream)>>>(d);
+  return int(cudaGetLastError());
+}
+
+// (the batch sets the kernel's shared-memory allowance once, before any
+// capture: prepare_temporal)
+int prepare_temporal(int cap) {
+  return int(cudaFuncSetAttribute(k_temporal_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(temporal_smem(cap))));
+}
+
+int launch_temporal_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int cap,
+                          void* stream) {
+  if (n_work <= 0) return 0;
+  k_temporal_batch<<<n_work, 32 * kTemporalWarps, temporal_smem(cap), cudaStream_t(stream)>>>(devs, base, work, it,
+                                                                                              cap);
   return int(cudaGetLastError());
 }
 

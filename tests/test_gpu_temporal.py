@@ -8,7 +8,7 @@ Each step is checked on its own from the same configuration (Step 1; Step 2
 cover one spatial domain and several, sub-blocks, N_beta from 2 to 5,
 t = 0, an empty 2x2 start, and beta t = 16 with several hundred worms per
 domain (both Step-5 groupings).  At full size the t = V = 0 closed form must
-hold with N_beta = 4 on 256x256.
+hold with N_beta = 4 on 256x256.  Replica batches run Step 1 too.
 """
 import numpy as np
 import pytest
@@ -128,8 +128,22 @@ def test_temporal_decoupled_sites_full_size():
     assert g.check() is None
 
 
-def test_temporal_batch_is_refused():
-    """Batches run instances without temporal domains (the batch kernels have
-    no Step 1); a parameter set with dom_tau > 1 is refused."""
-    with pytest.raises(P.PmwaError):
-        P.Batch([dict(Lx=8, Ly=8, beta=2.0, eta=0.2, dom_tau=2)])
+@pytest.mark.parametrize("graph", [0, 2])
+def test_temporal_batch_equals_alone_and_oracle(graph):
+    """A replica batch mixing instances with and without temporal domains
+    (Step 1 runs batched, one warp per site, only where it is due) gives each
+    instance exactly its bytes swept alone, and the oracle's."""
+    kws = [GEOMS[0], GEOMS[1], GEOMS[3], dict(Lx=8, Ly=8, beta=2.0, eta=0.2, n_cycle=5, seed=77, replica=9),
+           dict(GEOMS[2], exchange_every=3, replica=4)]
+    batch = P.Batch(kws)
+    if graph:
+        batch.graph(graph)
+    batch.sweep(6)
+    for i, kw in enumerate(kws):
+        alone = P.Sim(**kw)
+        alone.sweep(6)
+        assert np.array_equal(batch.export(i), alone.export()), i
+        _rows_same(batch.rows(i), alone.rows())
+        o = O.Oracle(**kw)
+        o.sweep(6)
+        assert np.array_equal(batch.export(i), o.export()), i

@@ -42,12 +42,36 @@ def n_cycle_estimate(p):
     return _lib.n_cycle(_lib.make_params(**{k: v for k, v in p.items() if k in _lib.DEFAULTS}))
 
 
+def admission(waiting, used, budget, slots, busy, max_bypass):
+    """The waiting jobs to admit now, in arrival order: every job whose
+    footprint fits the memory left and a free slot (first fit), so that a
+    large job at the head of the queue does not hold back small ones behind
+    it.  A job passed over `max_bypass` times blocks the jobs behind it until
+    it is admitted (no starvation).  With nothing resident the head job is
+    admitted even if it alone exceeds the budget.  Counts each pass-over on
+    the job (job.bypassed)."""
+    picked = []
+    for job in waiting:
+        if len(picked) >= slots:
+            break
+        fits = used + job.footprint <= budget or (not busy and not picked and job is waiting[0])
+        if fits:
+            picked.append(job)
+            used += job.footprint
+            continue
+        job.bypassed = getattr(job, "bypassed", 0) + 1
+        if job.bypassed > max_bypass:
+            break
+    return picked
+
+
 class Server:
-    def __init__(self, budget_bytes, max_jobs=64, chunk=8, device="cuda"):
+    def __init__(self, budget_bytes, max_jobs=64, chunk=8, device="cuda", max_bypass=8):
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
         self.max_jobs = int(max_jobs)
+        self.max_bypass = int(max_bypass)
         self.chunk = int(chunk)
         self.device = device
         self.waiting = []
@@ -74,18 +98,15 @@ class Server:
         self.waiting.append(job)
 
     def _admit(self, now):
-        changed = False
-        while self.waiting and len(self.resident) < self.max_jobs:
-            job = self.waiting[0]
-            if self.used + job.footprint > self.budget and self.resident:
-                break  # first in, first out: wait for memory
-            self.waiting.pop(0)
+        picked = admission(self.waiting, self.used, self.budget, self.max_jobs - len(self.resident),
+                           bool(self.resident), self.max_bypass)
+        for job in picked:
+            self.waiting.remove(job)
             job.sim = _lib.Sim(device=self.device, stream=self.stream, **job.params)
             self.used += job.footprint
             job.admitted = now
             self.resident.append(job)
-            changed = True
-        return changed
+        return bool(picked)
 
     def _rebuild(self):
         self._drop_batch()

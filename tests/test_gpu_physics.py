@@ -226,19 +226,20 @@ def test_gpu_superfluid_energy_at_the_papers_size():
                     reason="a ten-minute measurement campaign: set PMWA_LONG_PHYSICS=1 to run it")
 def test_gpu_superfluid_eta_series_linear_fit():
     """Fig. 2 (b) as the paper makes it: L = 128, beta t = 16, V/t = 3,
-    mu/t = 1.2 (superfluid) at eta = 0.06, 0.05, 0.04, 0.03, 0.02, two
+    mu/t = 1.2 (superfluid) at eta = 0.06, 0.04, 0.03 and 0.02, two
     independent chains each, advanced together as one replica batch; every
     chain starts from a configuration annealed at eta = 0.05 and follows
     the N_cycle rule.  The energy per site is fitted linearly in eta (the
-    paper's fit for this phase) with weights from the chains' scatter, and
-    the intercept must match the printed eta -> 0 value within 4 standard
-    errors of the fit combined with the paper's error."""
+    paper's fit for this phase) with weights from the bins of both chains,
+    and the intercept must match the printed eta -> 0 value within 4
+    standard errors of the fit combined with the paper's error.  Prints the
+    series after every block of sweeps."""
     g = _golden()["SF"]
-    etas = [0.06, 0.05, 0.04, 0.03, 0.02]
+    etas = [0.06, 0.04, 0.03, 0.02]
     kw = dict(Lx=128, Ly=128, beta=16.0, t=1.0, V=3.0, mu=g["mu"], dom_x=4, dom_y=4, sub_block=2,
               exchange_every=2, init=1, init_seed=5)
     hot = P.Sim(eta=0.05, seed=41, n_cycle=256, **kw)
-    hot.sweep(2000)
+    hot.sweep(1000)
     hot.rows()
     snap = hot.export()
     hot.close()
@@ -250,27 +251,29 @@ def test_gpu_superfluid_eta_series_linear_fit():
     b.sweep(500)
     for i in range(len(reps)):
         b.set_n_cycle(i, P.n_cycle(b.params[i], b.rows(i)[250:]))
-    b.sweep(2500)
+    b.sweep(1500)
     for i in range(len(reps)):
         b.rows(i)
     E = [[] for _ in reps]
-    for _ in range(10):
-        b.sweep(2000)
+
+    def fit():
+        means, errs = [], []
+        for k in range(len(etas)):
+            bins = np.concatenate([np.concatenate(E[2 * k + c]).reshape(-1, 500).mean(axis=1) for c in range(2)])
+            means.append(float(bins.mean()))
+            errs.append(float(bins.std(ddof=1) / np.sqrt(len(bins))))
+        x, y, w = np.array(etas), np.array(means), 1.0 / np.array(errs) ** 2
+        A = np.stack([np.ones_like(x), x], axis=1)
+        cov = np.linalg.inv(A.T @ (A * w[:, None]))
+        a, slope = cov @ (A.T @ (w * y))
+        return y, errs, a, float(np.sqrt(cov[0, 0])), slope
+
+    for blk in range(4):
+        b.sweep(1500)
         for i in range(len(reps)):
             E[i].append(P.observables(b.rows(i), b.params[i])["E"])
+        y, errs, a, sa, slope = fit()
+        print("block %d: E(eta) %s +- %s; fit a = %.5f +- %.5f, b = %.4f; DLA %.5f" % (
+            blk, np.round(y, 5).tolist(), np.round(errs, 5).tolist(), a, sa, slope, g["E_dla"]), flush=True)
     b.close()
-    means, errs = [], []
-    for k in range(len(etas)):
-        chains = [np.concatenate(E[2 * k + c]) for c in range(2)]
-        bins = np.concatenate([c.reshape(10, -1).mean(axis=1) for c in chains])
-        means.append(float(bins.mean()))
-        errs.append(float(bins.std(ddof=1) / np.sqrt(len(bins))))
-    x, y, w = np.array(etas), np.array(means), 1.0 / np.array(errs) ** 2
-    A = np.stack([np.ones_like(x), x], axis=1)
-    cov = np.linalg.inv(A.T @ (A * w[:, None]))
-    a, slope = cov @ (A.T @ (w * y))
-    sa = float(np.sqrt(cov[0, 0]))
-    msg = "E(eta) %s +- %s; fit a = %.5f +- %.5f, b = %.4f; DLA %.5f" % (
-        np.round(y, 5).tolist(), np.round(errs, 5).tolist(), a, sa, slope, g["E_dla"])
-    print(msg)
-    assert abs(a - g["E_dla"]) < Z * np.hypot(sa, g["err_dla"]), msg
+    assert abs(a - g["E_dla"]) < Z * np.hypot(sa, g["err_dla"]), (a, sa)

@@ -91,7 +91,16 @@ typedef struct {
                                N_beta > 1, boundary k sits at the grid point
                                floor(k 2^59 / N_beta) of every site; Step 1
                                (Eq. 3) runs when sweep % K == 0, before Step 2 */
-  int32_t  reserved[3];     /* must be 0                                          */
+  int32_t  reserved[1];     /* must be 0                                          */
+  double   vertex_window;   /* on-the-fly vertex generation (the paper's closing
+                               discussion of extensions): 0 = the vertex phase
+                               everywhere; w in (0, 1] = the vertex phase of a
+                               bond only at grid points within w beta of a worm
+                               of the current configuration on either of its
+                               sites (diagonal vertices elsewhere stay).  The
+                               windows depend on the worms alone, which Step 3
+                               does not move, so the distribution is kept.  Not
+                               in replica batches.                               */
 } pmwa_params;
 
 /* One row per sweep (Step 6 measurement after Step 5). */
@@ -180,9 +189,13 @@ int pmwa_green(pmwa_handle* h, int32_t K, int32_t rmax, double* gx, double* gy, 
    paper has no counterpart.  Limit: N*K <= 2^20 doubles (8 MiB, held on every
    GPU that loads the library until exit); larger requests return
    PMWA_EINVAL.  The handle's device must be current.  The first call on a
-   device looks up the array's device address; make that first call before
-   any stream capture.  Calls that overlap on the GPU share the array and
-   race; each call overwrites every value it returns. */
+   device looks up the array's device address and keeps it for the process;
+   make that first call before any stream capture.  The kept address belongs
+   to the device's primary context: after cudaDeviceReset (or anything else
+   that destroys that context) it is stale, and the handles created before
+   are unusable anyway, so do not call this entry point again in that
+   process.  Calls that overlap on the GPU share the array and race; each
+   call overwrites every value it returns. */
 int pmwa_rho_slices_static(pmwa_handle* h, int32_t K, double* host_out);
 
 /* Supplement S-I n-point functions of listed site tuples at equal time:

@@ -32,7 +32,7 @@ class Params(C.Structure):
                 ("init_seed", C.c_uint64), ("c_off", C.c_double),
                 ("replica", C.c_uint32), ("cap_site", C.c_int32),
                 ("rows_cap", C.c_int32), ("legs_hint", C.c_int32), ("dom_tau", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("reserved", C.c_int32 * 1), ("vertex_window", C.c_double)]
 
 
 ROW_DTYPE = np.dtype([("sweep", "<u8"), ("n_v", "<u8"), ("n_k", "<u8"), ("n_w", "<u8"),
@@ -50,7 +50,7 @@ SERIES = ("E", "E_eta", "n", "Q_raw", "Q_impr", "kin")
 
 DEFAULTS = dict(Lx=8, Ly=8, beta=2.0, t=1.0, V=0.0, mu=0.0, eta=0.2, seed=1, dom_x=0, dom_y=0,
                 exchange_every=2, n_cycle=8, sub_block=0, init=1, init_seed=1, c_off=-1.0,
-                replica=0, cap_site=0, rows_cap=0, legs_hint=0, dom_tau=1)
+                replica=0, cap_site=0, rows_cap=0, legs_hint=0, dom_tau=1, vertex_window=0.0)
 
 _lib = None
 

@@ -72,7 +72,8 @@ int validate(const pmwa_params* p) {
   if (p->replica >= 65536u || p->init < 0 || p->init > 2) return PMWA_EINVAL;
   if (p->cap_site < 0 || p->cap_site > (1 << 24) || p->rows_cap < 0) return PMWA_EINVAL;
   if (p->legs_hint < 0 || p->legs_hint > (1 << 20)) return PMWA_EINVAL;
-  for (int k = 0; k < 3; ++k) if (p->reserved[k]) return PMWA_EINVAL;
+  if (p->reserved[0]) return PMWA_EINVAL;
+  if (!(p->vertex_window >= 0.0 && p->vertex_window <= 1.0)) return PMWA_EINVAL;
   if (p->dom_tau < 0 || p->dom_tau > 64) return PMWA_EINVAL;
   // the gap arithmetic needs the mean grid spacings 2^59/(beta eta) and
   // 2^59/(beta D) in [2^39, 2^99]
@@ -446,6 +447,7 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.zig_cap = 64;
   d.worm_tries = 128;
   d.ntau = g.ntau;
+  d.win_half = (p->vertex_window >= 0.5) ? kTwo59 : uint64_t(p->vertex_window * 0x1p59);
   d.tq = kTwo59 / uint64_t(g.ntau);
   d.tr = kTwo59 % uint64_t(g.ntau);
   h->err = d.err;
@@ -517,6 +519,7 @@ int pmwa_tile_plan(const pmwa_params* p, int32_t* smem, int32_t* legcap, int32_t
   d.Lx = p->Lx; d.Ly = p->Ly; d.dom_x = g.dom_x; d.dom_y = g.dom_y; d.ndx = g.ndx; d.ndy = g.ndy;
   d.sub_block = p->sub_block; d.wcap = g.wcap; d.poolcap = g.poolcap;
   d.ntau = g.ntau;
+  d.win_half = (p->vertex_window >= 0.5) ? kTwo59 : uint64_t(p->vertex_window * 0x1p59);
   if (!plan_tile_smem(&d, g.legs_want, g.mb)) return PMWA_EINVAL;
   if (smem) *smem = d.sm_total;
   if (legcap) *legcap = d.legcap;
@@ -996,6 +999,7 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
   L->inst_off.resize(size_t(n));
   for (int i = 0; i < n; ++i) {
     if (validate(p + i)) return false;
+    if (p[i].vertex_window > 0.0) return false;  // the batch kernels run the plain vertex phase
     Derived g;
     derive(p + i, &g);
     if (g.ntau > 1) L->n_tw += g.N;  // upper bound: one site per block
@@ -1235,7 +1239,7 @@ size_t pmwa_batch_tables_bytes(pmwa_handle* const* hs, int32_t n) {
   if (!hs || n < 1 || n > 65536) return 0;
   int n_tile = 0, n_bw[2] = {0, 0}, n_tw = 0;
   for (int i = 0; i < n; ++i) {
-    if (!hs[i]) return 0;
+    if (!hs[i] || hs[i]->d.win_half) return 0;  // the batch kernels run the plain vertex phase
     const Dev& d = hs[i]->d;
     if (d.ntau > 1) n_tw += d.N;
     n_tile += d.ndom;

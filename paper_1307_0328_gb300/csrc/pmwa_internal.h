@@ -83,6 +83,10 @@ struct Dev {
   // m_k = k tq + (k tr) / ntau with 2^59 = tq ntau + tr, i.e. floor(k 2^59 / ntau)
   int ntau;
   uint64_t tq, tr;
+  // on-the-fly vertex generation: the vertex phase of a bond only within
+  // win_half worm grid points of a worm on its sites (0: everywhere)
+  uint64_t win_half;
+  int sm_wmo, sm_wm;  // shared-memory offsets of the windows' worm index (k_tile)
 };
 
 // Per-instance state at the start of a batched call: the sweep index, the

@@ -189,8 +189,27 @@ __device__ __forceinline__ int boundary_site(const Dev& d, int dir, int t) {
   return (t % d.Lx) + d.Lx * ((t / d.Lx) * d.dom_y + d.dom_y - 1);
 }
 
+// On-the-fly vertex generation: is grid point pos within half of a worm of
+// either staged list (cyclic)?
+__device__ __forceinline__ bool in_win_lists(const uint64_t* KA, int nA, const uint64_t* KB, int nB, uint64_t pos,
+                                             uint64_t half) {
+  for (int side = 0; side < 2; ++side) {
+    const uint64_t* K = side ? KB : KA;
+    const int n = side ? nB : nA;
+    for (int i = 0; i < n; ++i) {
+      if (!kworm(K[i])) continue;
+      const uint64_t m = kpk(K[i]) >> 3;
+      const uint64_t a = (pos - m) & (kTwo59 - 1), b = (m - pos) & (kTwo59 - 1);
+      if (min(a, b) <= half) return true;
+    }
+  }
+  return false;
+}
+
 // Step 2 + Step 3 on the boundary bond (a, dir) whose two site lists are
-// staged in KA (nA events) and KB (nB events); returns a status.
+// staged in KA (nA events) and KB (nB events); returns a status.  With
+// d.win_half > 0 the Step-3 part is confined to the windows around the worms
+// of the two sites (on-the-fly vertex generation).
 __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, int& nA, int& baseA,
                                     uint64_t* KB, int& nB, int& baseB, const ZigTab& Z) {
   const int tag = bond_tag(d, a, dir);
@@ -271,8 +290,15 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
   if (nA) baseA = kab(KA[nA - 1]);
   if (nB) baseB = kab(KB[nB - 1]);
   // Step 3 on this bond: erase its diagonal vertices, lay new ones
+  const bool otf = d.win_half > 0;
   {
-    auto diag = [&](uint64_t key) { return ktag(key) == tag && kab(key) == kbl(key); };
+    // (the windows do not move: the compaction drops only diagonal legs, so
+    // while it runs every worm of both lists is still found in their first
+    // nA / nB slots, some of them twice, which the window test does not mind)
+    auto diag = [&](uint64_t key) {
+      return ktag(key) == tag && kab(key) == kbl(key) &&
+             (!otf || in_win_lists(KA, nA, KB, nB, kpk(key) >> 3, d.win_half));
+    };
     const int wa = warp_compact(KA, nA, diag);
     const int wb = warp_compact(KB, nB, diag);
     const int removed = nA - wa, gone = nB - wb;
@@ -295,6 +321,7 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
     if (nxt >= kTwo59) break;
     pos = nxt;
     const uint64_t pk = (pos << 3) | uint64_t(tag);
+    if (otf && !in_win_lists(KA, nA, KB, nB, pos, d.win_half)) continue;
     if (slot_find(KA, nA, pk) >= 0) continue;
     const int na = slot_state(KA, nA, baseA, pk), nb = slot_state(KB, nB, baseB, pk);
     const int si = na | (nb << 1);

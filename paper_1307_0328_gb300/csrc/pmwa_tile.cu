@@ -116,6 +116,8 @@ struct Tile {
   uint16_t* sub;   // [4 nds] sub-block of each site for offset pattern pass & 3
   int* soff;       // [nds + 1] start of each site's events in old[] (when staged)
   uint64_t* old;   // [oldcap] the domain's current configuration (when staged)
+  int* wmo;        // [nds + 1] on-the-fly windows: start of each site's old worms in wm[]
+  uint64_t* wm;    // [wcap] grid points of the current configuration's worms, by site
   bool staged;
   int x0, y0, nds, nsub;
   int ngrp;  // Step-5 chains: sub-blocks x temporal slabs
@@ -136,10 +138,26 @@ struct Tile {
   }
 };
 
+// On-the-fly vertex generation (the paper's closing discussion of
+// extensions): with d.win_half > 0 the vertex phase of a bond is confined to
+// the grid points within win_half of a worm of the current configuration on
+// either of its two sites (cyclic).  R depends on the worms alone, which
+// Step 3 does not move, so the restricted heat bath keeps the distribution.
+__device__ __forceinline__ bool in_win(const Tile& T, int li, uint64_t pos) {
+  const uint64_t half = T.d->win_half;
+  for (int k = T.wmo[li]; k < T.wmo[li + 1]; ++k) {
+    const uint64_t a = (pos - T.wm[k]) & (kTwo59 - 1), b = (T.wm[k] - pos) & (kTwo59 - 1);
+    if (min(a, b) <= half) return true;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // phase 1: Step 3 candidates of bond (a, dir) from the current configuration
+// (with OTF, only inside the windows of the bond's local sites la, lb)
+template <bool OTF>
 __device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, const uint64_t* KA, const uint64_t* KB,
-                               uint64_t* buf, int cap, int* bad) {
+                               uint64_t* buf, int cap, int* bad, const Tile* T, int la, int lb) {
   const int b = site_step(d, a, dir, +1);
   const uint64_t tag = uint64_t(bond_tag(d, a, dir));
   const uint32_t ca = d.cntA[a], cb = d.cntA[b];
@@ -157,6 +175,7 @@ __device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, co
     first = false;
     if (nxt >= kTwo59) break;
     pos = nxt;
+    if (OTF && !(in_win(*T, la, pos) || in_win(*T, lb, pos))) continue;
     const uint64_t pk = (pos << 3) | tag;
     while (ia < nA && kpk(KA[ia]) < pk) ++ia;
     while (ib < nB && kpk(KB[ib]) < pk) ++ib;
@@ -174,11 +193,18 @@ __device__ int bond_candidates(const Dev& d, const ZigTab& z, int a, int dir, co
   return n;
 }
 
-// old event kept by Step 3: a kink, or any leg of a bond between domains
-__device__ __forceinline__ bool kept_leg(const uint8_t* tinfo6, uint64_t k) {
+// old event of local site li kept by Step 3: a kink, any leg of a bond
+// between domains, and (OTF) a diagonal leg outside the windows of its bond
+template <bool OTF>
+__device__ __forceinline__ bool kept_leg(const Tile& T, int li, uint64_t k) {
   if (kworm(k)) return false;
   if (kab(k) != kbl(k)) return true;
-  return (tinfo6[ktag(k)] & 2) != 0;
+  if (T.tinfo[li * 6 + ktag(k)] & 2) return true;
+  if (OTF) {
+    const uint64_t pos = kpk(k) >> 3;
+    return !(in_win(T, li, pos) || in_win(T, T.nbr[li * 6 + ktag(k)] >> 1, pos));
+  }
+  return false;
 }
 
 // the four bonds of local site li: (s,x) (s,y) with s the lower site, then
@@ -513,6 +539,7 @@ __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+template <bool OTF>
 __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int stop, unsigned char* sm,
                                           int* wsum) {
   Tile T;
@@ -590,6 +617,31 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     __syncthreads();
   }
 
+  if (OTF) {
+    // the worms of the current configuration, by site: the windows of the
+    // on-the-fly vertex phase
+    T.wmo = reinterpret_cast<int*>(sm + d.sm_wmo);
+    T.wm = reinterpret_cast<uint64_t*>(sm + d.sm_wm);
+    for (int li = tid; li < nds; li += NT) {
+      const int s = T.gsite(li), n = cnt_n(d.cntA[s]);
+      const uint64_t* KO = T.okeys(li, s);
+      int c = 0;
+      for (int k = 0; k < n; ++k) c += kworm(KO[k]) ? 1 : 0;
+      T.wmo[li] = c;
+    }
+    __syncthreads();
+    if (block_scan(T.wmo, nds, wsum) > d.wcap) { if (tid == 0) tile_fail(misc, PMWA_ECAPACITY, 35); }
+    __syncthreads();
+    if (misc->err) goto fail;
+    for (int li = tid; li < nds; li += NT) {
+      const int s = T.gsite(li), n = cnt_n(d.cntA[s]);
+      const uint64_t* KO = T.okeys(li, s);
+      int o = T.wmo[li];
+      for (int k = 0; k < n; ++k) if (kworm(KO[k])) T.wm[o++] = kpk(KO[k]) >> 3;
+    }
+    __syncthreads();
+  }
+
   // ---- phase 1: Step 3 candidates per bond
   for (int lb = tid; lb < 2 * nds; lb += NT) {
     const int li = lb >> 1, dir = lb & 1;
@@ -598,8 +650,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     int n = 0, bad = 0;
     if (d.has_vertices && !boundary_bond(d, a, dir)) {
       const int b = site_step(d, a, dir, +1);
-      n = bond_candidates(d, Z, a, dir, T.okeys(li, a), T.okeys(T.lsite(b), b), buf, min(d.capb, kMaxCandPerBond),
-                          &bad);
+      n = bond_candidates<OTF>(d, Z, a, dir, T.okeys(li, a), T.okeys(T.lsite(b), b), buf,
+                               min(d.capb, kMaxCandPerBond), &bad, &T, li, T.lsite(b));
     }
     if (bad) { tile_fail(misc, bad, 31); n = 0; }
     int o = 0;
@@ -621,8 +673,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     const uint64_t* KO = T.okeys(li, s);
     const int nO = cnt_n(d.cntA[s]);
     int c = 0;
-    const uint8_t* ti = T.tinfo + li * 6;
-    for (int k = 0; k < nO; ++k) c += kept_leg(ti, KO[k]);
+    for (int k = 0; k < nO; ++k) c += kept_leg<OTF>(T, li, KO[k]);
     int lb[4];
     site_bonds(T, li, lb);
     for (int j = 0; j < 4; ++j) if (lb[j] >= 0) c += T.bcnt[lb[j]];
@@ -647,7 +698,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     const int NB = d.ntau > 1 ? d.ntau : 0, base0 = cnt_base(d.cntA[s]);
     int ib = 0;
     for (;;) {
-      while (io < nO && !kept_leg(T.tinfo + li * 6, KO[io])) ++io;
+      while (io < nO && !kept_leg<OTF>(T, li, KO[io])) ++io;
       uint64_t best = ~0ull;
       int src = -1;
       if (io < nO) { best = kpk(KO[io]); src = 4; }
@@ -986,12 +1037,12 @@ fail:
   if (tid == 0) set_err(d.err, misc->err, misc->where);
 }
 
-template <int NT>
+template <int NT, bool OTF>
 __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ Dev d, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wsum[32];
   if (instance_failed(d.err)) return;
-  tile_body(d, int(blockIdx.x), stop, sm, wsum);
+  tile_body<OTF>(d, int(blockIdx.x), stop, sm, wsum);
 }
 
 // Batched form: one CTA per (instance, domain) work item; the instance's
@@ -1009,7 +1060,7 @@ __global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
   if (threadIdx.x == 0) sd = at_iteration(devs[w.x], base[w.x], it);
   __syncthreads();
   if (instance_failed(sd.err)) return;
-  tile_body(sd, w.y, stop, sm, wsum);
+  tile_body<false>(sd, w.y, stop, sm, wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -1046,7 +1097,9 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const size_t cnt_bytes = up16(size_t(warps) * size_t(nsub) * sizeof(int));
   const size_t worm_bytes = up16(size_t(d->wcap) * sizeof(WormRec)) + 4 * up16(size_t(d->wcap) * 2) +
                             up16(size_t(d->wcap) * 16) + 2 * up16(size_t(nb) * sizeof(int)) + cnt_bytes;
-  const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t));
+  // (on-the-fly windows: the worms of the current configuration by site, beside the pool)
+  const size_t otf_bytes = d->win_half ? up16(size_t(nds + 1) * sizeof(int)) + up16(size_t(d->wcap) * 8) : 0;
+  const size_t pool_bytes = up16(size_t(d->poolcap) * sizeof(uint64_t)) + otf_bytes;
   const long long want = std::min<long long>((long long)legs_want, 65000);
   const long long limit = (long long)kSmemLimit - 1024;
   // CTAs per SM: shared memory (1 KB the hardware reserves a CTA and up to
@@ -1082,6 +1135,8 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   d->use_part = part ? 1 : 0;
   d->sm_part = int(o); if (part) o = up16(o + size_t(d->legcap) * 2);
   d->sm_pool = int(o);
+  d->sm_wmo = int(o + up16(size_t(d->poolcap) * sizeof(uint64_t)));
+  d->sm_wm = int(d->sm_wmo + up16(size_t(nds + 1) * sizeof(int)));
   d->sm_soff = int(o + pool_bytes);
   d->sm_old = int(o + pool_bytes + up16(size_t(nds + 1) * sizeof(int)));
   d->sm_worm = int(o);
@@ -1105,7 +1160,6 @@ int upload_zig_tile(const Zig& z) { return upload_constants(z); }
 // CTA sizes of the sweep kernel: small domains take small CTAs, so that many
 // of them share an SM (class 0: 64 threads, 1: 128, 2: 256)
 int tile_class(int domain_sites) { return domain_sites <= 32 ? 0 : (domain_sites <= 96 ? 1 : 2); }
-static constexpr int kClassThreads[3] = {64, 128, 256};
 
 int prepare_tile_batch(int cls, int smem) {
   cudaError_t e;
@@ -1129,27 +1183,23 @@ int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int
   return int(cudaGetLastError());
 }
 
+template <int NT, bool OTF>
+static int launch_tile_k(const Dev& d, int stop, cudaStream_t st) {
+  const cudaError_t e = cudaFuncSetAttribute(k_tile<NT, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
+  if (e) return int(e);
+  k_tile<NT, OTF><<<d.ndom, NT, d.sm_total, st>>>(d, stop);
+  return int(cudaGetLastError());
+}
+
 int launch_tile(const Dev& d, int stop, void* stream) {
   const int cls = tile_class(d.dom_x * d.dom_y);
   const cudaStream_t st = cudaStream_t(stream);
-  cudaError_t e;
+  const bool otf = d.win_half > 0;
   switch (cls) {
-    case 0:
-      e = cudaFuncSetAttribute(k_tile<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
-      if (!e) k_tile<64><<<d.ndom, 64, d.sm_total, st>>>(d, stop);
-      break;
-    case 1:
-      e = cudaFuncSetAttribute(k_tile<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
-      if (!e) k_tile<128><<<d.ndom, 128, d.sm_total, st>>>(d, stop);
-      break;
-    default:
-      e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, d.sm_total);
-      if (!e) k_tile<256><<<d.ndom, 256, d.sm_total, st>>>(d, stop);
-      break;
+    case 0: return otf ? launch_tile_k<64, true>(d, stop, st) : launch_tile_k<64, false>(d, stop, st);
+    case 1: return otf ? launch_tile_k<128, true>(d, stop, st) : launch_tile_k<128, false>(d, stop, st);
+    default: return otf ? launch_tile_k<256, true>(d, stop, st) : launch_tile_k<256, false>(d, stop, st);
   }
-  if (e) return int(e);
-  (void)kClassThreads;
-  return int(cudaGetLastError());
 }
 
 }  // namespace pmwa

@@ -134,3 +134,18 @@ def test_n_cycle_rule():
     # N_cycle = ceil(2 * 2N beta (1/2 + 1/2) / (beta eta N / 2)) = ceil(8 / eta)
     assert P.n_cycle(p) == int(np.ceil(8.0 / 0.2))
     assert P.n_cycle(P.make_params(**dict(kw, eta=0.001))) == 512
+
+
+def test_vertex_window_parameter():
+    """vertex_window in [0, 1] (the on-the-fly vertex phase); replica batches
+    refuse it (their kernels run the plain vertex phase)."""
+    kw = dict(Lx=8, Ly=8, beta=2.0, eta=0.2)
+    assert P.pmwa_footprint(P.make_params(vertex_window=0.1, **kw)) > 0
+    for bad in (-0.1, 1.5, float("nan")):
+        assert P.pmwa_footprint(P.make_params(vertex_window=bad, **kw)) == 0
+    import ctypes as C
+    from paper_1307_0328_gb300._lib import Params
+    arr = (Params * 1)(P.make_params(vertex_window=0.1, **kw))
+    assert P.load().pmwa_batch_footprint(arr, 1) == 0
+    arr = (Params * 1)(P.make_params(**kw))
+    assert P.load().pmwa_batch_footprint(arr, 1) > 0

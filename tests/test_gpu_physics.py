@@ -226,20 +226,23 @@ def test_gpu_superfluid_energy_at_the_papers_size():
                     reason="a ten-minute measurement campaign: set PMWA_LONG_PHYSICS=1 to run it")
 def test_gpu_superfluid_eta_series_linear_fit():
     """Fig. 2 (b) as the paper makes it: L = 128, beta t = 16, V/t = 3,
-    mu/t = 1.2 (superfluid) at eta = 0.06, 0.04, 0.03 and 0.02, two
+    mu/t = 1.2 (superfluid) at eta = 0.08, 0.06, 0.05 and 0.04, two
     independent chains each, advanced together as one replica batch; every
-    chain starts from a configuration annealed at eta = 0.05 and follows
-    the N_cycle rule.  The energy per site is fitted linearly in eta (the
+    chain starts from a configuration annealed for 4000 sweeps at eta = 0.08
+    (a run that started from 1000 sweeps at eta = 0.05 and measured at
+    eta = 0.06..0.02 was still drifting after 7 minutes: the smaller eta,
+    the fewer worms and the slower the chain) and follows the N_cycle
+    rule.  The energy per site is fitted linearly in eta (the
     paper's fit for this phase) with weights from the bins of both chains,
     and the intercept must match the printed eta -> 0 value within 4
     standard errors of the fit combined with the paper's error.  Prints the
     series after every block of sweeps."""
     g = _golden()["SF"]
-    etas = [0.06, 0.04, 0.03, 0.02]
+    etas = [0.08, 0.06, 0.05, 0.04]
     kw = dict(Lx=128, Ly=128, beta=16.0, t=1.0, V=3.0, mu=g["mu"], dom_x=4, dom_y=4, sub_block=2,
               exchange_every=2, init=1, init_seed=5)
-    hot = P.Sim(eta=0.05, seed=41, n_cycle=256, **kw)
-    hot.sweep(1000)
+    hot = P.Sim(eta=0.08, seed=41, n_cycle=128, **kw)
+    hot.sweep(4000)
     hot.rows()
     snap = hot.export()
     hot.close()
@@ -251,7 +254,7 @@ def test_gpu_superfluid_eta_series_linear_fit():
     b.sweep(500)
     for i in range(len(reps)):
         b.set_n_cycle(i, P.n_cycle(b.params[i], b.rows(i)[250:]))
-    b.sweep(1500)
+    b.sweep(2500)
     for i in range(len(reps)):
         b.rows(i)
     E = [[] for _ in reps]
@@ -268,7 +271,7 @@ def test_gpu_superfluid_eta_series_linear_fit():
         a, slope = cov @ (A.T @ (w * y))
         return y, errs, a, float(np.sqrt(cov[0, 0])), slope
 
-    for blk in range(4):
+    for blk in range(6):
         b.sweep(1500)
         for i in range(len(reps)):
             E[i].append(P.observables(b.rows(i), b.params[i])["E"])

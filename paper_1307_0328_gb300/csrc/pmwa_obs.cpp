@@ -37,7 +37,8 @@ bool model_of(const pmwa_params* p, Model* m) {
   m->eta = p->eta;
   m->t = p->t;
   const int dx = p->dom_x ? p->dom_x : p->Lx, dy = p->dom_y ? p->dom_y : p->Ly;
-  m->domains = double(p->Lx / dx) * double(p->Ly / dy);
+  const int nt = p->dom_tau > 1 ? p->dom_tau : 1;
+  m->domains = double(p->Lx / dx) * double(p->Ly / dy) * double(nt);
   return true;
 }
 

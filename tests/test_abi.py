@@ -79,7 +79,9 @@ def _oracle_rows(**kw):
 @pytest.mark.parametrize("kw", [dict(Lx=4, Ly=4, beta=2.0, eta=0.2, n_cycle=6, seed=3),
                                 dict(Lx=8, Ly=4, beta=1.0, eta=0.3, V=1.0, mu=0.6, t=0.7, dom_x=4,
                                      dom_y=2, n_cycle=4, seed=5),
-                                dict(Lx=4, Ly=4, beta=1.0, eta=0.4, t=0.0, mu=0.5, n_cycle=3, seed=8)])
+                                dict(Lx=4, Ly=4, beta=1.0, eta=0.4, t=0.0, mu=0.5, n_cycle=3, seed=8),
+                                dict(Lx=8, Ly=8, beta=2.0, eta=0.2, V=1.0, mu=0.4, dom_x=4, dom_y=4,
+                                     dom_tau=3, n_cycle=5, seed=11)])
 def test_step6_observables_follow_their_definitions(kw):
     """pmwa_row_observables / pmwa_observables (host code of the library)
     against the Step-6 definitions restated here from the model (Eq. 5 per
@@ -108,7 +110,7 @@ def test_step6_observables_follow_their_definitions(kw):
         b = want[k][: 8 * m].reshape(8, m).mean(axis=1)
         assert s[k] == pytest.approx(b.mean(), rel=1e-12, abs=1e-13), k
         assert s[k + "_err"] == pytest.approx(b.std(ddof=1) / np.sqrt(8), rel=1e-9, abs=1e-15), k
-    nd = (kw["Lx"] // kw.get("dom_x", kw["Lx"])) * (kw["Ly"] // kw.get("dom_y", kw["Ly"]))
+    nd = (kw["Lx"] // kw.get("dom_x", kw["Lx"])) * (kw["Ly"] // kw.get("dom_y", kw["Ly"])) * kw.get("dom_tau", 1)
     used = rows[: 8 * m]
     assert s["w_dom_mean"] == pytest.approx(used["n_w"].mean() / nd, rel=1e-12)
     assert s["w_dom_min"] == used["w_dom_min"].min()

@@ -400,7 +400,8 @@ int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
    candidates (Step 3), 1 leg merge (Step 3), 2 worm creation (Step 4),
    3 scattering (Step 5) outside the passes, 4 output + measurement
    (Step 6), 5 per-pass set-up of Step 5 (bucketing, label order, random
-   words), 6 the moves of Step 5; n >= 8 entries,
+   words), 6 the moves of Step 5; 7 (a count, not cycles) the rounds of
+   independent moves the passes of Step 5 took; n >= 8 entries,
    cleared after reading.  No paper counterpart: measurement plumbing. */
 int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n);
 

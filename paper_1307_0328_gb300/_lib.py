@@ -327,7 +327,7 @@ def pmwa_profile_read(h):
 
 
 PHASES = ("vertex_candidates", "leg_merge", "worm_creation", "scatter", "output_measure",
-          "scatter_pass_setup", "scatter_moves")
+          "scatter_pass_setup", "scatter_moves", "scatter_rounds")
 
 
 def pmwa_profile_phases(h):

@@ -4,7 +4,7 @@ The tuner picks, per instance, the domain edge and the Step-5 sub-block edge.
 A CTA's time is set mostly by per-site chains (the legs of one site are
 handled in order), which do not depend on the domain's size, so a batch's
 throughput follows the number of sites resident per SM: CTAs per SM (shared
-memory of the plan, pmwa_tile_smem; about 80 registers a thread; the 32-CTA
+memory of the plan, pmwa_tile_smem; up to 128 registers a thread; the 32-CTA
 limit) times the sites of a domain.  Among the square domains that divide L,
 at most 16 and at least 4 sites wide when the lattice allows it, the tuner
 takes the most sites per SM, then the most warps per SM, then the larger
@@ -36,8 +36,8 @@ def _threads(sites):
 def per_sm(smem, sites):
     """CTAs of a domain plan per SM: shared memory (1 KB the hardware
     reserves a CTA, up to 1 KB of the kernels' static shared memory),
-    registers (about 80 a thread) and the 32-CTA limit."""
-    by_regs = 65536 // (80 * _threads(sites))
+    registers (up to 128 a thread) and the 32-CTA limit."""
+    by_regs = 65536 // (128 * _threads(sites))
     return min(SM_SMEM // (smem + 2048), by_regs, 32)
 
 

@@ -37,10 +37,11 @@ constexpr int kSmemLimit = 232448;  // opt-in shared memory per block on sm_103a
 
 struct WormRec {
   uint64_t key;
-  uint64_t lab;
+  uint64_t lab;   // label (Step 4); in a Step-5 pass the move's intervals, then its wait mask
   uint16_t site;  // local site index
   uint16_t leg;   // leg array index of the delimiter just below (kNone: site without legs)
-  uint32_t slab;  // temporal slab (0 without temporal domains); fixed through Step 5
+  uint16_t slab;  // temporal slab (0 without temporal domains); fixed through Step 5
+  uint16_t xr;    // in a Step-5 pass: rank in the sub-block, then the round of the move
 };
 
 struct Misc {
@@ -232,52 +233,75 @@ __device__ int leg_index(const Tile& T, int x, uint64_t pv) {
   return (lo < en && kpk(T.leg[lo]) == pv) ? lo : -1;
 }
 
-__device__ __forceinline__ uint32_t site_leg(const WormRec& w) {
-  return *reinterpret_cast<const uint32_t*>(&w.site);  // site | leg << 16
-}
+constexpr uint64_t kFpTurn = ~0ull;  // descriptor of a worm that turns round whatever the others do
 
-// The worm at (site li, interval above leg L) heading up or down: reverse at
-// another worm of its interval or at a vertex of an inactive bond; otherwise
-// enter the vertex v with probability L_min / L_i (word0 >> 32 against the
-// exact ratio), leave by leg j (threshold table, low half of word0), land on
-// a uniform worm grid point of leg j (mulhi of word1) heading away from v.
-// Leg l of v runs from v to the nearest event on its site and side (other
-// vertex leg or worm, the moving worm excluded; the whole circle if none).
-__device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q,
-                         uint64_t w0, uint64_t w1) {
-  WormRec& w = T.W[seg[r]];
+// The vertex that a Step-5 move of worm w (rank r in its sub-block) in pass
+// pattern q reaches, as two words.  d0: the four intervals round the vertex,
+// each named by the leg index of its lower delimiter -- ia_dn, ia on the
+// bond's lower site a and ib_dn, ib on its upper site b (ia, ib: the vertex's
+// legs); d1: the legs ia_up, ib_up above the vertex, the bond's other site
+// (not w's) and r, 16 bits each.  d0 = kFpTurn: the worm turns round whatever
+// the other worms do (a site without legs, a temporal boundary, a bond to
+// another domain or sub-block).  Returns PMWA_EINVARIANT when the vertex has
+// no partner leg on the other site.
+__device__ int move_desc(const Tile& T, const WormRec& w, int q, int r, uint64_t& d0, uint64_t& d1) {
+  d0 = kFpTurn;
+  d1 = 0;
   const int li = w.site;
-  const uint64_t key = w.key;
-  const bool up = kdir(key);
   const int st = T.off[li], en = T.off[li + 1];
-  if (st == en) { w.key = key ^ 2u; return PMWA_OK; }  // a site of worms only
+  if (st == en) return PMWA_OK;
   const int L = w.leg;
-  const uint64_t pL = kpk(T.leg[L]);
-  const uint64_t my = (kpk(key) - pL) & kMask62;
-  const uint32_t self = uint32_t(li) | (uint32_t(L) << 16);
-  if (T.wcnt[L] > 1) {  // other worms share the interval: is one of them ahead?
-    for (int k = 0; k < n; ++k) {
-      const WormRec& o = T.W[seg[k]];
-      if (k == r || site_leg(o) != self) continue;
-      const uint64_t off = (kpk(o.key) - pL) & kMask62;
-      if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
-    }
-  }
-  const int iv = up ? ((L + 1 == en) ? st : L + 1) : L;
-  const uint64_t pv = kpk(T.leg[iv]);
-  if (ktag(T.leg[iv]) == 6) { w.key = key ^ 2u; return PMWA_OK; }  // a temporal boundary
-  const int nb = T.nbr[li * 6 + ktag(T.leg[iv])];
-  if (nb < 0) { w.key = key ^ 2u; return PMWA_OK; }   // bond to another domain
+  const int iv = kdir(w.key) ? ((L + 1 == en) ? st : L + 1) : L;
+  const uint64_t kv = T.leg[iv];
+  if (ktag(kv) == 6) return PMWA_OK;
+  const int nb = T.nbr[li * 6 + ktag(kv)];
+  if (nb < 0) return PMWA_OK;
   const int pl = nb >> 1;
-  const bool li_a = nb & 1;                            // li is the bond's lower site
-  if (T.sub[li * 4 + q] != T.sub[pl * 4 + q]) { w.key = key ^ 2u; return PMWA_OK; }
-  const int ip = T.d->use_part ? (T.part[iv] == kNone ? -1 : int(T.part[iv])) : leg_index(T, pl, pv);
+  if (T.sub[li * 4 + q] != T.sub[pl * 4 + q]) return PMWA_OK;
+  const int ip = T.d->use_part ? (T.part[iv] == kNone ? -1 : int(T.part[iv])) : leg_index(T, pl, kpk(kv));
   if (ip < 0) return PMWA_EINVARIANT;
+  const bool li_a = nb & 1;  // li is the bond's lower site
   const int al = li_a ? li : pl, bl = li_a ? pl : li;
   const int ia = li_a ? iv : ip, ib = li_a ? ip : iv;
   const int sa = T.off[al], ea = T.off[al + 1], sb = T.off[bl], eb = T.off[bl + 1];
   const int ia_dn = (ia == sa) ? ea - 1 : ia - 1, ib_dn = (ib == sb) ? eb - 1 : ib - 1;
   const int ia_up = (ia + 1 == ea) ? sa : ia + 1, ib_up = (ib + 1 == eb) ? sb : ib + 1;
+  d0 = uint64_t(ia_dn) | (uint64_t(ia) << 16) | (uint64_t(ib_dn) << 32) | (uint64_t(ib) << 48);
+  d1 = uint64_t(ia_up) | (uint64_t(ib_up) << 16) | (uint64_t(pl) << 32) | (uint64_t(r) << 48);
+  return PMWA_OK;
+}
+
+// A Step-5 move of worm w = T.W[seg[r]] that reaches the vertex of its
+// descriptor (d0 != kFpTurn); seg[0..n) are the worms of its sub-block, the
+// only ones that can sit on the sub-block's sites.  The worm reverses at
+// another worm ahead of it in its interval; otherwise it enters the vertex v
+// with probability L_min / L_i (word0 >> 32 against the exact ratio), leaves
+// by leg j (threshold table, low half of word0) and lands on a uniform worm
+// grid point of leg j (mulhi of word1) heading away from v.  Leg l of v runs
+// from v to the nearest event on its site and side (another vertex leg or
+// worm, the moving worm excluded; the whole circle if none).  Legs are
+// unique to their sites, so a worm's interval is named by its leg alone.
+__device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t d0, uint64_t d1, const uint16_t* seg, int n, int r,
+                           uint64_t w0, uint64_t w1) {
+  const uint64_t key = w.key;
+  const bool up = kdir(key);
+  const int li = w.site, L = w.leg;
+  const int ia_dn = int(d0 & 0xffff), ia = int((d0 >> 16) & 0xffff);
+  const int ib_dn = int((d0 >> 32) & 0xffff), ib = int(d0 >> 48);
+  const int ia_up = int(d1 & 0xffff), ib_up = int((d1 >> 16) & 0xffff), pl = int((d1 >> 32) & 0xffff);
+  const bool li_a = (L == ia || L == ia_dn);  // the worm sits on the bond's lower site
+  const uint64_t pL = kpk(T.leg[L]);
+  const uint64_t my = (kpk(key) - pL) & kMask62;
+  if (T.wcnt[L] > 1) {  // other worms share the interval: is one of them ahead?
+    for (int k = 0; k < n; ++k) {
+      const WormRec& o = T.W[seg[k]];
+      if (k == r || int(o.leg) != L) continue;
+      const uint64_t off = (kpk(o.key) - pL) & kMask62;
+      if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
+    }
+  }
+  const uint64_t pv = kpk(T.leg[ia]);
+  const int al = li_a ? li : pl, bl = li_a ? pl : li;
   const uint64_t pa_dn = kpk(T.leg[ia_dn]), pb_dn = kpk(T.leg[ib_dn]);
   // offsets from v up to the nearest object above, and from the lower leg up
   // to the highest worm of the interval below v
@@ -285,21 +309,19 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   uint64_t ub = (ib_up == ib) ? kTwo62 : ((kpk(T.leg[ib_up]) - pv) & kMask62);
   uint64_t da = 0, db = 0;
   bool fa = false, fb = false;
-  const uint32_t ka_up = uint32_t(al) | (uint32_t(ia) << 16), kb_up = uint32_t(bl) | (uint32_t(ib) << 16);
-  const uint32_t ka_dn = uint32_t(al) | (uint32_t(ia_dn) << 16), kb_dn = uint32_t(bl) | (uint32_t(ib_dn) << 16);
   // worms (other than this one) in the four intervals around v?
   int others = T.wcnt[ia] + T.wcnt[ib] + (ia_dn != ia ? T.wcnt[ia_dn] : 0) + (ib_dn != ib ? T.wcnt[ib_dn] : 0) - 1;
   for (int k = 0; k < n && others > 0; ++k) {
     if (k == r) continue;
     const WormRec& o = T.W[seg[k]];
-    const uint32_t sl = site_leg(o);
-    if (sl != ka_up && sl != kb_up && sl != ka_dn && sl != kb_dn) continue;
+    const int lg = o.leg;
+    if (lg != ia && lg != ib && lg != ia_dn && lg != ib_dn) continue;
     --others;
     const uint64_t po = kpk(o.key);
-    if (sl == ka_up) { const uint64_t x = (po - pv) & kMask62; if (x < ua) ua = x; }
-    if (sl == kb_up) { const uint64_t x = (po - pv) & kMask62; if (x < ub) ub = x; }
-    if (sl == ka_dn) { const uint64_t x = (po - pa_dn) & kMask62; if (!fa || x > da) { da = x; fa = true; } }
-    if (sl == kb_dn) { const uint64_t x = (po - pb_dn) & kMask62; if (!fb || x > db) { db = x; fb = true; } }
+    if (lg == ia) { const uint64_t x = (po - pv) & kMask62; if (x < ua) ua = x; }
+    if (lg == ib) { const uint64_t x = (po - pv) & kMask62; if (x < ub) ub = x; }
+    if (lg == ia_dn) { const uint64_t x = (po - pa_dn) & kMask62; if (!fa || x > da) { da = x; fa = true; } }
+    if (lg == ib_dn) { const uint64_t x = (po - pb_dn) & kMask62; if (!fb || x > db) { db = x; fb = true; } }
   }
   const uint64_t L2 = wpts(pv, (pv + ua) & kMask62);
   const uint64_t L3 = wpts(pv, (pv + ub) & kMask62);
@@ -324,17 +346,25 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   const uint64_t vx = T.leg[ix];
   const uint64_t Lj = (j == 0) ? L0 : (j == 1) ? L1 : (j == 2) ? L2 : L3;
   const uint64_t o = __umul64hi(w1, Lj);
+  const int nl = (j >= 2) ? ix : ((j & 1) ? ib_dn : ia_dn);
+  w.key = (j >= 2) ? wkey((wm_above(pv) + o) & (kTwo59 - 1), 1, kab(vx) ^ 1)
+                   : wkey((wm_below(pv) + kTwo59 - o) & (kTwo59 - 1), 0, kbl(vx));
   T.wcnt[L] -= 1;
-  if (j >= 2) {
-    w.key = wkey((wm_above(pv) + o) & (kTwo59 - 1), 1, kab(vx) ^ 1);
-    w.leg = uint16_t(ix);
-  } else {
-    w.key = wkey((wm_below(pv) + kTwo59 - o) & (kTwo59 - 1), 0, kbl(vx));
-    w.leg = uint16_t((j & 1) ? ib_dn : ia_dn);
-  }
-  T.wcnt[w.leg] += 1;
-  w.site = uint16_t((j & 1) ? bl : al);
+  T.wcnt[nl] += 1;
+  // site and leg in one store: a move of the same pass that runs beside this
+  // one reads either the old or the new pair
+  *reinterpret_cast<uint32_t*>(&w.site) = uint32_t((j & 1) ? bl : al) | (uint32_t(nl) << 16);
   return PMWA_OK;
+}
+
+// One Step-5 move of worm seg[r] in pass pattern q, from scratch.
+__device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q, uint64_t w0, uint64_t w1) {
+  WormRec& w = T.W[seg[r]];
+  uint64_t d0, d1;
+  const int rc = move_desc(T, w, q, r, d0, d1);
+  if (rc) return rc;
+  if (d0 == kFpTurn) { w.key ^= 2u; return PMWA_OK; }
+  return tile_move_d(T, w, d0, d1, seg, n, r, w0, w1);
 }
 
 // per-phase cycle counters (profiling only): thread 0 adds the cycles since
@@ -352,6 +382,95 @@ __device__ __forceinline__ void phase_tick(const Dev& d, int k, long long& t) {
 // boundaries and every leg ends there)
 __device__ __forceinline__ int worm_group(const Tile& T, const WormRec& w, int q) {
   return int(T.sub[w.site * 4 + q]) * T.d->ntau + int(w.slab);
+}
+
+// ---------------------------------------------------------------------------
+// Rounds of independent moves.  In a pass the worms of one sub-block move one
+// after another in label order, and a move reads and writes nothing but its
+// own worm and the four intervals round the vertex it reaches: their worm
+// counts, the worms in them and the states of the vertex's two legs.  A worm
+// that turns round whatever the others do changes nothing another move
+// reads.  So a move need wait only for the earlier moves of its sub-block
+// whose intervals meet its own: rounds that run every move whose such
+// predecessors have run give exactly the configuration of the moves made one
+// by one.
+constexpr int kNear = 47;  // predecessors a wait mask names one by one
+constexpr uint64_t kNearMask = (1ull << kNear) - 1;
+constexpr uint16_t kPending = 0xFFFF;
+
+// do two sets of four intervals (16-bit leg indices) share one?
+__device__ __forceinline__ bool fp_meet(uint64_t a, uint64_t b) {
+  const uint32_t a0 = uint32_t(a), a1 = uint32_t(a >> 32), b0 = uint32_t(b), b1 = uint32_t(b >> 32);
+  const uint32_t c0 = __byte_perm(b0, 0, 0x1032), c1 = __byte_perm(b1, 0, 0x1032);  // halves swapped
+  return (__vcmpeq2(a0, b0) | __vcmpeq2(a0, c0) | __vcmpeq2(a0, b1) | __vcmpeq2(a0, c1) | __vcmpeq2(a1, b0) |
+          __vcmpeq2(a1, c0) | __vcmpeq2(a1, b1) | __vcmpeq2(a1, c1)) != 0;
+}
+
+// The moves of one pass (all threads).  On entry the grouped order idx[]
+// (position p = fill[u] + r holds the r-th worm of group u), each position's
+// move descriptor in rw[2p], rw[2p + 1] and each worm's group in xr are in
+// place.  First each worm's wait mask goes to lab: bit i (i < kNear) = wait
+// for position p - 1 - i, bits kNear.. = the group, bit 63 = also wait for
+// every position of the group more than kNear before it.  Then rounds until
+// every worm has moved, each move drawing Philox block r of stream
+// (domain * groups + u, c2) and recording its round in xr.  Ends with a
+// barrier.
+__device__ void pass_rounds(const Tile& T, int dom, int nw, uint32_t c2) {
+  const Dev& d = *T.d;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int p = tid; p < nw; p += NT) {
+    WormRec& w = T.W[T.idx[p]];
+    const uint64_t f = T.rw[2 * p];
+    uint64_t m = uint64_t(w.xr) << kNear;
+    if (f != kFpTurn) {
+      const int r = int(T.rw[2 * p + 1] >> 48);
+      for (int i = 0; i < r; ++i) {
+        const uint64_t g = T.rw[2 * (p - 1 - i)];
+        if (g != kFpTurn && fp_meet(f, g)) m |= (i < kNear) ? (1ull << i) : (1ull << 63);
+      }
+    }
+    w.lab = m;
+  }
+  __syncthreads();
+  for (int p = tid; p < nw; p += NT) T.W[T.idx[p]].xr = kPending;
+  __syncthreads();
+  for (int round = 0;; ++round) {
+    int pending = 0;
+    for (int p = tid; p < nw; p += NT) {
+      WormRec& w = T.W[T.idx[p]];
+      if (w.xr != kPending) continue;
+      const uint64_t d0 = T.rw[2 * p];
+      if (d0 == kFpTurn) {
+        w.key ^= 2u;
+        w.xr = uint16_t(round);
+        continue;
+      }
+      const uint64_t d1 = T.rw[2 * p + 1], m = w.lab;
+      const int r = int(d1 >> 48), u = int((m >> kNear) & 0xffff);
+      bool ready = true;
+      for (uint64_t b = m & kNearMask; b && ready; b &= b - 1)
+        ready = T.W[T.idx[p - __ffsll((long long)b)]].xr < round;
+      if (ready && (m >> 63))
+        for (int j = p - r; j < p - kNear && ready; ++j) ready = T.W[T.idx[j]].xr < round;
+      if (!ready) {
+        pending = 1;
+        continue;
+      }
+      const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
+      const int rc = tile_move_d(T, w, d0, d1, T.idx + (p - r), T.fill[u + 1] - T.fill[u], r,
+                                 uint64_t(b.x) | (uint64_t(b.y) << 32), uint64_t(b.z) | (uint64_t(b.w) << 32));
+      if (rc) tile_fail(T.misc, rc, 5);
+      w.xr = uint16_t(round);
+    }
+    if (!__syncthreads_or(pending)) {
+      if (d.phase_cycles && tid == 0) atomicAdd(d.phase_cycles + 7, (unsigned long long)(round + 1));
+      break;
+    }
+    if (round >= nw) {  // (each round moves the first waiting worm of every group: never taken)
+      if (tid == 0) tile_fail(T.misc, PMWA_EINVARIANT, 7);
+      break;
+    }
+  }
 }
 
 __device__ __forceinline__ bool worm_less(const WormRec& a, const WormRec& b) {
@@ -777,7 +896,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           if (o + n > d.wcap) bad = PMWA_ECAPACITY;
           for (int k = 0; k < n && !bad; ++k) {
             const uint64_t w = rs.word();
-            T.W[o + k] = WormRec{wkey(offs[k], int(w & 1), s0 ^ 1 ^ (k & 1)), w >> 1, uint16_t(li), kNone, 0u};
+            T.W[o + k] = WormRec{wkey(offs[k], int(w & 1), s0 ^ 1 ^ (k & 1)), w >> 1, uint16_t(li), kNone, 0, 0};
           }
         }
       } else {
@@ -801,7 +920,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           for (int j = 0; j < n; ++j) {
             const uint64_t w = rs.word();
             T.W[o + j] = WormRec{wkey((m0 + offs[j]) & (kTwo59 - 1), int(w & 1), p ^ 1 ^ (j & 1)), w >> 1,
-                                 uint16_t(li), uint16_t(st + k), uint32_t(sl)};
+                                 uint16_t(li), uint16_t(st + k), uint16_t(sl), 0};
           }
         }
       }
@@ -838,14 +957,14 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           // on its rank and sub-block, so it is drawn while fill[] is formed
           int u, r;
           rank_pass_block(T, nw, q, pass, u, r);
-          P4 b{0u, 0u, 0u, 0u};
-          if (u >= 0) b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
           __syncthreads();
           if (u >= 0) {
             const int at = T.fill[u] + r;
             T.idx[at] = T.ord[tid];
-            T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
-            T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+            WormRec& w = T.W[T.ord[tid]];
+            const int rc = move_desc(T, w, q, r, T.rw[2 * at], T.rw[2 * at + 1]);
+            if (rc) tile_fail(misc, rc, 5);
+            w.xr = uint16_t(u);
           }
         } else {
           if (tid < 32) rank_pass(T, nw, q, tid);
@@ -853,22 +972,16 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
           for (int k = tid; k < nw; k += NT) {
             const int u = T.wsb[k], r = T.wrk[k], at = T.fill[u] + r;
             T.idx[at] = T.ord[k];
-            const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
-            T.rw[2 * at] = uint64_t(b.x) | (uint64_t(b.y) << 32);
-            T.rw[2 * at + 1] = uint64_t(b.z) | (uint64_t(b.w) << 32);
+            WormRec& w = T.W[T.ord[k]];
+            const int rc = move_desc(T, w, q, r, T.rw[2 * at], T.rw[2 * at + 1]);
+            if (rc) tile_fail(misc, rc, 5);
+            w.xr = uint16_t(u);
           }
         }
         __syncthreads();
         phase_tick(d, 5, tclk);
-        for (int u = tid; u < T.ngrp; u += NT) {
-          const int lo = T.fill[u], n = T.fill[u + 1] - lo;
-          const uint16_t* seg = T.idx + lo;
-          for (int r = 0; r < n; ++r) {
-            const int rc = tile_move(T, seg, n, r, q, T.rw[2 * (lo + r)], T.rw[2 * (lo + r) + 1]);
-            if (rc) { tile_fail(misc, rc, 5); break; }
-          }
-        }
-        __syncthreads();
+        if (misc->err) goto fail;
+        pass_rounds(T, dom, nw, c2);
         phase_tick(d, 6, tclk);
         if (misc->err) goto fail;
       }
@@ -1037,8 +1150,10 @@ fail:
   if (tid == 0) set_err(d.err, misc->err, misc->where);
 }
 
+// CTAs of NT threads may use up to 128 registers a thread (512 / NT CTAs per
+// SM by registers)
 template <int NT, bool OTF>
-__global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ Dev d, int stop) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_tile(const __grid_constant__ Dev d, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wsum[32];
   if (instance_failed(d.err)) return;
@@ -1049,7 +1164,7 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ Dev d, int 
 // parameters are copied into shared memory and advanced to sweep iteration
 // `it` of the current batch call (buffers, sweep index, row).
 template <int NT>
-__global__ void __launch_bounds__(NT) k_tile_batch(const Dev* __restrict__ devs,
+__global__ void __launch_bounds__(NT, 512 / NT) k_tile_batch(const Dev* __restrict__ devs,
                                                    const BatchBase* __restrict__ base,
                                                    const int2* __restrict__ work, int it, int stop) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -1103,9 +1218,9 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   const long long want = std::min<long long>((long long)legs_want, 65000);
   const long long limit = (long long)kSmemLimit - 1024;
   // CTAs per SM: shared memory (1 KB the hardware reserves a CTA and up to
-  // 1 KB of static shared memory), registers (about 80 a thread: 3, 6 or 12
+  // 1 KB of static shared memory), registers (up to 128 a thread: 2, 4 or 8
   // CTAs of 256, 128 or 64 threads) and the 32-CTA limit
-  const long long by_regs = nds <= 32 ? 12 : (nds <= 96 ? 6 : 3);
+  const long long by_regs = nds <= 32 ? 8 : (nds <= 96 ? 4 : 2);
   auto per_sm = [&](long long bytes) { return std::min(std::min((228LL * 1024) / (bytes + 2048), by_regs), 32LL); };
   // without staging
   const long long uni0 = (long long)std::max(worm_bytes, pool_bytes);

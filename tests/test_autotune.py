@@ -18,8 +18,8 @@ from paper_1307_0328_gb300 import autotune as A
 def test_residency_counts_static_shared_memory():
     assert A.per_sm(115648, 64) == 1
     assert A.per_sm(113000, 64) == 2
-    assert A.per_sm(1000, 16) == 65536 // (80 * 64)
-    assert A.per_sm(1000, 256) == 65536 // (80 * 256)
+    assert A.per_sm(1000, 16) == 65536 // (128 * 64)
+    assert A.per_sm(1000, 256) == 65536 // (128 * 256)
 
 
 def _admissible(p):

@@ -29,15 +29,22 @@ def _divisors(L):
     return [s for s in range(L, 1, -1) if L % s == 0]
 
 
-def _threads(sites):
-    return 64 if sites <= 32 else (128 if sites <= 96 else 256)
+def _threads(sites, smem=None):
+    """Threads of the sweep kernel's CTA for a domain plan, as the library
+    picks them: 64, 128 or 256 by the domain's sites, 512 for a large domain
+    whose plan leaves room for one CTA per SM."""
+    if sites <= 32:
+        return 64
+    if sites <= 96:
+        return 128
+    return 512 if smem is not None and SM_SMEM // (smem + 2048) <= 1 else 256
 
 
 def per_sm(smem, sites):
     """CTAs of a domain plan per SM: shared memory (1 KB the hardware
     reserves a CTA, up to 1 KB of the kernels' static shared memory),
     registers (up to 128 a thread) and the 32-CTA limit."""
-    by_regs = 65536 // (128 * _threads(sites))
+    by_regs = 65536 // (128 * _threads(sites, smem))
     return min(SM_SMEM // (smem + 2048), by_regs, 32)
 
 
@@ -83,7 +90,7 @@ def tune(p):
         if not sm or plan["legcap"] < min(int(legs_wanted(trial, sites)), 65000):
             continue
         k = per_sm(sm, sites)
-        score = (k * sites, k * _threads(sites), sites)
+        score = (k * sites, k * _threads(sites, sm), sites)
         if best_score is None or score > best_score:
             best, best_score = dict(dom_x=sx, dom_y=sy, sub_block=B), score
     if best is None:

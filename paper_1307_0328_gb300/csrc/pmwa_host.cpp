@@ -1027,7 +1027,7 @@ bool batch_layout(const pmwa_params* p, int n, BatchLayout* L) {
 // whose plans allow different residencies go to different launches: a few
 // large plans then do not cut the residency of all the others.
 int batch_group(const Dev& d) {
-  const int c = tile_class(d.dom_x * d.dom_y);
+  const int c = tile_class(d.dom_x * d.dom_y, d.sm_total);
   // (1 KB the hardware reserves a CTA, up to 1 KB of static shared memory)
   const int per_sm = int((228LL * 1024) / (static_cast<long long>(d.sm_total) + 2048));
   const int r = per_sm >= 8 ? 5 : per_sm >= 6 ? 4 : per_sm >= 4 ? 3 : per_sm >= 3 ? 2 : per_sm >= 2 ? 1 : 0;
@@ -1133,10 +1133,10 @@ int batch_upload(pmwa_batch* b) {
       cudaMemcpy(b->tile_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice))
     return PMWA_ECUDA;
   // the largest reservation of each CTA-size class is its kernel's allowance
-  int allow[3] = {0, 0, 0};
+  int allow[4] = {0, 0, 0, 0};
   for (int g = 0; g < kBatchGroups; ++g)
     if (b->cls_n[g]) allow[b->cls_thr[g]] = std::max(allow[b->cls_thr[g]], b->cls_smem[g]);
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < 4; ++c)
     if (allow[c] && prepare_tile_batch(c, allow[c])) return PMWA_ECUDA;
   return PMWA_OK;
 }

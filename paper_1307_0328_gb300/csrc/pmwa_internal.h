@@ -134,10 +134,10 @@ int launch_temporal_batch(const Dev* devs, const BatchBase* base, const int2* wo
 int temporal_sites_per_block();
 int prepare_temporal(int cap);
 int launch_tile(const Dev& d, int stop, void* stream);
-int tile_class(int domain_sites);
+int tile_class(int domain_sites, int smem);
 // batch launch groups: 3 CTA-size classes x residency levels by shared memory
 constexpr int kResidencyLevels = 6;
-constexpr int kBatchGroups = 3 * kResidencyLevels;
+constexpr int kBatchGroups = 4 * kResidencyLevels;
 int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int2* work, int n_work, int smem,
                       int it, int stop, void* stream);
 int launch_boundary_batch(const Dev* devs, const BatchBase* base, const int2* work, int n_work, int it, int dir,

@@ -110,7 +110,7 @@ struct Tile {
   uint16_t* wrk;   // [wcap] rank of the k-th worm inside its sub-block (a pass)
   uint64_t* rw;    // [2 wcap] Philox words of each grouped position (a pass)
   int* bkt;        // [max(nsub, nds) + 1]
-  int* cnt;        // [warps x nsub] per 32-worm chunk: pass stamp << 16 | worms of sub-block u
+  uint16_t* cnt;   // [warps x groups] per 32-worm chunk: pass stamp << 8 | worms of group u
   int* fill;       // [max(nsub, nds)]
   int16_t* nbr;    // [6 nds] per leg tag: partner site << 1 | lower-site bit, -1 off-domain
   uint8_t* tinfo;  // [6 nds] per leg tag: 1 = lower site of the bond, 2 = bond leaves the domain
@@ -560,30 +560,34 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
 // (called by every thread; contains one block barrier).  Warp c ranks the
 // 32 worms of chunk c of the label order among themselves (__match_any_sync)
 // and its group leaders record the chunk's count of each sub-block in
-// cnt[c][u], stamped with the pass (an entry with another stamp counts 0).
+// cnt[c][u], stamped with pass_stamp(pass) (an entry with another stamp
+// counts 0; the table is cleared every 255 passes, so a stale stamp never
+// matches).
 // After the barrier every worm adds the counts of the earlier chunks to its
 // rank, while one warp forms fill[] from the totals: the last warp when it
 // holds no worms, else warp 0 (whose worms add nothing).  The worm of thread
 // k = threadIdx.x gets its sub-block u (-1: no worm) and rank r; fill comes
 // out as rank_pass makes it (after a barrier); bkt[] is scratch.
+__device__ __forceinline__ int pass_stamp(int pass) { return ((pass % 255) + 1) << 8; }
+
 __device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_out, int& r_out) {
   const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int W = (nw + 31) >> 5, n = T.ngrp;
-  const int stamp = (pass + 1) << 16;
+  const int stamp = pass_stamp(pass);
   const int k = tid;
   int u = -1, r = 0;
   if (c < W) {  // warp-uniform
     u = (k < nw) ? worm_group(T, T.W[T.ord[k]], q) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     r = __popc(peers & lt);
-    if (u >= 0 && (peers & lt) == 0) T.cnt[c * n + u] = stamp | __popc(peers);
+    if (u >= 0 && (peers & lt) == 0) T.cnt[c * n + u] = uint16_t(stamp | __popc(peers));
   }
   __syncthreads();
   if (c > 0 && u >= 0) {
     for (int c2 = 0; c2 < c; ++c2) {
       const int v = T.cnt[c2 * n + u];
-      if ((v & ~0xffff) == stamp) r += v & 0xffff;
+      if ((v & ~0xff) == stamp) r += v & 0xff;
     }
   }
   u_out = u;
@@ -597,7 +601,7 @@ __device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_o
       int tot = 0;
       for (int c2 = 0; c2 < W; ++c2) {
         const int v = T.cnt[c2 * n + i];
-        if ((v & ~0xffff) == stamp) tot += v & 0xffff;
+        if ((v & ~0xff) == stamp) tot += v & 0xff;
       }
       T.bkt[i] = tot;
       sum += tot;
@@ -680,7 +684,7 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   T.wrk = reinterpret_cast<uint16_t*>(sm + d.sm_wrk);
   T.rw = reinterpret_cast<uint64_t*>(sm + d.sm_rw);
   T.bkt = reinterpret_cast<int*>(sm + d.sm_bkt);
-  T.cnt = reinterpret_cast<int*>(sm + d.sm_cnt);
+  T.cnt = reinterpret_cast<uint16_t*>(sm + d.sm_cnt);
   T.fill = reinterpret_cast<int*>(sm + d.sm_fill);
   T.nbr = reinterpret_cast<int16_t*>(sm + d.sm_nbr);
   T.tinfo = reinterpret_cast<uint8_t*>(sm + d.sm_tinfo);
@@ -953,8 +957,11 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
         const int q = pass & 3;
         const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
         if (nw <= NT) {
-          // all warps, one chunk each; each worm's Philox block depends only
-          // on its rank and sub-block, so it is drawn while fill[] is formed
+          // all warps, one chunk each
+          if (pass > 0 && pass % 255 == 0) {  // the stamps start over: no entry may carry one
+            for (int i = tid; i < (NT >> 5) * T.ngrp; i += NT) T.cnt[i] = 0;
+            __syncthreads();
+          }
           int u, r;
           rank_pass_block(T, nw, q, pass, u, r);
           __syncthreads();
@@ -1207,9 +1214,9 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
   // worm side of the union: table, index, label order, sub-block ids and
   // ranks, Philox words, two bucket arrays
   // (and the per-chunk sub-block counts of the block-wide grouping: one row
-  // per warp of the domain's CTA)
-  const int warps = (nds <= 32 ? 64 : (nds <= 96 ? 128 : 256)) / 32;
-  const size_t cnt_bytes = up16(size_t(warps) * size_t(nsub) * sizeof(int));
+  // per warp of the domain's CTA, 16 for CTAs of 256 or 512 threads)
+  const int warps = nds <= 32 ? 2 : (nds <= 96 ? 4 : 16);
+  const size_t cnt_bytes = up16(size_t(warps) * size_t(nsub) * sizeof(uint16_t));
   const size_t worm_bytes = up16(size_t(d->wcap) * sizeof(WormRec)) + 4 * up16(size_t(d->wcap) * 2) +
                             up16(size_t(d->wcap) * 16) + 2 * up16(size_t(nb) * sizeof(int)) + cnt_bytes;
   // (on-the-fly windows: the worms of the current configuration by site, beside the pool)
@@ -1273,15 +1280,22 @@ bool plan_tile_smem(Dev* d, double legs_want, double cands_per_bond) {
 int upload_zig_tile(const Zig& z) { return upload_constants(z); }
 
 // CTA sizes of the sweep kernel: small domains take small CTAs, so that many
-// of them share an SM (class 0: 64 threads, 1: 128, 2: 256)
-int tile_class(int domain_sites) { return domain_sites <= 32 ? 0 : (domain_sites <= 96 ? 1 : 2); }
+// of them share an SM (class 0: 64 threads, 1: 128, 2: 256); a large domain
+// whose plan leaves room for one CTA per SM takes 512 threads (class 3),
+// which the registers then allow
+int tile_class(int domain_sites, int smem) {
+  if (domain_sites <= 32) return 0;
+  if (domain_sites <= 96) return 1;
+  return (228LL * 1024) / (static_cast<long long>(smem) + 2048) <= 1 ? 3 : 2;
+}
 
 int prepare_tile_batch(int cls, int smem) {
   cudaError_t e;
   switch (cls) {
     case 0: e = cudaFuncSetAttribute(k_tile_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
     case 1: e = cudaFuncSetAttribute(k_tile_batch<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
-    default: e = cudaFuncSetAttribute(k_tile_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 2: e = cudaFuncSetAttribute(k_tile_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    default: e = cudaFuncSetAttribute(k_tile_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
   }
   return int(e);
 }
@@ -1293,7 +1307,8 @@ int launch_tile_batch(int cls, const Dev* devs, const BatchBase* base, const int
   switch (cls) {
     case 0: k_tile_batch<64><<<n_work, 64, smem, st>>>(devs, base, work, it, stop); break;
     case 1: k_tile_batch<128><<<n_work, 128, smem, st>>>(devs, base, work, it, stop); break;
-    default: k_tile_batch<256><<<n_work, 256, smem, st>>>(devs, base, work, it, stop); break;
+    case 2: k_tile_batch<256><<<n_work, 256, smem, st>>>(devs, base, work, it, stop); break;
+    default: k_tile_batch<512><<<n_work, 512, smem, st>>>(devs, base, work, it, stop); break;
   }
   return int(cudaGetLastError());
 }
@@ -1307,13 +1322,14 @@ static int launch_tile_k(const Dev& d, int stop, cudaStream_t st) {
 }
 
 int launch_tile(const Dev& d, int stop, void* stream) {
-  const int cls = tile_class(d.dom_x * d.dom_y);
+  const int cls = tile_class(d.dom_x * d.dom_y, d.sm_total);
   const cudaStream_t st = cudaStream_t(stream);
   const bool otf = d.win_half > 0;
   switch (cls) {
     case 0: return otf ? launch_tile_k<64, true>(d, stop, st) : launch_tile_k<64, false>(d, stop, st);
     case 1: return otf ? launch_tile_k<128, true>(d, stop, st) : launch_tile_k<128, false>(d, stop, st);
-    default: return otf ? launch_tile_k<256, true>(d, stop, st) : launch_tile_k<256, false>(d, stop, st);
+    case 2: return otf ? launch_tile_k<256, true>(d, stop, st) : launch_tile_k<256, false>(d, stop, st);
+    default: return otf ? launch_tile_k<512, true>(d, stop, st) : launch_tile_k<512, false>(d, stop, st);
   }
 }
 

@@ -57,8 +57,11 @@ GEOMS = [
     dict(Lx=16, Ly=16, beta=4.0, eta=0.3, sub_block=2, n_cycle=6, seed=17, init=1, init_seed=5),
     dict(Lx=32, Ly=32, beta=4.0, eta=0.25, dom_x=16, dom_y=16, sub_block=2, n_cycle=8,
          exchange_every=2, seed=19, init=1, init_seed=9),
+    # more than 255 passes of the block-wide grouping: its per-chunk counts
+    # carry a pass stamp that starts over every 255 passes
+    dict(Lx=16, Ly=16, beta=2.0, eta=0.5, sub_block=2, n_cycle=300, seed=53, init=1, init_seed=6),
 ]
-MANY_WORMS = GEOMS[-2:]
+MANY_WORMS = GEOMS[-3:]
 
 
 def _pair(kw):
@@ -176,7 +179,7 @@ def test_rows_buffer_full_is_reported():
 
 @pytest.mark.parametrize("kw", MANY_WORMS)
 def test_many_worm_cases_exceed_one_warp(kw):
-    """The last two geometries really hold more than 32 worms per domain
+    """The last three geometries really hold more than 32 worms per domain
     (so the block-wide passes are the ones compared above)."""
     g = P.Sim(**kw)
     g.sweep(4)

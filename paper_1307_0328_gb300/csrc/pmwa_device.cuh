@@ -16,6 +16,7 @@ namespace pmwa {
 __constant__ double c_zX[257];
 __constant__ double c_zF[257];
 __constant__ double c_zW[256];
+__constant__ double c_zS[256];
 __constant__ unsigned long long c_zK[256];
 __constant__ unsigned long long c_zXF[256];
 __constant__ unsigned long long c_zRF;
@@ -32,6 +33,7 @@ static int upload_constants(const Zig& z) {
   if ((e = cudaMemcpyToSymbol(c_zX, z.X, sizeof z.X))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zF, z.F, sizeof z.F))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zW, z.W, sizeof z.W))) return int(e);
+  if ((e = cudaMemcpyToSymbol(c_zS, z.S, sizeof z.S))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zK, z.K, sizeof z.K))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zR, &z.R, sizeof z.R))) return int(e);
   if ((e = cudaMemcpyToSymbol(c_zXF, z.XF, sizeof z.XF))) return int(e);
@@ -255,6 +257,16 @@ __device__ inline uint64_t zig_exp(const ZigTab& z, Stream& s, int* bad) {
     const double t1 = __dmul_rn(__ull2double_rn(w2 >> 11), 0x1p-53);
     const double t2 = __dsub_rn(c_zF[i + 1], c_zF[i]);
     const double y = __dadd_rn(c_zF[i], __dmul_rn(t1, t2));
+    // The test y < exp_det(-x), decided first by bounds of e^-x on the
+    // strip's wedge [a, b] = [X[i+1], X[i]]: the tangent at a below
+    // (e^-x >= e^-a (1 - (x - a))) and the chord above (e^-x is convex).
+    // Away from the curve by more than eps = F[i+1] 2^-40 -- far beyond the
+    // rounding of the bounds, of the tables and of exp_det (a few units in
+    // the last place) -- the bounds give the same answer as the exact test,
+    // which runs only inside that margin.
+    const double fa = c_zF[i + 1], dl = __dsub_rn(x, c_zX[i + 1]), eps = __dmul_rn(fa, 0x1p-40);
+    if (y < __dsub_rn(__dmul_rn(fa, __dsub_rn(1.0, dl)), eps)) return zfix_add(acc, xf);
+    if (y > __dadd_rn(__dadd_rn(fa, __dmul_rn(dl, c_zS[i])), eps)) continue;
     if (y < exp_det(-x)) return zfix_add(acc, xf);
   }
   *bad = PMWA_ETIMEOUT;

@@ -321,6 +321,7 @@ static int lay_strips(double R, Zig* z) {
     std::memcpy(z->X, X, sizeof X);
     std::memcpy(z->F, F, sizeof F);
     for (int i = 0; i < 256; ++i) {
+      z->S[i] = (i == 0) ? 0.0 : (F[i] - F[i + 1]) / (X[i] - X[i + 1]);
       z->K[i] = (uint64_t)std::floor(X[i + 1] / X[i] * 0x1p53);
       z->W[i] = X[i] * 0x1p-53;
       z->XF[i] = (uint64_t)(X[i] * 0x1p58);  // exact: 53-bit X[i] >= 2^-5
@@ -432,8 +433,10 @@ int pmwa_create(const pmwa_params* p, void* arena, size_t bytes, void* stream, p
   d.beta = p->beta; d.eta = p->eta; d.SV = g.SV; d.SW = g.SW; d.XW = g.XW; d.SWI = g.SWI;
   d.SVs = g.SVs; d.SWs = g.SWs; d.XQ = g.XQ;
   d.has_vertices = g.D > 0.0 ? 1 : 0;
-  for (int s = 0; s < 4; ++s) { d.TV[s] = g.TV[s]; d.dvw[s] = g.d[s]; }
+  for (int s = 0; s < 4; ++s) { d.TV[s] = g.TV[s]; d.dvw[s] = g.d[s]; d.dvwf[s] = float(g.d[s]); }
   d.tkink = g.tkink;
+  d.tkinkf = float(g.tkink);
+  d.XWf = float(g.XW);
   d.err = reinterpret_cast<DevErr*>(base + L.err);
   d.TH = reinterpret_cast<const uint64_t*>(base + L.TH);
   d.rows = reinterpret_cast<pmwa_row*>(base + L.rows);

@@ -61,6 +61,7 @@ struct Dev {
   uint64_t TV[4];
   double dvw[4];    // diagonal vertex weights d(s), s = na | nb << 1
   double tkink;     // kink weight t
+  float dvwf[4], tkinkf, XWf;  // the same rounded to binary32 (heat-bath pre-decision)
   // buffers
   uint64_t* keyA;   // current configuration: N slots of cap keys
   uint32_t* cntA;   // count | base << 31
@@ -116,6 +117,7 @@ __host__ __device__ inline Dev at_iteration(const Dev& d0, const BatchBase& b, i
 // Exponential ziggurat tables, built on the host (pmwa_host.cpp).
 struct Zig {
   double X[257], F[257], W[256];
+  double S[256];     // slope (F[i] - F[i+1]) / (X[i] - X[i+1]) of strip i's chord (i >= 1)
   uint64_t K[256];
   uint64_t XF[256];  // X[i] 2^58 (exact)
   uint64_t RF;       // R 2^58 (exact)

@@ -175,6 +175,57 @@ __device__ __noinline__ int regen_interval(const Dev& d, const ZigTab& z, Stream
 }
 
 __device__ __forceinline__ double fsig(int sigma, double em1) { return sigma ? -em1 : __dadd_rn(2.0, em1); }
+
+// Eq. 4 in binary32 (lane < 16: state S = lane; all 32 lanes call it): the
+// same heat bath with the leg factors from expm1f and the vertex weights
+// rounded to binary32.  Its cumulative fractions c_S / tot lie within 2^-16
+// of the binary64 ones (expm1f within a few units in the last place, at
+// most four factors and one vertex weight, a sum of at most six terms, each
+// a relative 2^-22 or better), so when the uniform r = (w >> 11) 2^-53 lies
+// more than 2^-12 from 0, 1 and every boundary, the binary64 computation
+// picks the same state.  (A state whose binary32 weight vanishes while its
+// binary64 one does not has a fraction below 2^-100 and so sits within the
+// margin of a neighbouring boundary or of 0.)  Returns that state, or -1.
+__device__ int heat_bath_f32(const Dev& d, const Legs& La, const Legs& Lb, uint64_t w, int lane) {
+  float e4 = 0.f;
+  if (lane < 4) {
+    uint64_t I;
+    if (lane == 0) I = La.single ? kTwo59 : La.Idn;
+    else if (lane == 1) I = Lb.single ? kTwo59 : Lb.Idn;
+    else if (lane == 2) I = La.single ? kTwo59 : La.Iup;
+    else I = Lb.single ? kTwo59 : Lb.Iup;
+    e4 = expm1f(-2.0f * __ull2float_rn(I) * d.XWf);
+  }
+  const float ea_dn = __shfl_sync(0xffffffffu, e4, 0), eb_dn = __shfl_sync(0xffffffffu, e4, 1);
+  const float ea_up = __shfl_sync(0xffffffffu, e4, 2), eb_up = __shfl_sync(0xffffffffu, e4, 3);
+  float wS = 0.f;
+  if (lane < 16) {
+    const int S = lane, s0 = S & 1, s1 = (S >> 1) & 1, s2 = (S >> 2) & 1, s3 = (S >> 3) & 1;
+    if (s0 + s1 == s2 + s3) {
+      float v = (s0 == s2) ? d.dvwf[s0 | (s1 << 1)] : d.tkinkf;
+      auto f = [](int sg, float e) { return sg ? -e : 2.0f + e; };
+      if (!La.single) v *= f(La.far_dn ^ s0, ea_dn);
+      if (!Lb.single) v *= f(Lb.far_dn ^ s1, eb_dn);
+      v *= La.single ? f(s2 ^ s0, ea_up) : f(s2 ^ La.far_up, ea_up);
+      v *= Lb.single ? f(s3 ^ s1, eb_up) : f(s3 ^ Lb.far_up, eb_up);
+      wS = v;
+    }
+  }
+  float c = wS;  // inclusive running sums over the states
+  for (int o = 1; o < 16; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, c, o);
+    if (lane >= o) c += t;
+  }
+  const float tot = __shfl_sync(0xffffffffu, c, 15);
+  if (!(tot > 0x1p-100f)) return -1;
+  const float r = __ull2float_rn(w >> 11) * 0x1p-53f;
+  const float fr = c / tot;
+  const bool pos = lane < 16 && wS > 0.f;
+  const bool near = (pos && fabsf(r - fr) <= 0x1p-12f) || r <= 0x1p-12f;
+  if (__any_sync(0xffffffffu, near)) return -1;
+  const unsigned hit = __ballot_sync(0xffffffffu, pos && r < fr);
+  return hit ? __ffs(int(hit)) - 1 : -1;
+}
 __device__ __forceinline__ double em1_of(uint64_t I, double XW) {
   return expm1_det(__dmul_rn(-2.0, __dmul_rn(__ull2double_rn(I), XW)));
 }
@@ -228,9 +279,14 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
     any = true;
     Legs La, Lb;
     if (!site_legs(d, KA, nA, pv, &La) || !site_legs(d, KB, nB, pv, &Lb)) return PMWA_EINVARIANT;
-    // heat-bath over the root states (Eq. 4), one lane per leg factor and one
-    // lane per state; the weights are summed in the fixed order S = 0..15
+    // heat-bath over the root states (Eq. 4): decided in binary32 when the
+    // uniform lies clear of every boundary, else in binary64 with one lane
+    // per leg factor and one lane per state and the weights summed in the
+    // fixed order S = 0..15
     const int lane = threadIdx.x & 31;
+    const uint64_t wu = st.word();
+    int Sn = heat_bath_f32(d, La, Lb, wu, lane);
+    if (Sn < 0) {
     double e4 = 0.0;
     if (lane < 4) {
       uint64_t I;
@@ -267,9 +323,10 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
       if (lane == S) cumS = tot;
     }
     const int lastS = 31 - __clz(int(pos));
-    const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
+    const double u = __dmul_rn(__dmul_rn(__ull2double_rn(wu >> 11), 0x1p-53), tot);
     const unsigned hit = __ballot_sync(0xffffffffu, lane < 16 && u < cumS);
-    const int Sn = hit ? (__ffs(int(hit)) - 1) : lastS;
+    Sn = hit ? (__ffs(int(hit)) - 1) : lastS;
+    }
     const int s0 = Sn & 1, s1 = (Sn >> 1) & 1, s2 = (Sn >> 2) & 1, s3 = (Sn >> 3) & 1;
     {
       const int ka = slot_find(KA, nA, pv), kb = slot_find(KB, nB, pv);

@@ -86,6 +86,34 @@ struct Stream {
   }
 };
 
+// The same word sequence for a warp that runs one scalar chain (every lane
+// calls word() with the same state, all lanes active): lane j holds block
+// base + j of a 32-block window and each word is fetched by two shuffles,
+// so the warp evaluates Philox once per 64 words instead of once per 2.
+struct WarpStream {
+  uint32_t k0, k1, unit, c2, sweep;
+  uint64_t pos;
+  uint64_t base;  // first block of the window the lanes hold
+  P4 mine;        // block base + lane
+  __device__ void init(uint32_t key0, uint32_t key1, uint32_t u, uint32_t cc2, uint32_t sw) {
+    k0 = key0; k1 = key1; unit = u; c2 = cc2; sweep = sw; pos = 0;
+    base = ~0ull - 63;  // (b - base = b + 64 >= 32: the first word fills the window)
+  }
+  __device__ uint64_t word() {
+    const uint64_t b = pos >> 1;
+    if (b - base >= 32) {
+      base = b & ~31ull;
+      mine = philox(uint32_t(base) + (threadIdx.x & 31), unit, c2, sweep, k0, k1);
+    }
+    const int src = int(b - base);
+    const bool odd = pos & 1;
+    const uint32_t lo = __shfl_sync(0xffffffffu, odd ? mine.z : mine.x, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, odd ? mine.w : mine.y, src);
+    ++pos;
+    return uint64_t(lo) | (uint64_t(hi) << 32);
+  }
+};
+
 __device__ __forceinline__ uint32_t c2_word(uint32_t phase, uint32_t pass, uint32_t replica) {
   return phase | (pass << 4) | (replica << 16);
 }
@@ -242,7 +270,8 @@ __device__ __forceinline__ uint64_t zfix_add(uint64_t a, uint64_t b) { return (a
 // product (u XF[i]) >> 53; accept when u < K[i]; strip 0 past R restarts at
 // R + new deviate; else a binary64 wedge test y < e^-x with a second word.
 // <= z.zcap (64) words.
-__device__ inline uint64_t zig_exp(const ZigTab& z, Stream& s, int* bad) {
+template <class St>
+__device__ inline uint64_t zig_exp(const ZigTab& z, St& s, int* bad) {
   uint64_t acc = 0;
   for (int tries = 0; tries < z.zcap; ++tries) {
     const uint64_t w = s.word();
@@ -295,8 +324,8 @@ __device__ __forceinline__ uint64_t grid_gap(uint64_t Ef, GridScale S) {
 // (M <= SWI) the proposal is 1 + count, kept with probability 1/n when n is
 // odd, the extra worm uniform on the interval (a clash rejects).  Returns the
 // count (offsets sorted in offs[0..n)), or -1 with *bad set.
-template <int MAXN>
-__device__ int sample_worms(const ZigTab& z, Stream& s, uint64_t M, int sigma, GridScale SW, uint64_t SWI,
+template <int MAXN, class St>
+__device__ int sample_worms(const ZigTab& z, St& s, uint64_t M, int sigma, GridScale SW, uint64_t SWI,
                             uint64_t* offs, int* bad) {
   if (M == 0) { if (sigma) { *bad = PMWA_EINVARIANT; return -1; } return 0; }
   for (int tries = 0; tries < z.wtries; ++tries) {

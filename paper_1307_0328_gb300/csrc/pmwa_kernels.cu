@@ -152,7 +152,7 @@ __device__ __forceinline__ int warp_find_tag(const uint64_t* K, int n, int from,
 // erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
 // and draw new ones with end states p (above lo) and q (below hi); K holds
 // n events (capacity cap).
-__device__ __noinline__ int regen_interval(const Dev& d, const ZigTab& z, Stream& st, uint64_t* K, int& n,
+__device__ __noinline__ int regen_interval(const Dev& d, const ZigTab& z, WarpStream& st, uint64_t* K, int& n,
                               uint64_t lo, uint64_t hi, int p, int q) {
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
   n = warp_compact(K, n, [&](uint64_t key) {  // the worms of the interval
@@ -265,7 +265,7 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
                                     uint64_t* KB, int& nB, int& baseB, const ZigTab& Z) {
   const int tag = bond_tag(d, a, dir);
   const int bid = 2 * a + dir;
-  Stream st;
+  WarpStream st;
   st.init(d.key0, d.key1, uint32_t(bid), c2_word(dir ? kBy : kBx, 0, d.replica), d.sweep);
   int rc = PMWA_OK;
   // Step 2: the bond's vertices in time order (worms move, vertices do not)
@@ -364,7 +364,7 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
     if (gone != removed) return PMWA_EINVARIANT;
   }
   if (!d.has_vertices) return PMWA_OK;
-  Stream sv;
+  WarpStream sv;
   sv.init(d.key0, d.key1, uint32_t(bid), c2_word(kVertex, 0, d.replica), d.sweep);
   uint64_t pos = 0;
   bool first = true;
@@ -503,7 +503,7 @@ __device__ __forceinline__ void tb_delim(const Dev& d, const uint64_t* K, int n,
 }
 
 __device__ int temporal_site(const Dev& d, int s, uint64_t* K, int& n, int& base, const ZigTab& Z) {
-  Stream st;
+  WarpStream st;
   st.init(d.key0, d.key1, uint32_t(s), c2_word(kTemporal, 0, d.replica), d.sweep);
   for (int k = 0; k < d.ntau; ++k) {
     const uint64_t B = tb_pk(d, k);

@@ -271,28 +271,33 @@ __device__ int move_desc(const Tile& T, const WormRec& w, int q, int r, uint64_t
   return PMWA_OK;
 }
 
-// A Step-5 move of worm w = T.W[seg[r]] that reaches the vertex of its
-// descriptor (d0 != kFpTurn); seg[0..n) are the worms of its sub-block, the
-// only ones that can sit on the sub-block's sites.  The worm reverses at
-// another worm ahead of it in its interval; otherwise it enters the vertex v
-// with probability L_min / L_i (word0 >> 32 against the exact ratio), leaves
-// by leg j (threshold table, low half of word0) and lands on a uniform worm
-// grid point of leg j (mulhi of word1) heading away from v.  Leg l of v runs
-// from v to the nearest event on its site and side (another vertex leg or
-// worm, the moving worm excluded; the whole circle if none).  Legs are
-// unique to their sites, so a worm's interval is named by its leg alone.
-__device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t d0, uint64_t d1, const uint16_t* seg, int n, int r,
-                           uint64_t w0, uint64_t w1) {
-  const uint64_t key = w.key;
+// A Step-5 move of worm w = T.W[seg[r]] (key, local site li and leg L as
+// read at the start of the pass: only its own move changes them) that
+// reaches the vertex of its descriptor (d0 != kFpTurn); seg[0..n) are the
+// worms of its sub-block, the only ones that can sit on the sub-block's
+// sites.  The worm reverses at another worm ahead of it in its interval;
+// otherwise it enters the vertex v with probability L_min / L_i (word0 >> 32
+// against the exact ratio), leaves by leg j (threshold table, low half of
+// word0) and lands on a uniform worm grid point of leg j (mulhi of word1)
+// heading away from v.  Leg l of v runs from v to the nearest event on its
+// site and side (another vertex leg or worm, the moving worm excluded; the
+// whole circle if none).  Legs are unique to their sites, so a worm's
+// interval is named by its leg alone.  The legs and worm counts the move
+// reads are loaded together up front; the vertex's two legs are updated in
+// registers and stored once.
+__device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t key, int li, int L, uint64_t d0, uint64_t d1,
+                           const uint16_t* seg, int n, int r, uint64_t w0, uint64_t w1) {
   const bool up = kdir(key);
-  const int li = w.site, L = w.leg;
   const int ia_dn = int(d0 & 0xffff), ia = int((d0 >> 16) & 0xffff);
   const int ib_dn = int((d0 >> 32) & 0xffff), ib = int(d0 >> 48);
   const int ia_up = int(d1 & 0xffff), ib_up = int((d1 >> 16) & 0xffff), pl = int((d1 >> 32) & 0xffff);
   const bool li_a = (L == ia || L == ia_dn);  // the worm sits on the bond's lower site
-  const uint64_t pL = kpk(T.leg[L]);
+  const uint64_t kL = T.leg[L], va = T.leg[ia], vb = T.leg[ib];
+  const uint64_t kad = T.leg[ia_dn], kbd = T.leg[ib_dn], kau = T.leg[ia_up], kbu = T.leg[ib_up];
+  const int cL = T.wcnt[L], cia = T.wcnt[ia], cib = T.wcnt[ib], ciad = T.wcnt[ia_dn], cibd = T.wcnt[ib_dn];
+  const uint64_t pL = kpk(kL);
   const uint64_t my = (kpk(key) - pL) & kMask62;
-  if (T.wcnt[L] > 1) {  // other worms share the interval: is one of them ahead?
+  if (cL > 1) {  // other worms share the interval: is one of them ahead?
     for (int k = 0; k < n; ++k) {
       const WormRec& o = T.W[seg[k]];
       if (k == r || int(o.leg) != L) continue;
@@ -300,17 +305,17 @@ __device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t d0, uint64_t d1, 
       if (up ? off > my : off < my) { w.key = key ^ 2u; return PMWA_OK; }
     }
   }
-  const uint64_t pv = kpk(T.leg[ia]);
+  const uint64_t pv = kpk(va);
   const int al = li_a ? li : pl, bl = li_a ? pl : li;
-  const uint64_t pa_dn = kpk(T.leg[ia_dn]), pb_dn = kpk(T.leg[ib_dn]);
+  const uint64_t pa_dn = kpk(kad), pb_dn = kpk(kbd);
   // offsets from v up to the nearest object above, and from the lower leg up
   // to the highest worm of the interval below v
-  uint64_t ua = (ia_up == ia) ? kTwo62 : ((kpk(T.leg[ia_up]) - pv) & kMask62);
-  uint64_t ub = (ib_up == ib) ? kTwo62 : ((kpk(T.leg[ib_up]) - pv) & kMask62);
+  uint64_t ua = (ia_up == ia) ? kTwo62 : ((kpk(kau) - pv) & kMask62);
+  uint64_t ub = (ib_up == ib) ? kTwo62 : ((kpk(kbu) - pv) & kMask62);
   uint64_t da = 0, db = 0;
   bool fa = false, fb = false;
   // worms (other than this one) in the four intervals around v?
-  int others = T.wcnt[ia] + T.wcnt[ib] + (ia_dn != ia ? T.wcnt[ia_dn] : 0) + (ib_dn != ib ? T.wcnt[ib_dn] : 0) - 1;
+  int others = cia + cib + (ia_dn != ia ? ciad : 0) + (ib_dn != ib ? cibd : 0) - 1;
   for (int k = 0; k < n && others > 0; ++k) {
     if (k == r) continue;
     const WormRec& o = T.W[seg[k]];
@@ -335,15 +340,18 @@ __device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t d0, uint64_t d1, 
   const uint64_t ph = __umul64hi(z1, Li), plo = z1 * Li;
   const uint64_t qh = Lmin >> 32, ql = Lmin << 32;
   if (!(ph < qh || (ph == qh && plo < ql))) { w.key = key ^ 2u; return PMWA_OK; }
-  const uint64_t va = T.leg[ia], vb = T.leg[ib];
   const int S = kbl(va) | (kbl(vb) << 1) | (kab(va) << 2) | (kab(vb) << 3);
   const uint64_t* th = T.th + (S * 4 + i) * 4;
-  int j = 0;
-  while (j < 3 && !(z0 < th[j])) ++j;
-  T.leg[(i & 1) ? ib : ia] ^= (i < 2) ? 2u : 1u;
-  T.leg[(j & 1) ? ib : ia] ^= (j < 2) ? 2u : 1u;
+  const uint64_t t0 = th[0], t1 = th[1], t2 = th[2];
+  const int j = (z0 < t0) ? 0 : (z0 < t1) ? 1 : (z0 < t2) ? 2 : 3;
+  // the worm leaves leg i and takes leg j: flip their states
+  uint64_t na = va, nb = vb;
+  if (i & 1) nb ^= (i < 2) ? 2u : 1u; else na ^= (i < 2) ? 2u : 1u;
+  if (j & 1) nb ^= (j < 2) ? 2u : 1u; else na ^= (j < 2) ? 2u : 1u;
+  T.leg[ia] = na;
+  T.leg[ib] = nb;
   const int ix = (j & 1) ? ib : ia;
-  const uint64_t vx = T.leg[ix];
+  const uint64_t vx = (j & 1) ? nb : na;
   const uint64_t Lj = (j == 0) ? L0 : (j == 1) ? L1 : (j == 2) ? L2 : L3;
   const uint64_t o = __umul64hi(w1, Lj);
   const int nl = (j >= 2) ? ix : ((j & 1) ? ib_dn : ia_dn);
@@ -364,7 +372,7 @@ __device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q
   const int rc = move_desc(T, w, q, r, d0, d1);
   if (rc) return rc;
   if (d0 == kFpTurn) { w.key ^= 2u; return PMWA_OK; }
-  return tile_move_d(T, w, d0, d1, seg, n, r, w0, w1);
+  return tile_move_d(T, w, w.key, w.site, w.leg, d0, d1, seg, n, r, w0, w1);
 }
 
 // per-phase cycle counters (profiling only): thread 0 adds the cycles since
@@ -408,20 +416,20 @@ __device__ __forceinline__ bool fp_meet(uint64_t a, uint64_t b) {
 
 // The moves of one pass (all threads).  On entry the grouped order idx[]
 // (position p = fill[u] + r holds the r-th worm of group u), each position's
-// move descriptor in rw[2p], rw[2p + 1] and each worm's group in xr are in
-// place.  First each worm's wait mask goes to lab: bit i (i < kNear) = wait
-// for position p - 1 - i, bits kNear.. = the group, bit 63 = also wait for
-// every position of the group more than kNear before it.  Then rounds until
-// every worm has moved, each move drawing Philox block r of stream
-// (domain * groups + u, c2) and recording its round in xr.  Ends with a
-// barrier.
+// move descriptor in rw[2p], rw[2p + 1], each worm's group in lab and
+// kPending in xr are in place.  First each worm's wait mask goes to lab:
+// bit i (i < kNear) = wait for position p - 1 - i, bits kNear.. = the group,
+// bit 63 = also wait for every position of the group more than kNear before
+// it.  Then rounds until every worm has moved, each move drawing Philox
+// block r of stream (domain * groups + u, c2) and recording its round in
+// xr.  Ends with a barrier.
 __device__ void pass_rounds(const Tile& T, int dom, int nw, uint32_t c2) {
   const Dev& d = *T.d;
   const int tid = threadIdx.x, NT = blockDim.x;
   for (int p = tid; p < nw; p += NT) {
     WormRec& w = T.W[T.idx[p]];
     const uint64_t f = T.rw[2 * p];
-    uint64_t m = uint64_t(w.xr) << kNear;
+    uint64_t m = w.lab << kNear;
     if (f != kFpTurn) {
       const int r = int(T.rw[2 * p + 1] >> 48);
       for (int i = 0; i < r; ++i) {
@@ -431,8 +439,6 @@ __device__ void pass_rounds(const Tile& T, int dom, int nw, uint32_t c2) {
     }
     w.lab = m;
   }
-  __syncthreads();
-  for (int p = tid; p < nw; p += NT) T.W[T.idx[p]].xr = kPending;
   __syncthreads();
   for (int round = 0;; ++round) {
     int pending = 0;
@@ -457,7 +463,7 @@ __device__ void pass_rounds(const Tile& T, int dom, int nw, uint32_t c2) {
         continue;
       }
       const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
-      const int rc = tile_move_d(T, w, d0, d1, T.idx + (p - r), T.fill[u + 1] - T.fill[u], r,
+      const int rc = tile_move_d(T, w, w.key, w.site, w.leg, d0, d1, T.idx + (p - r), T.fill[u + 1] - T.fill[u], r,
                                  uint64_t(b.x) | (uint64_t(b.y) << 32), uint64_t(b.z) | (uint64_t(b.w) << 32));
       if (rc) tile_fail(T.misc, rc, 5);
       w.xr = uint16_t(round);
@@ -556,8 +562,8 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
   if (lane == 31) T.fill[n] = v;
 }
 
-// The grouping of rank_pass by the whole block, for nw <= blockDim.x worms
-// (called by every thread; contains one block barrier).  Warp c ranks the
+// The grouping of rank_pass by the whole block, for nw <= blockDim.x worms,
+// in two halves around a block barrier (called by every thread).  Warp c ranks the
 // 32 worms of chunk c of the label order among themselves (__match_any_sync)
 // and its group leaders record the chunk's count of each sub-block in
 // cnt[c][u], stamped with pass_stamp(pass) (an entry with another stamp
@@ -570,28 +576,33 @@ __device__ void rank_pass(const Tile& T, int nw, int q, int lane) {
 // out as rank_pass makes it (after a barrier); bkt[] is scratch.
 __device__ __forceinline__ int pass_stamp(int pass) { return ((pass % 255) + 1) << 8; }
 
-__device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_out, int& r_out) {
+// (before the barrier: the chunk ranks and counts)
+__device__ void rank_chunk(const Tile& T, int nw, int q, int pass, int& u, int& r) {
   const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int W = (nw + 31) >> 5, n = T.ngrp;
   const int stamp = pass_stamp(pass);
-  const int k = tid;
-  int u = -1, r = 0;
+  u = -1;
+  r = 0;
   if (c < W) {  // warp-uniform
-    u = (k < nw) ? worm_group(T, T.W[T.ord[k]], q) : -1;
+    u = (tid < nw) ? worm_group(T, T.W[T.ord[tid]], q) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     r = __popc(peers & lt);
     if (u >= 0 && (peers & lt) == 0) T.cnt[c * n + u] = uint16_t(stamp | __popc(peers));
   }
-  __syncthreads();
+}
+
+// (after the barrier: the earlier chunks' counts, and fill[])
+__device__ void rank_finish(const Tile& T, int nw, int pass, int u, int& r) {
+  const int tid = threadIdx.x, c = tid >> 5, lane = tid & 31;
+  const int W = (nw + 31) >> 5, n = T.ngrp;
+  const int stamp = pass_stamp(pass);
   if (c > 0 && u >= 0) {
     for (int c2 = 0; c2 < c; ++c2) {
       const int v = T.cnt[c2 * n + u];
       if ((v & ~0xff) == stamp) r += v & 0xff;
     }
   }
-  u_out = u;
-  r_out = r;
   const int nwarps = int(blockDim.x) >> 5;
   if (c == (W < nwarps ? nwarps - 1 : 0)) {
     const int chunk = (n + 31) / 32;
@@ -619,6 +630,98 @@ __device__ void rank_pass_block(const Tile& T, int nw, int q, int pass, int& u_o
     }
     if (lane == 31) T.fill[n] = v;
   }
+}
+
+// One pass when every worm has a thread (32 < nw <= blockDim.x; called by
+// every thread, ends with a barrier).  Thread k holds the k-th worm of the
+// label order from its grouping to its move: the worm's key, site and leg,
+// its move descriptor, its rank r in its group u, its wait mask and its
+// Philox block r of stream (domain * groups + u, c2) stay in registers.
+// Other threads read only the descriptor's intervals (rw[at], for the wait
+// masks) and the round of each position's move (wsb[at], kPending until it
+// has moved), at its grouped position at = fill[u] + r.  The wait mask:
+// bit i < 63 = wait for position at - 1 - i; bit 63 = also wait for every
+// position of the group at least 64 before.  tclk: the phase clock (set-up
+// to counter 5, moves to counter 6).
+__device__ void pass_fast(const Tile& T, int dom, int nw, int q, int pass, uint32_t c2, long long& tclk) {
+  const Dev& d = *T.d;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  if (pass > 0 && pass % 255 == 0) {  // the stamps start over: no entry may carry one
+    for (int i = tid; i < (NT >> 5) * T.ngrp; i += NT) T.cnt[i] = 0;
+    __syncthreads();
+  }
+  int u, r;
+  rank_chunk(T, nw, q, pass, u, r);
+  const bool act = u >= 0;
+  int wi = 0, li = 0, L = 0, rc = PMWA_OK;
+  uint64_t key = 0, d0 = kFpTurn, d1 = 0;
+  if (act) {
+    wi = T.ord[tid];
+    const WormRec& w = T.W[wi];
+    key = w.key;
+    li = w.site;
+    L = w.leg;
+    rc = move_desc(T, w, q, 0, d0, d1);
+  }
+  __syncthreads();
+  rank_finish(T, nw, pass, u, r);
+  __syncthreads();
+  int at = 0, lo = 0, n = 0;
+  uint64_t w0 = 0, w1 = 0;
+  if (act) {
+    lo = T.fill[u];
+    n = T.fill[u + 1] - lo;
+    at = lo + r;
+    T.idx[at] = uint16_t(wi);
+    T.rw[at] = d0;
+    T.wsb[at] = kPending;
+    if (rc) tile_fail(T.misc, rc, 5);
+    if (d0 != kFpTurn) {
+      const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2, d.sweep, d.key0, d.key1);
+      w0 = uint64_t(b.x) | (uint64_t(b.y) << 32);
+      w1 = uint64_t(b.z) | (uint64_t(b.w) << 32);
+    }
+  }
+  __syncthreads();
+  phase_tick(d, 5, tclk);
+  uint64_t m = 0;
+  if (act && d0 != kFpTurn)
+    for (int i = 0; i < r; ++i) {
+      const uint64_t g = T.rw[at - 1 - i];
+      if (g != kFpTurn && fp_meet(d0, g)) m |= (i < 63) ? (1ull << i) : (1ull << 63);
+    }
+  bool done = !act;
+  for (int round = 0;; ++round) {
+    int pending = 0;
+    if (!done) {
+      bool ready = true;
+      for (uint64_t b = m & ~(1ull << 63); b && ready; b &= b - 1) ready = T.wsb[at - __ffsll((long long)b)] < round;
+      if (ready && (m >> 63))
+        for (int j = lo; j < at - 63 && ready; ++j) ready = T.wsb[j] < round;
+      if (ready) {
+        WormRec& w = T.W[wi];
+        if (d0 == kFpTurn) {
+          w.key = key ^ 2u;
+        } else {
+          const int rc2 = tile_move_d(T, w, key, li, L, d0, d1, T.idx + lo, n, r, w0, w1);
+          if (rc2) tile_fail(T.misc, rc2, 5);
+        }
+        T.wsb[at] = uint16_t(round);
+        done = true;
+      } else {
+        pending = 1;
+      }
+    }
+    if (!__syncthreads_or(pending)) {
+      if (d.phase_cycles && tid == 0) atomicAdd(d.phase_cycles + 7, (unsigned long long)(round + 1));
+      break;
+    }
+    if (round >= nw) {  // (each round moves the first waiting worm of every group: never taken)
+      if (tid == 0) tile_fail(T.misc, PMWA_EINVARIANT, 7);
+      break;
+    }
+  }
+  phase_tick(d, 6, tclk);
 }
 
 // All N_cycle passes of a domain holding nw <= 32 worms, run by one warp
@@ -956,24 +1059,12 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
       for (int pass = 0; pass < (nw > 32 ? d.n_cycle : 0); ++pass) {  // no worms: nothing moves
         const int q = pass & 3;
         const uint32_t c2 = c2_word(kScatter, uint32_t(pass), d.replica);
-        if (nw <= NT) {
-          // all warps, one chunk each
-          if (pass > 0 && pass % 255 == 0) {  // the stamps start over: no entry may carry one
-            for (int i = tid; i < (NT >> 5) * T.ngrp; i += NT) T.cnt[i] = 0;
-            __syncthreads();
-          }
-          int u, r;
-          rank_pass_block(T, nw, q, pass, u, r);
-          __syncthreads();
-          if (u >= 0) {
-            const int at = T.fill[u] + r;
-            T.idx[at] = T.ord[tid];
-            WormRec& w = T.W[T.ord[tid]];
-            const int rc = move_desc(T, w, q, r, T.rw[2 * at], T.rw[2 * at + 1]);
-            if (rc) tile_fail(misc, rc, 5);
-            w.xr = uint16_t(u);
-          }
-        } else {
+        if (nw <= NT) {  // all warps, one chunk each, one worm a thread
+          pass_fast(T, dom, nw, q, pass, c2, tclk);
+          if (misc->err) goto fail;
+          continue;
+        }
+        {
           if (tid < 32) rank_pass(T, nw, q, tid);
           __syncthreads();
           for (int k = tid; k < nw; k += NT) {
@@ -982,7 +1073,8 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
             WormRec& w = T.W[T.ord[k]];
             const int rc = move_desc(T, w, q, r, T.rw[2 * at], T.rw[2 * at + 1]);
             if (rc) tile_fail(misc, rc, 5);
-            w.xr = uint16_t(u);
+            w.lab = uint64_t(u);
+            w.xr = kPending;
           }
         }
         __syncthreads();

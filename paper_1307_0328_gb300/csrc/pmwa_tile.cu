@@ -53,6 +53,13 @@ struct Misc {
 };
 
 __device__ __forceinline__ int cnt_n(uint32_t c) { return int(c & kCntMask); }
+
+// bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global
+// address into L2 (TMA engine; no registers, no completion to wait for)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tcp.async.bulk.prefetch.L2.global [ga], %1;\n\t}"
+               :: "l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ int cnt_base(uint32_t c) { return int(c >> 31); }
 
 __device__ __forceinline__ void tile_fail(Misc* m, int code, int where) {
@@ -804,6 +811,14 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   Misc* misc = T.misc;
 
   long long tclk = clock64();
+  // the domain's current event lists on their way into L2 before the scans
+  // of Step 3 reach them: one bulk prefetch per site of its used slots (a
+  // list starts 64-byte aligned; its length rounded up to 16 bytes stays
+  // within the site's cap, a multiple of 8 keys)
+  for (int li = tid; li < nds; li += NT) {
+    const int s = T.gsite(li), n = cnt_n(d.cntA[s]);
+    if (n) prefetch_l2(d.keyA + size_t(s) * d.cap, uint32_t((n * 8 + 15) & ~15));
+  }
   const ZigTab Z = zig_stage(sm + d.sm_zig, d.zig_cap, d.worm_tries);
   for (int k = tid; k < 256; k += NT) T.th[k] = d.TH[k];
   if (tid == 0) { misc->pool_used = 0; misc->nworms = 0; misc->err = 0; misc->where = 0; }
@@ -914,37 +929,51 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
     const int s = T.gsite(li);
     const uint64_t* KO = T.okeys(li, s);
     const int nO = cnt_n(d.cntA[s]);
-    int lb[4], ci[4] = {0, 0, 0, 0}, cn[4];
+    int lb[4];
     site_bonds(T, li, lb);
-    for (int j = 0; j < 4; ++j) cn[j] = lb[j] >= 0 ? T.bcnt[lb[j]] : 0;
+    // the new legs of the site's four bonds, each run in time order: the run's
+    // next candidate (h) and how many remain (m); the site is the lower site
+    // of bonds 0 and 1 (its state in bit 0 of a candidate) and the upper site
+    // of bonds 2 and 3 (bit 1)
+    const uint64_t* q0 = T.pool + (lb[0] >= 0 ? T.boff[lb[0]] : 0);
+    const uint64_t* q1 = T.pool + (lb[1] >= 0 ? T.boff[lb[1]] : 0);
+    const uint64_t* q2 = T.pool + (lb[2] >= 0 ? T.boff[lb[2]] : 0);
+    const uint64_t* q3 = T.pool + (lb[3] >= 0 ? T.boff[lb[3]] : 0);
+    int m0 = lb[0] >= 0 ? T.bcnt[lb[0]] : 0, m1 = lb[1] >= 0 ? T.bcnt[lb[1]] : 0;
+    int m2 = lb[2] >= 0 ? T.bcnt[lb[2]] : 0, m3 = lb[3] >= 0 ? T.bcnt[lb[3]] : 0;
+    uint64_t h0 = m0 ? q0[0] : 0, h1 = m1 ? q1[0] : 0, h2 = m2 ? q2[0] : 0, h3 = m3 ? q3[0] : 0;
     int io = 0, o = T.off[li];
     // temporal boundaries join the legs as delimiters (tag 6) whose state
     // above and below is the worldline's state there in the current
     // configuration (Step 3 changes no state)
     const int NB = d.ntau > 1 ? d.ntau : 0, base0 = cnt_base(d.cntA[s]);
     int ib = 0;
+    uint64_t tb = NB ? tb_pk(d, 0) : 0;
     for (;;) {
-      while (io < nO && !kept_leg<OTF>(T, li, KO[io])) ++io;
+      uint64_t ko = 0;
+      while (io < nO && !kept_leg<OTF>(T, li, ko = KO[io])) ++io;
       uint64_t best = ~0ull;
       int src = -1;
-      if (io < nO) { best = kpk(KO[io]); src = 4; }
-      for (int j = 0; j < 4; ++j)
-        if (ci[j] < cn[j]) {
-          const uint64_t p = T.pool[T.boff[lb[j]] + ci[j]] >> 2;
-          if (p < best) { best = p; src = j; }
-        }
-      if (ib < NB && tb_pk(d, ib) < best) { best = tb_pk(d, ib); src = 5; }
+      if (io < nO) { best = kpk(ko); src = 4; }
+      if (m0 && (h0 >> 2) < best) { best = h0 >> 2; src = 0; }
+      if (m1 && (h1 >> 2) < best) { best = h1 >> 2; src = 1; }
+      if (m2 && (h2 >> 2) < best) { best = h2 >> 2; src = 2; }
+      if (m3 && (h3 >> 2) < best) { best = h3 >> 2; src = 3; }
+      if (ib < NB && tb < best) { best = tb; src = 5; }
       if (src < 0) break;
       uint64_t key;
-      if (src == 4) key = KO[io++];
-      else if (src == 5) {
-        const uint64_t bst = uint64_t(slot_state(KO, nO, base0, best));
-        key = (best << 2) | (bst << 1) | bst;
-        ++ib;
-      } else {
-        const uint64_t c = T.pool[T.boff[lb[src]] + ci[src]++];
-        const uint64_t st = (c >> (src < 2 ? 0 : 1)) & 1;
-        key = ((c >> 2) << 2) | (st << 1) | st;
+      switch (src) {
+        case 4: key = ko; ++io; break;
+        case 5: {
+          const uint64_t bst = uint64_t(slot_state(KO, nO, base0, best));
+          key = (best << 2) | (bst << 1) | bst;
+          if (++ib < NB) tb = tb_pk(d, ib);
+          break;
+        }
+        case 0: { const uint64_t st = h0 & 1; key = ((h0 >> 2) << 2) | (st << 1) | st; if (--m0) h0 = *++q0; break; }
+        case 1: { const uint64_t st = h1 & 1; key = ((h1 >> 2) << 2) | (st << 1) | st; if (--m1) h1 = *++q1; break; }
+        case 2: { const uint64_t st = (h2 >> 1) & 1; key = ((h2 >> 2) << 2) | (st << 1) | st; if (--m2) h2 = *++q2; break; }
+        default: { const uint64_t st = (h3 >> 1) & 1; key = ((h3 >> 2) << 2) | (st << 1) | st; if (--m3) h3 = *++q3; break; }
       }
       T.leg[o++] = key;
     }

@@ -372,16 +372,6 @@ __device__ int tile_move_d(const Tile& T, WormRec& w, uint64_t key, int li, int 
   return PMWA_OK;
 }
 
-// One Step-5 move of worm seg[r] in pass pattern q, from scratch.
-__device__ int tile_move(const Tile& T, const uint16_t* seg, int n, int r, int q, uint64_t w0, uint64_t w1) {
-  WormRec& w = T.W[seg[r]];
-  uint64_t d0, d1;
-  const int rc = move_desc(T, w, q, r, d0, d1);
-  if (rc) return rc;
-  if (d0 == kFpTurn) { w.key ^= 2u; return PMWA_OK; }
-  return tile_move_d(T, w, w.key, w.site, w.leg, d0, d1, seg, n, r, w0, w1);
-}
-
 // per-phase cycle counters (profiling only): thread 0 adds the cycles since
 // the last tick to counter k
 __device__ __forceinline__ void phase_tick(const Dev& d, int k, long long& t) {
@@ -733,11 +723,14 @@ __device__ void pass_fast(const Tile& T, int dom, int nw, int q, int pass, uint3
 
 // All N_cycle passes of a domain holding nw <= 32 worms, run by one warp
 // (lane = threadIdx.x < 32) with no block barrier.  Lane k holds the k-th
-// worm in label order; __match_any_sync over the sub-blocks gives each worm
-// its rank r inside its sub-block, and round r moves the r-th worm of every
-// sub-block at once (sub-blocks share no sites), so every sub-block's worms
-// move in label order with the r-th move drawing Philox block r, as in the
-// block-wide passes.  Returns a status (the same for all lanes).
+// worm in label order; __match_any_sync over the groups gives each worm its
+// rank r in its group, and the r-th move of a group draws Philox block r,
+// as in the block-wide passes.  Each lane forms its move's descriptor (the
+// intervals go through rw[lane]); a lane waits for the lanes of its group of
+// lower rank whose intervals meet its own, and rounds move every lane whose
+// waits are over (at most 32 rounds: the first waiting lane of each group
+// waits for nobody), which gives each group's moves made one by one in rank
+// order.  Returns a status (the same for all lanes).
 __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
   const Dev& d = *T.d;
   const unsigned lt = (1u << lane) - 1u;
@@ -748,23 +741,51 @@ __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
     const int u = act ? worm_group(T, T.W[w], q) : 0x7fffffff;
     const unsigned peers = __match_any_sync(0xffffffffu, u);
     const int r = __popc(peers & lt), n = __popc(peers);
-    int less = 0;  // worms of sub-blocks numbered below u: the start of u's group
+    int less = 0;  // worms of groups numbered below u: the start of u's group
     for (int j = 0; j < 32; ++j) less += (__shfl_sync(0xffffffffu, u, j) < u) ? 1 : 0;
-    if (act) T.idx[less + r] = uint16_t(w);
-    const int maxr = __reduce_max_sync(0xffffffffu, act ? r : 0);
-    P4 b{0u, 0u, 0u, 0u};
-    if (act) b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2_word(kScatter, uint32_t(pass), d.replica),
-                        d.sweep, d.key0, d.key1);
+    int rc = PMWA_OK, li = 0, L = 0;
+    uint64_t key = 0, d0 = kFpTurn, d1 = 0, w0 = 0, w1 = 0;
+    if (act) {
+      T.idx[less + r] = uint16_t(w);
+      const WormRec& wr = T.W[w];
+      key = wr.key;
+      li = wr.site;
+      L = wr.leg;
+      rc = move_desc(T, wr, q, r, d0, d1);
+      if (d0 != kFpTurn) {
+        const P4 b = philox(uint32_t(r), uint32_t(dom * T.ngrp + u), c2_word(kScatter, uint32_t(pass), d.replica),
+                            d.sweep, d.key0, d.key1);
+        w0 = uint64_t(b.x) | (uint64_t(b.y) << 32);
+        w1 = uint64_t(b.z) | (uint64_t(b.w) << 32);
+      }
+      T.rw[lane] = d0;
+    }
     __syncwarp();
-    int rc = PMWA_OK;
-    for (int rr = 0; rr <= maxr; ++rr) {
-      if (act && r == rr)
-        rc = tile_move(T, T.idx + less, n, r, q, uint64_t(b.x) | (uint64_t(b.y) << 32),
-                       uint64_t(b.z) | (uint64_t(b.w) << 32));
+    unsigned wait = 0;  // lanes this move waits for
+    if (act && d0 != kFpTurn)
+      for (unsigned m = peers & lt; m; m &= m - 1) {
+        const int j = __ffs(int(m)) - 1;
+        const uint64_t g = T.rw[j];
+        if (g != kFpTurn && fp_meet(d0, g)) wait |= 1u << j;
+      }
+    bool moved = !act;
+    unsigned done = __ballot_sync(0xffffffffu, moved);
+    while (done != 0xffffffffu) {
+      if (!moved && (wait & ~done) == 0) {
+        WormRec& wr = T.W[w];
+        if (d0 == kFpTurn) {
+          wr.key = key ^ 2u;
+        } else if (rc == PMWA_OK) {
+          rc = tile_move_d(T, wr, key, li, L, d0, d1, T.idx + less, n, r, w0, w1);
+        }
+        moved = true;
+      }
       __syncwarp();
+      done = __ballot_sync(0xffffffffu, moved);
     }
     const unsigned bad = __ballot_sync(0xffffffffu, rc != PMWA_OK);
     if (bad) return __shfl_sync(0xffffffffu, rc, __ffs(int(bad)) - 1);
+    __syncwarp();
   }
   return PMWA_OK;
 }

@@ -369,7 +369,13 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
         reps = [dict(reps0[i], n_cycle=ncs[i]) for i in range(len(reps0))]
         batch = timed(reps)
     ms_b = batch.last_ms()
-    nv_b = sum(float(batch.rows(i)["n_v"].sum()) for i in range(batch.n))
+    rows_b = [batch.rows(i) for i in range(batch.n)]
+    nv_b = sum(float(r["n_v"].sum()) for r in rows_b)
+    # the scope table's bytes of every instance's sweeps (as for k_tile) over
+    # the whole batched time, boundary steps and all launch groups included
+    alg_b = sum(tile_bytes(float(r["n_v"].sum()), float(r["n_w"].sum()), p["dom_x"]) for r, p in zip(rows_b, reps))
+    peak, which = peaks()
+    gbs_b = alg_b / (ms_b / 1000.0) / 1e9
     footprint = batch.arena.numel() / 1e9
     batch.close()
     # plain: each instance alone, its own launches, from the same
@@ -394,6 +400,13 @@ def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
                plain_value=nv_p / (ms_p / 1000.0), plain_ms_per_step=ms_p / steps,
                speedup=(nv_b / ms_b) / (nv_p / ms_p), vertices_per_sweep=nv_b / steps,
                n_cycle_mean=float(sum(ncs)) / len(ncs), footprint_gb=footprint,
+               roofline=dict(bound="hbm", kernel="batched sweep (all launch groups, boundary steps included)",
+                             achieved=gbs_b, peak=peak, unit="GB/s", frac=gbs_b / peak,
+                             alg_bytes_per_sweep=alg_b / steps,
+                             byte_model="64 B per vertex + 16 B per worm + 32 B per vertex / domain width, "
+                                        "summed over the instances",
+                             peak_source=(which + " MEASURED_PEAKS.json hbm_gbs") if which == "measured"
+                             else "fallback 6.8 TB/s"),
                leg_hints=hinted, mean_domain_sites=sum(p["dom_x"] * p["dom_y"] for p in reps) / len(reps))
     batch.close()
     return out

@@ -511,13 +511,28 @@ __device__ int temporal_site(const Dev& d, int s, uint64_t* K, int& n, int& base
     int p, q;
     tb_delim(d, K, n, base, k, false, &lo, &p);
     tb_delim(d, K, n, base, k, true, &hi, &q);
-    const double e1 = em1_of(wpts(B, hi), d.XW), e2 = em1_of(wpts(lo, B), d.XW);
-    const double w0 = __dmul_rn(fsig(q, e1), fsig(p, e2));
-    const double w1 = __dmul_rn(fsig(q ^ 1, e1), fsig(1 ^ p, e2));
-    const double tot = __dadd_rn(w0, w1);
-    if (!(tot > 0.0)) return PMWA_EINVARIANT;
-    const double u = __dmul_rn(__dmul_rn(__ull2double_rn(st.word() >> 11), 0x1p-53), tot);
-    const int sn = (u < w0) ? 0 : 1;
+    const uint64_t I1 = wpts(B, hi), I2 = wpts(lo, B);
+    const uint64_t wu = st.word();
+    // decided in binary32 when the uniform lies more than 2^-12 from the
+    // fraction w0 / (w0 + w1) (two leg factors: the binary32 fraction is
+    // within 2^-18 of the binary64 one), else in binary64
+    int sn;
+    {
+      auto f = [](int sg, float e) { return sg ? -e : 2.0f + e; };
+      const float g1 = expm1f(-2.0f * __ull2float_rn(I1) * d.XWf), g2 = expm1f(-2.0f * __ull2float_rn(I2) * d.XWf);
+      const float v0 = f(q, g1) * f(p, g2), v1 = f(q ^ 1, g1) * f(1 ^ p, g2);
+      const float r = __ull2float_rn(wu >> 11) * 0x1p-53f, fr = v0 / (v0 + v1);
+      sn = (v0 + v1 > 0x1p-100f && fabsf(r - fr) > 0x1p-12f && r > 0x1p-12f) ? (r < fr ? 0 : 1) : -1;
+    }
+    if (sn < 0) {
+      const double e1 = em1_of(I1, d.XW), e2 = em1_of(I2, d.XW);
+      const double w0 = __dmul_rn(fsig(q, e1), fsig(p, e2));
+      const double w1 = __dmul_rn(fsig(q ^ 1, e1), fsig(1 ^ p, e2));
+      const double tot = __dadd_rn(w0, w1);
+      if (!(tot > 0.0)) return PMWA_EINVARIANT;
+      const double u = __dmul_rn(__dmul_rn(__ull2double_rn(wu >> 11), 0x1p-53), tot);
+      sn = (u < w0) ? 0 : 1;
+    }
     int rc = regen_interval(d, Z, st, K, n, lo, B, p, sn);
     if (!rc) rc = regen_interval(d, Z, st, K, n, B, hi, sn, q);
     if (rc) return rc;

@@ -68,6 +68,7 @@ struct Legs {
   int single;
   uint64_t plo, phi, Idn, Iup;
   int far_dn, far_up;
+  int wdn, wup;  // worms between the vertex and the next vertex leg below / above (0: none in the legs)
 };
 
 // the two legs of the vertex at pv on a site: to the next vertex leg below
@@ -77,10 +78,12 @@ struct Legs {
 __device__ __noinline__ bool site_legs(const Dev& d, const uint64_t* K, int n, uint64_t pv, Legs* L) {
   const int iv = slot_find(K, n, pv);
   if (iv < 0) return false;
-  int jn = iv, jp = iv;
-  for (int k = 0; k < n; ++k) { jn = (jn + 1 == n) ? 0 : jn + 1; if (jn == iv || !kworm(K[jn])) break; }
-  for (int k = 0; k < n; ++k) { jp = (jp == 0) ? n - 1 : jp - 1; if (jp == iv || !kworm(K[jp])) break; }
+  int jn = iv, jp = iv, wu = 0, wd = 0;
+  for (int k = 0; k < n; ++k) { jn = (jn + 1 == n) ? 0 : jn + 1; if (jn == iv || !kworm(K[jn])) break; ++wu; }
+  for (int k = 0; k < n; ++k) { jp = (jp == 0) ? n - 1 : jp - 1; if (jp == iv || !kworm(K[jp])) break; ++wd; }
   L->single = (jn == iv);
+  L->wup = wu;
+  L->wdn = wd;
   if (d.ntau > 1) {
     const uint64_t bu = tb_pk(d, tb_above(d, pv)), bd = tb_pk(d, tb_below(d, pv));
     if (L->single || up_dist(pv, bu) < up_dist(pv, kpk(K[jn]))) { L->phi = bu; L->far_up = slot_state(K, n, 0, bu); }
@@ -149,17 +152,18 @@ __device__ __forceinline__ int warp_find_tag(const uint64_t* K, int n, int from,
   return n;
 }
 
-// erase the worms strictly inside (lo, hi) going up (lo == hi: all of them)
-// and draw new ones with end states p (above lo) and q (below hi); K holds
-// n events (capacity cap).
+// erase the worms strictly inside (lo, hi) going up (lo == hi: all of them;
+// erase false: the caller knows there are none) and draw new ones with end
+// states p (above lo) and q (below hi); K holds n events (capacity cap).
 __device__ __noinline__ int regen_interval(const Dev& d, const ZigTab& z, WarpStream& st, uint64_t* K, int& n,
-                              uint64_t lo, uint64_t hi, int p, int q) {
+                              uint64_t lo, uint64_t hi, int p, int q, bool erase) {
   const uint64_t span = (hi > lo) ? hi - lo : hi + kTwo62 - lo;
-  n = warp_compact(K, n, [&](uint64_t key) {  // the worms of the interval
-    if (!kworm(key)) return false;
-    const uint64_t off = (kpk(key) + kTwo62 - lo) & (kTwo62 - 1);
-    return off > 0 && off < span;
-  });
+  if (erase)
+    n = warp_compact(K, n, [&](uint64_t key) {  // the worms of the interval
+      if (!kworm(key)) return false;
+      const uint64_t off = (kpk(key) + kTwo62 - lo) & (kTwo62 - 1);
+      return off > 0 && off < span;
+    });
   uint64_t offs[kMaxWormsPerInterval];
   int bad = 0;
   const int nw = sample_worms<kMaxWormsPerInterval>(z, st, wpts(lo, hi), p ^ q, d.SWs, d.SWI, offs, &bad);
@@ -334,12 +338,14 @@ __device__ int boundary_bond_update(const Dev& d, int a, int dir, uint64_t* KA, 
       KA[ka] = (KA[ka] & ~3ull) | (uint64_t(s0) << 1) | uint64_t(s2);
       KB[kb] = (KB[kb] & ~3ull) | (uint64_t(s1) << 1) | uint64_t(s3);
     }
-    if (!La.single) rc = regen_interval(d, Z, st, KA, nA, La.plo, pv, La.far_dn, s0);
-    if (!rc && !Lb.single) rc = regen_interval(d, Z, st, KB, nB, Lb.plo, pv, Lb.far_dn, s1);
-    if (!rc) rc = La.single ? regen_interval(d, Z, st, KA, nA, pv, pv, s2, s0)
-                            : regen_interval(d, Z, st, KA, nA, pv, La.phi, s2, La.far_up);
-    if (!rc) rc = Lb.single ? regen_interval(d, Z, st, KB, nB, pv, pv, s3, s1)
-                            : regen_interval(d, Z, st, KB, nB, pv, Lb.phi, s3, Lb.far_up);
+    // (the worm counts of the legs were taken before any redraw; a redraw
+    // below v adds worms only below v, so the counts above v still hold)
+    if (!La.single) rc = regen_interval(d, Z, st, KA, nA, La.plo, pv, La.far_dn, s0, La.wdn > 0);
+    if (!rc && !Lb.single) rc = regen_interval(d, Z, st, KB, nB, Lb.plo, pv, Lb.far_dn, s1, Lb.wdn > 0);
+    if (!rc) rc = La.single ? regen_interval(d, Z, st, KA, nA, pv, pv, s2, s0, La.wup > 0)
+                            : regen_interval(d, Z, st, KA, nA, pv, La.phi, s2, La.far_up, La.wup > 0);
+    if (!rc) rc = Lb.single ? regen_interval(d, Z, st, KB, nB, pv, pv, s3, s1, Lb.wup > 0)
+                            : regen_interval(d, Z, st, KB, nB, pv, Lb.phi, s3, Lb.far_up, Lb.wup > 0);
     if (rc) return rc;
   }
   if (st.pos >= (uint64_t(1) << 33)) return PMWA_ETIMEOUT;
@@ -533,8 +539,8 @@ __device__ int temporal_site(const Dev& d, int s, uint64_t* K, int& n, int& base
       const double u = __dmul_rn(__dmul_rn(__ull2double_rn(wu >> 11), 0x1p-53), tot);
       sn = (u < w0) ? 0 : 1;
     }
-    int rc = regen_interval(d, Z, st, K, n, lo, B, p, sn);
-    if (!rc) rc = regen_interval(d, Z, st, K, n, B, hi, sn, q);
+    int rc = regen_interval(d, Z, st, K, n, lo, B, p, sn, true);
+    if (!rc) rc = regen_interval(d, Z, st, K, n, B, hi, sn, q, true);
     if (rc) return rc;
     if (n == 0) base = sn;
   }

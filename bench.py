@@ -315,7 +315,7 @@ def _rebuild(P, reps, snaps):
     return batch
 
 
-def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=40):
+def batched_vs_plain(P, steps, warmup, n_reps=512, graph_sweeps=None, pilot=100):
     """The 512-replica workload (L in {16..64}, beta t in {1..16}, mu in
     [-2, 2], V in {0, 1}, eta in {0.05, 0.1, 0.2}) swept (a) batched: one
     launch per kernel per sweep and launch group, replayed from a CUDA graph,

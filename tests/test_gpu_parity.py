@@ -60,8 +60,11 @@ GEOMS = [
     # more than 255 passes of the block-wide grouping: its per-chunk counts
     # carry a pass stamp that starts over every 255 passes
     dict(Lx=16, Ly=16, beta=2.0, eta=0.5, sub_block=2, n_cycle=300, seed=53, init=1, init_seed=6),
+    # one Step-5 group of 64 to 128 worms (sub_block 0: the whole domain): a
+    # move may wait for a predecessor 64 or more ranks before it
+    dict(Lx=8, Ly=8, beta=4.0, eta=0.45, sub_block=0, n_cycle=6, seed=59, init=1, init_seed=8),
 ]
-MANY_WORMS = GEOMS[-3:]
+MANY_WORMS = GEOMS[-4:]
 
 
 def _pair(kw):
@@ -179,7 +182,7 @@ def test_rows_buffer_full_is_reported():
 
 @pytest.mark.parametrize("kw", MANY_WORMS)
 def test_many_worm_cases_exceed_one_warp(kw):
-    """The last three geometries really hold more than 32 worms per domain
+    """The last four geometries really hold more than 32 worms per domain
     (so the block-wide passes are the ones compared above)."""
     g = P.Sim(**kw)
     g.sweep(4)

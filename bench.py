@@ -55,13 +55,26 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TILE_SOURCES = ["pmwa_tile.cu", "pmwa_device.cuh", "pmwa_internal.h"]
 
 
+def code_lines(text):
+    """The code of a C/CUDA source without its // comments and blank lines
+    (the sources of the sweep kernel hold no /* */ comments and no // inside
+    a string), so that a change of a comment keeps a capture valid."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out)
+
+
 def tile_source_hash():
-    """sha256 over the sources of the sweep kernel (k_tile)."""
+    """sha256 over the code (comments left out) of the sources of the sweep
+    kernel (k_tile)."""
     import hashlib
     h = hashlib.sha256()
     for f in TILE_SOURCES:
-        with open(os.path.join(ROOT, "paper_1307_0328_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1307_0328_gb300", "csrc", f)) as fh:
+            h.update(code_lines(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -2,16 +2,19 @@
 // domain, the domain's vertex legs and worms resident in shared memory.
 //
 //   phase 1  Step 3 candidates, one thread per bond of the domain, written to
-//            a shared pool (the current configuration is read from HBM/L2)
+//            a shared pool (the current configuration is read from HBM/L2,
+//            prefetched into L2 by bulk copies at kernel start)
 //   phase 2  per site: the kept vertex legs of the current configuration
 //            merged in time order with the new ones into the shared leg array
 //   phase 3  Step 4, one thread per site: worms of every interval (Eq. 1)
 //            into the shared worm table; each worm records its site and the
 //            index of the vertex leg just below it (its interval)
 //   phase 4  Step 5, N_cycle passes of the shifted sub-block schedule: worms
-//            bucketed by sub-block, one thread per sub-block moves its worms
-//            in label order (Eq. 2); vertex legs never move in Step 5, so a
-//            move is a handful of shared-memory reads and two bit flips
+//            grouped by sub-block, each group's worms moved in label order
+//            (Eq. 2) by rounds of moves whose intervals do not meet, which
+//            gives the moves made one by one; vertex legs never move in
+//            Step 5, so a move is a handful of shared-memory reads and two
+//            bit flips
 //   phase 5  legs and worms merged per site into the next configuration in
 //            HBM, with the Step-6 counters and the Supplement S-I estimator
 //

